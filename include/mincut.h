@@ -1,0 +1,187 @@
+/*
+ * mincut.h -- C ABI of the GB300 exact minimum-cut library (libmincut.so).
+ *
+ * Problem (Sec. 2, "Basic Concepts"): G = (V, E, c) undirected with
+ * non-negative integer edge weights.  A cut (A, V \ A) splits V into two
+ * non-empty sides; its capacity is the total weight of the edges between
+ * them; lambda(G) is the smallest capacity.  The library computes lambda(G)
+ * exactly with the contraction rounds of Sec. 2.1 / Algorithm 2: bounds from
+ * vertex degrees (trivial and collapsed-vertex cuts) and label propagation,
+ * edge marking by the Padberg-Rinaldi tests and by concurrent CAPFOREST
+ * passes (Algorithm 1), union-find over the marked edges and CSR contraction,
+ * until the graph is trivial or the bound is proven.  All arithmetic is exact
+ * integer: int32 input weights, int64 cut values.
+ *
+ * Conventions shared by every call
+ *   - Graph input: a symmetric CSR.  row_ptr int64[n+1] (row_ptr[0] = 0,
+ *     non-decreasing), col int32[M] with values in [0, n), w int32[M] >= 0.
+ *     Every undirected edge {u, v} appears in row u and in row v with the same
+ *     total weight.  Rows need not be sorted; duplicate entries are summed,
+ *     self-loops and zero weights are dropped.
+ *   - Streams: every call is ordered on the CUDA stream given at graph
+ *     creation and returns after that stream's work for the call finished.
+ *   - Ownership: the library copies inputs; callers own every buffer they
+ *     pass; the library owns a graph's device memory until
+ *     mincut_graph_destroy().
+ *   - Errors: every int-returning call returns a mincut_status; on error
+ *     mincut_last_error() gives a per-thread message.  Calls on distinct
+ *     graphs are thread-safe; calls on one graph must not overlap.
+ *   - Device waits inside kernels are bounded; a wait that runs out sets an
+ *     error status (MINCUT_ERR_DEVICE_TIMEOUT) instead of hanging.
+ */
+#ifndef MINCUT_H
+#define MINCUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MINCUT_OK = 0,
+    MINCUT_ERR_INVALID = -1,        /* bad argument or malformed graph */
+    MINCUT_ERR_OOM = -2,            /* device allocation failed */
+    MINCUT_ERR_OVERFLOW = -3,       /* a size or sum exceeds the supported range */
+    MINCUT_ERR_DEVICE_TIMEOUT = -4, /* a bounded device wait ran out */
+    MINCUT_ERR_CUDA = -5,           /* a CUDA runtime call failed */
+    MINCUT_ERR_INTERNAL = -6        /* an internal consistency check failed */
+} mincut_status;
+
+/* flags of mincut_graph_from_csr */
+#define MINCUT_HOST_PTRS 0u      /* row_ptr/col/w are host pointers */
+#define MINCUT_DEVICE_PTRS 1u    /* row_ptr/col/w are device pointers */
+#define MINCUT_SKIP_VALIDATE 2u  /* caller guarantees symmetry; skip that check */
+
+/* Device allocator used for all of a graph's device memory.  alloc returns a
+ * device pointer of at least `bytes` (256-byte aligned) or NULL; free releases
+ * it.  Both are called on the host thread that makes the library call, with
+ * the graph's stream.  NULL allocator: cudaMallocAsync / cudaFreeAsync. */
+typedef struct mincut_allocator {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} mincut_allocator;
+
+typedef struct mincut_graph mincut_graph; /* opaque, device-resident */
+
+/* Options of a full solve.  mincut_default_options() fills the defaults. */
+typedef struct mincut_options {
+    int32_t lp_iters;        /* label-propagation sweeps per bound (default 2; 0 = off) */
+    int32_t lp_min_n;        /* run LP only on graphs with n >= lp_min_n (default 10000) */
+    int32_t lp_every_round;  /* 1: LP bound in every round (default); 0: first round only */
+    uint32_t pr_mask;        /* PR1..PR4 as bits 0..3 (default 0xF) */
+    int64_t pr_budget;       /* PR3/PR4 only if min(|N(u)|,|N(v)|) <= budget (default 64; <0 = all) */
+    int32_t passes;          /* concurrent CAPFOREST passes per wave (0 = auto) */
+    int32_t pass_table;      /* per-pass table slots, power of two in [256, 2048] (0 = auto) */
+    int32_t waves;           /* CAPFOREST waves per round (0 = auto) */
+    uint64_t seed;           /* start-vertex seed of the concurrent passes */
+    int32_t deterministic;   /* 1: one sequential CAPFOREST pass from vertex 0 per round */
+    int32_t max_rounds;      /* 0 = unlimited */
+    int64_t spin_limit;      /* iteration limit of bounded device waits (0 = default) */
+} mincut_options;
+
+/* Statistics of a solve (all optional to read). */
+typedef struct mincut_stats {
+    int64_t n_input, m_input;    /* canonical input: vertices, undirected edges */
+    int32_t rounds;              /* contraction rounds run */
+    int32_t seq_passes;          /* rounds that needed the sequential CAPFOREST pass */
+    int64_t marks_pr;            /* edges marked by PR1..PR4 over all rounds */
+    int64_t marks_cf;            /* edges marked by CAPFOREST over all rounds */
+    int64_t entries_processed;   /* sum over rounds of the round graph's directed entries */
+    int32_t lambda_source;       /* 1 degree, 2 label propagation, 3 CAPFOREST alpha */
+    int32_t kernel_launches;     /* kernels launched by the solve */
+    double ms_total;             /* host wall time of the solve */
+} mincut_stats;
+
+/* One round, for testing and for callers that drive the loop themselves.
+ * Zero-initialise, then set what you need (mincut_default_round_options()). */
+typedef struct mincut_round_options {
+    int64_t lambda_in;       /* carried-in upper bound (INT64_MAX: none) */
+    int32_t lp_iters, lp_min_n;
+    uint32_t pr_mask;
+    int64_t pr_budget;
+    int32_t capforest;       /* 0 none; 1 concurrent passes (+ sequential pass if no
+                                marks); 2 one sequential pass from cf_start */
+    int32_t cf_start;
+    int32_t passes, pass_table, waves;
+    uint64_t seed;
+    /* optional external marking (host pointers; replaces all marking):   */
+    const int32_t* groups;   /* [n] group id in [0, n) per vertex: contract each group */
+    int64_t npairs;          /* or: contract the components of these pairs */
+    const int32_t* pair_u;
+    const int32_t* pair_v;
+    /* optional outputs (host pointers, sized for the round's input graph): */
+    uint8_t* pr_flags_out;   /* [M] PR flags (bit0..3 = PR1..PR4) per directed entry */
+    int32_t* cf_order_out;   /* [n] visit order of the sequential pass (capforest == 2) */
+    int32_t* cf_marks_out;   /* [2*cf_marks_cap] marked pairs (x, y) of that pass */
+    int64_t cf_marks_cap;
+} mincut_round_options;
+
+typedef struct mincut_round_result {
+    int64_t n_in, m_in;      /* round input: vertices, directed entries */
+    int64_t n_out, m_out;    /* contracted graph */
+    int64_t lambda_out;      /* bound after the round */
+    int64_t marks_pr, marks_cf;
+    int32_t stopped;         /* 1: n <= 2 or bound 0 after the degree bound (no contraction) */
+    int32_t seq_pass;        /* 1: the sequential CAPFOREST pass ran */
+    int64_t cf_nscanned;     /* vertices visited by the sequential pass */
+    int64_t cf_nmarks;       /* marks of the sequential pass */
+} mincut_round_result;
+
+void mincut_default_options(mincut_options* o);
+void mincut_default_round_options(mincut_round_options* ro);
+
+/* Build a device graph from a CSR (Sec. 2, G = (V, E, c)).  The graph is
+ * validated (indices in range, weights >= 0, symmetric unless
+ * MINCUT_SKIP_VALIDATE) and brought to canonical form: rows sorted, duplicates
+ * summed, self-loops and zero weights dropped.  n >= 2 (a cut needs two
+ * non-empty sides, Sec. 2) else MINCUT_ERR_INVALID.  cuda_stream is a
+ * cudaStream_t (NULL: the legacy default stream).  On success *out owns the
+ * graph. */
+int mincut_graph_from_csr(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                          const int32_t* w, uint32_t flags, void* cuda_stream,
+                          const mincut_allocator* alloc, mincut_graph** out);
+
+/* Exact minimum cut (Algorithm 2 with the round of Sec. 2.1).  *cut_value =
+ * lambda(G).  side_bitmap (nullable; host or device memory, ceil(n/64)
+ * words): bit v (word v/64, bit v%64) is 1 iff vertex v is on the side of a
+ * minimum cut that does not contain vertex 0; both sides are non-empty.
+ * stats is nullable.  Starts from the input graph (solve does not consume
+ * the rounds run by mincut_contract_round). */
+int mincut_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_value,
+                 uint64_t* side_bitmap, mincut_stats* stats);
+
+/* Run one contraction round on the graph's current state and replace it by
+ * the contracted graph (Algorithm 2, one loop iteration; Algorithm 1 for the
+ * CAPFOREST marking).  With ro->groups or ro->pair_u/pair_v set, only the
+ * contraction runs, with that marking.  res is required. */
+int mincut_contract_round(mincut_graph* g, const mincut_round_options* ro,
+                          mincut_round_result* res);
+
+/* Size of the graph's current state: vertices and directed CSR entries. */
+int mincut_graph_info(const mincut_graph* g, int64_t* n, int64_t* m_directed);
+
+/* Copy the current canonical CSR to host buffers sized by mincut_graph_info:
+ * row_ptr[n+1], col[M], w[M] (weights widened to int64). */
+int mincut_graph_export_csr(const mincut_graph* g, int64_t* row_ptr, int32_t* col,
+                            int64_t* w);
+
+/* Return the current state to the canonical input graph. */
+int mincut_graph_reset(mincut_graph* g);
+
+/* Release a graph and its device memory (NULL is ignored). */
+void mincut_graph_destroy(mincut_graph* g);
+
+/* Static description of a status code. */
+const char* mincut_status_string(int status);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* mincut_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MINCUT_H */

@@ -405,7 +405,10 @@ void orc_pr_marks(int32_t n, const int64_t* rp, const int32_t* col, const int64_
  * order (capacity n) and *nscanned, q_out[M] (q(e) on the entry x->y that was
  * scanned, -1 elsewhere), *best_len = length of the visited prefix whose cut
  * gave the returned lambda (0 if lambda never dropped below lambda_in).
- * Returns the final lambda. */
+ * Returns the final lambda.
+ * Note: when alpha lowers lambda, every queued y has r(y) = c(y, S) <= c(S,
+ * V \ S) = alpha, so no stored key exceeds the new bound; re-capping the queue
+ * at that moment would change nothing. */
 int64_t orc_capforest(int32_t n, const int64_t* rp, const int32_t* col, const int64_t* w,
                       int64_t lambda, int32_t start, int32_t* mark_u, int32_t* mark_v,
                       int64_t* nmarks, int32_t* order, int32_t* nscanned, int64_t* q_out,

@@ -1,0 +1,340 @@
+"""Python binding of libmincut.so, the GB300 exact minimum-cut library.
+
+Argument marshalling only: every step of a solve runs in the CUDA kernels of
+``libmincut.so`` (see ``include/mincut.h``).  The names follow the C ABI:
+
+    g = mincut_graph_from_csr(n, row_ptr, col, w)     # numpy (host) or torch CUDA tensors
+    value, side_bitmap, stats = mincut_solve(g)
+    res = mincut_contract_round(g, round_options)
+    n, M = mincut_graph_info(g); rp, col, w = mincut_graph_export_csr(g)
+    mincut_graph_reset(g); mincut_graph_destroy(g)
+
+PyTorch supplies device memory (optionally through its caching allocator,
+``use_torch_allocator=True``) and the CUDA stream.  There is no CPU fallback:
+importing works anywhere, but every call raises if libmincut.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Any, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmincut.so")
+INT64_MAX = (1 << 63) - 1
+
+MINCUT_OK = 0
+MINCUT_ERR_INVALID = -1
+MINCUT_ERR_OOM = -2
+MINCUT_ERR_OVERFLOW = -3
+MINCUT_ERR_DEVICE_TIMEOUT = -4
+MINCUT_ERR_CUDA = -5
+MINCUT_ERR_INTERNAL = -6
+
+MINCUT_HOST_PTRS = 0
+MINCUT_DEVICE_PTRS = 1
+MINCUT_SKIP_VALIDATE = 2
+
+
+class MincutError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mincut status {status}: {msg}")
+        self.status = status
+
+
+class MincutOptions(ctypes.Structure):
+    _fields_ = [("lp_iters", ctypes.c_int32), ("lp_min_n", ctypes.c_int32),
+                ("lp_every_round", ctypes.c_int32), ("pr_mask", ctypes.c_uint32),
+                ("pr_budget", ctypes.c_int64), ("passes", ctypes.c_int32),
+                ("pass_table", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("deterministic", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+
+
+class MincutStats(ctypes.Structure):
+    _fields_ = [("n_input", ctypes.c_int64), ("m_input", ctypes.c_int64),
+                ("rounds", ctypes.c_int32), ("seq_passes", ctypes.c_int32),
+                ("marks_pr", ctypes.c_int64), ("marks_cf", ctypes.c_int64),
+                ("entries_processed", ctypes.c_int64), ("lambda_source", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MincutRoundOptions(ctypes.Structure):
+    _fields_ = [("lambda_in", ctypes.c_int64), ("lp_iters", ctypes.c_int32),
+                ("lp_min_n", ctypes.c_int32), ("pr_mask", ctypes.c_uint32),
+                ("pr_budget", ctypes.c_int64), ("capforest", ctypes.c_int32),
+                ("cf_start", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("pass_table", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("seed", ctypes.c_uint64),
+                ("groups", ctypes.c_void_p), ("npairs", ctypes.c_int64),
+                ("pair_u", ctypes.c_void_p), ("pair_v", ctypes.c_void_p),
+                ("pr_flags_out", ctypes.c_void_p), ("cf_order_out", ctypes.c_void_p),
+                ("cf_marks_out", ctypes.c_void_p), ("cf_marks_cap", ctypes.c_int64)]
+
+
+class MincutRoundResult(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int64), ("m_in", ctypes.c_int64), ("n_out", ctypes.c_int64),
+                ("m_out", ctypes.c_int64), ("lambda_out", ctypes.c_int64),
+                ("marks_pr", ctypes.c_int64), ("marks_cf", ctypes.c_int64),
+                ("stopped", ctypes.c_int32), ("seq_pass", ctypes.c_int32),
+                ("cf_nscanned", ctypes.c_int64), ("cf_nmarks", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                            ctypes.c_void_p)
+
+
+class MincutAllocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libmincut.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    lib.mincut_default_options.argtypes = [ctypes.POINTER(MincutOptions)]
+    lib.mincut_default_round_options.argtypes = [ctypes.POINTER(MincutRoundOptions)]
+    lib.mincut_graph_from_csr.argtypes = [i64, vp, vp, vp, u32, vp,
+                                          ctypes.POINTER(MincutAllocator),
+                                          ctypes.POINTER(vp)]
+    lib.mincut_graph_from_csr.restype = ctypes.c_int
+    lib.mincut_solve.argtypes = [vp, ctypes.POINTER(MincutOptions), ctypes.POINTER(i64), vp,
+                                 ctypes.POINTER(MincutStats)]
+    lib.mincut_solve.restype = ctypes.c_int
+    lib.mincut_contract_round.argtypes = [vp, ctypes.POINTER(MincutRoundOptions),
+                                          ctypes.POINTER(MincutRoundResult)]
+    lib.mincut_contract_round.restype = ctypes.c_int
+    lib.mincut_graph_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.mincut_graph_info.restype = ctypes.c_int
+    lib.mincut_graph_export_csr.argtypes = [vp, vp, vp, vp]
+    lib.mincut_graph_export_csr.restype = ctypes.c_int
+    lib.mincut_graph_reset.argtypes = [vp]
+    lib.mincut_graph_reset.restype = ctypes.c_int
+    lib.mincut_graph_destroy.argtypes = [vp]
+    lib.mincut_graph_destroy.restype = None
+    lib.mincut_status_string.argtypes = [ctypes.c_int]
+    lib.mincut_status_string.restype = ctypes.c_char_p
+    lib.mincut_last_error.argtypes = []
+    lib.mincut_last_error.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int) -> None:
+    if rc != MINCUT_OK:
+        lib = load_library()
+        msg = (lib.mincut_last_error() or b"").decode() or lib.mincut_status_string(rc).decode()
+        raise MincutError(rc, msg)
+
+
+def default_options(**kw) -> MincutOptions:
+    o = MincutOptions()
+    load_library().mincut_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def default_round_options(**kw) -> MincutRoundOptions:
+    o = MincutRoundOptions()
+    load_library().mincut_default_round_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _is_torch_cuda(x: Any) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through torch's caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live: dict[int, int] = {}
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                         stream if stream else None)
+            except Exception:
+                return None
+            self.live[int(ptr)] = int(nbytes)
+            return int(ptr)
+
+        def _free(ptr, nbytes, stream, ctx):
+            if ptr and int(ptr) in self.live:
+                del self.live[int(ptr)]
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._alloc = _ALLOC_FN(_alloc)
+        self._free = _FREE_FN(_free)
+        self.struct = MincutAllocator(self._alloc, self._free, None)
+
+
+class Graph:
+    """Owning handle of a device graph (destroyed with mincut_graph_destroy)."""
+
+    def __init__(self, handle: int, n: int, keep: list, allocator=None):
+        self.handle = ctypes.c_void_p(handle)
+        self.n = n
+        self._keep = keep
+        self._allocator = allocator
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def destroy(self) -> None:
+        if self.handle and self.handle.value:
+            load_library().mincut_graph_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+
+def mincut_graph_from_csr(n: int, row_ptr, col, w, *, stream: Any = None,
+                          skip_validate: bool = False, use_torch_allocator: bool = False
+                          ) -> Graph:
+    """Build a device graph from a symmetric CSR (numpy host arrays or torch
+    CUDA tensors: int64 row_ptr[n+1], int32 col[M], int32 w[M])."""
+    lib = load_library()
+    keep = []
+    if _is_torch_cuda(row_ptr):
+        import torch
+        assert row_ptr.dtype == torch.int64 and col.dtype == torch.int32 and w.dtype == torch.int32
+        row_ptr, col, w = row_ptr.contiguous(), col.contiguous(), w.contiguous()
+        keep += [row_ptr, col, w]
+        ptrs = (row_ptr.data_ptr(), col.data_ptr(), w.data_ptr())
+        flags = MINCUT_DEVICE_PTRS
+        if stream is None:
+            stream = torch.cuda.current_stream(row_ptr.device).cuda_stream
+        device = row_ptr.device.index or 0
+    else:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int32)
+        if col.size == 0:
+            col = np.zeros(1, np.int32)
+            w = np.zeros(1, np.int32)
+        keep += [row_ptr, col, w]
+        ptrs = (row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data)
+        flags = MINCUT_HOST_PTRS
+        device = 0
+    if skip_validate:
+        flags |= MINCUT_SKIP_VALIDATE
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    alloc = _TorchAllocator(device) if use_torch_allocator else None
+    out = ctypes.c_void_p(0)
+    rc = lib.mincut_graph_from_csr(n, ptrs[0], ptrs[1], ptrs[2], flags,
+                                   ctypes.c_void_p(stream or 0),
+                                   ctypes.byref(alloc.struct) if alloc else None,
+                                   ctypes.byref(out))
+    _check(rc)
+    return Graph(out.value, n, keep, alloc)
+
+
+def mincut_solve(g: Graph, opts: Optional[MincutOptions] = None, *, bitmap: bool = True,
+                 side_bitmap_out=None):
+    """Exact minimum cut.  Returns (value, bitmap uint64[ceil(n/64)] or None,
+    stats dict).  side_bitmap_out may be a torch CUDA tensor (int64) or a
+    numpy uint64 array to write into."""
+    lib = load_library()
+    val = ctypes.c_int64(0)
+    st = MincutStats()
+    bm = None
+    ptr = None
+    if side_bitmap_out is not None:
+        bm = side_bitmap_out
+        ptr = bm.data_ptr() if _is_torch_cuda(bm) else bm.ctypes.data
+    elif bitmap:
+        bm = np.zeros((g.n + 63) // 64, np.uint64)
+        ptr = bm.ctypes.data
+    rc = lib.mincut_solve(g.handle, ctypes.byref(opts) if opts is not None else None,
+                          ctypes.byref(val), ctypes.c_void_p(ptr) if ptr else None,
+                          ctypes.byref(st))
+    _check(rc)
+    return int(val.value), bm, st.as_dict()
+
+
+def bitmap_to_side(bm: np.ndarray, n: int) -> np.ndarray:
+    """uint8[n] side flags from a solve bitmap (bit v of word v // 64)."""
+    bits = np.unpackbits(np.asarray(bm, dtype=np.uint64).view(np.uint8), bitorder="little")
+    return bits[:n].astype(np.uint8)
+
+
+def mincut_contract_round(g: Graph, ro: Optional[MincutRoundOptions] = None) -> dict:
+    """One contraction round on the graph's current state (see the header)."""
+    lib = load_library()
+    if ro is None:
+        ro = default_round_options()
+    res = MincutRoundResult()
+    _check(lib.mincut_contract_round(g.handle, ctypes.byref(ro), ctypes.byref(res)))
+    return res.as_dict()
+
+
+def mincut_graph_info(g: Graph) -> tuple[int, int]:
+    n = ctypes.c_int64(0)
+    m = ctypes.c_int64(0)
+    _check(load_library().mincut_graph_info(g.handle, ctypes.byref(n), ctypes.byref(m)))
+    return int(n.value), int(m.value)
+
+
+def mincut_graph_export_csr(g: Graph):
+    """Current canonical CSR as numpy arrays (row_ptr int64, col int32, w int64)."""
+    n, M = mincut_graph_info(g)
+    rp = np.zeros(n + 1, np.int64)
+    col = np.zeros(max(M, 1), np.int32)
+    w = np.zeros(max(M, 1), np.int64)
+    _check(load_library().mincut_graph_export_csr(g.handle, rp.ctypes.data, col.ctypes.data,
+                                                  w.ctypes.data))
+    return rp, col[:M], w[:M]
+
+
+def mincut_graph_reset(g: Graph) -> None:
+    _check(load_library().mincut_graph_reset(g.handle))
+
+
+def mincut_graph_destroy(g: Graph) -> None:
+    g.destroy()
+
+
+def mincut_status_string(status: int) -> str:
+    return load_library().mincut_status_string(status).decode()
+
+
+def mincut_last_error() -> str:
+    return (load_library().mincut_last_error() or b"").decode()
+
+
+def exported_symbols() -> list[str]:
+    """Function names declared in include/mincut.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "mincut.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(mincut_[a-z_]+)\s*\(", text)))

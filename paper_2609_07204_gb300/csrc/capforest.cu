@@ -1,0 +1,492 @@
+// capforest.cu -- CAPFOREST edge marking (Algorithm 1; Sec. 2.1).
+//
+// A pass grows a visited set S in maximum-adjacency order: it repeatedly takes
+// the queued vertex x of highest bounded priority Q(x) = min(r(x), lambda)
+// (ties: the smaller vertex id), adds it to S, updates
+// alpha += c(x) - 2 r(x) (alpha = capacity of the cut (S, V \ S)) and lowers
+// lambda to alpha while S != V, then scans x's edges to unvisited y:
+// if r(y) < lambda <= r(y) + c(x, y) the edge is contractible (union-find
+// hook), r(y) += c(x, y), Q(y) = min(r(y), lambda).
+//
+// capforest_passes: Algorithm 1 proper.  Many passes run at once, one warp
+// each, from seeded start vertices; the shared visit array T is `owner`
+// (a vertex is claimed by CAS, so each vertex is scanned by one pass; a pass
+// that pops a vertex claimed by another pass blacklists it).  An edge whose
+// far end is already claimed by another pass is skipped when scanned; that
+// only removes marks (marking fewer edges is always sound) and keeps the
+// pass a maximum-adjacency prefix of G minus the vertices it saw claimed.
+// Each pass keeps its queue in shared memory: an open-addressing table of
+// `table` slots (vertex, r, packed priority) plus one max per 32 slots.  A
+// pass stops when the next vertex's row might overflow the table (stopping
+// early keeps every mark valid: the marks only depend on the prefix).
+//
+// capforest_sequential: one pass over the whole graph by one block (the
+// sequential CAPFOREST of Algorithm 2, used when the concurrent passes mark
+// nothing, and the deterministic mode).  Its queue is a 32-ary max tree over
+// per-vertex keys (key + 1, 0 = not queued); the descent takes the leftmost
+// maximum, i.e. the smallest vertex id among the largest keys.  Keys only
+// grow between pops (when alpha lowers lambda, every queued r(y) is at most
+// alpha, so no key exceeds the new bound), so the tree is maintained with
+// atomicMax and recomputed only along the popped vertex's path.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mc {
+
+namespace {
+
+int num_sms_cf() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned slot_hash(int v) { return (unsigned)v * 0x9E3779B1u; }
+
+// Packed priority: (key + 1) in the high word, ~vertex in the low word, so
+// the maximum is the largest key and, among equal keys, the smallest vertex.
+__device__ __forceinline__ unsigned long long pack_key(long long key, int v) {
+  return ((unsigned long long)(key + 1) << 32) | (unsigned long long)(0xffffffffu - (unsigned)v);
+}
+
+// ------------------------------------------------------ concurrent passes
+template <typename WT>
+__global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                                 const WT* __restrict__ w, const WT* __restrict__ deg,
+                                 int* owner, int* parent, int* __restrict__ visit_log,
+                                 unsigned long long* __restrict__ pass_best,
+                                 int* __restrict__ pass_len, int total_passes, int table,
+                                 unsigned long long seed, int* pass_counter, DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int nsum = table >> 5;
+  const size_t per_warp = (size_t)table * (sizeof(int) + sizeof(WT) + 8) + (size_t)nsum * 8;
+  unsigned char* base = smem + per_warp * warp;
+  unsigned long long* pk = reinterpret_cast<unsigned long long*>(base);
+  unsigned long long* summ = pk + table;
+  WT* rr = reinterpret_cast<WT*>(summ + nsum);
+  int* vid = reinterpret_cast<int*>(rr + table);
+  volatile int* vowner = owner;
+  const int load_cap = table - (table >> 3);
+
+  unsigned long long marks_total = 0, scanned_total = 0;
+  bool uf_fail = false;
+  for (;;) {
+    int p = 0;
+    if (lane == 0) p = atomicAdd(pass_counter, 1);
+    p = __shfl_sync(FULL, p, 0);
+    if (p >= total_passes) break;
+    // ---- reset the table
+    for (int i = lane; i < table; i += 32) { vid[i] = -1; rr[i] = 0; pk[i] = 0; }
+    for (int i = lane; i < nsum; i += 32) summ[i] = 0;
+    __syncwarp();
+    long long lam = (long long)*(volatile unsigned long long*)&st->lambda;
+    // ---- start vertex: hash(seed, p), then the first unclaimed of 32 probes
+    int start = -1;
+    {
+      const unsigned long long h = mix64(seed ^ mix64((unsigned long long)p + 1));
+      const int s0 = (int)(h % (unsigned long long)n);
+      for (int tries = 0; tries < 4 && start < 0; ++tries) {
+        const int c = (int)(((long long)s0 + tries * 32 + lane) % n);
+        const unsigned free_mask = __ballot_sync(FULL, vowner[c] == 0);
+        if (free_mask) start = __shfl_sync(FULL, c, __ffs(free_mask) - 1);
+      }
+    }
+    unsigned long long best_alpha = ~0ull;
+    int best_len = 0;
+    if (start >= 0 && lam > 0) {
+      if (lane == 0) {
+        const int h = slot_hash(start) & (table - 1);
+        vid[h] = start;
+        pk[h] = pack_key(0, start);
+        summ[h >> 5] = pk[h];
+      }
+      __syncwarp();
+      int count = 1, nscanned = 0;
+      long long alpha = 0;
+      for (int it = 0; it < table; ++it) {
+        // ---- pop the maximum packed priority
+        unsigned long long m = 0;
+        int mchunk = -1;
+        for (int c = lane; c < nsum; c += 32) {
+          const unsigned long long x = summ[c];
+          if (x > m) { m = x; mchunk = c; }
+        }
+        const unsigned long long gm = warp_max(m);
+        if (gm == 0) break;
+        const unsigned hit = __ballot_sync(FULL, m == gm && mchunk >= 0);
+        const int chunk = __shfl_sync(FULL, mchunk, __ffs(hit) - 1);
+        const int slot_l = chunk * 32 + lane;
+        const unsigned own = __ballot_sync(FULL, pk[slot_l] == gm);
+        if (own == 0) {  // cannot happen: summaries are exact maxima
+          if (lane == 0) set_error(st, ERR_INTERNAL);
+          break;
+        }
+        const int wl = __ffs(own) - 1;
+        const int slot = chunk * 32 + wl;
+        const int x = vid[slot];
+        const long long rx = (long long)rr[slot];
+        __syncwarp();
+        if (lane == wl) pk[slot] = 0;
+        __syncwarp();
+        {
+          const unsigned long long y = warp_max(pk[slot_l]);
+          if (lane == 0) summ[chunk] = y;
+        }
+        __syncwarp();
+        const long long rb = rp[x], re = rp[x + 1];
+        if (count + (re - rb) > load_cap) break;  // the row might not fit: stop
+        int claimed = 0;
+        if (lane == 0) claimed = atomicCAS(&owner[x], 0, p + 1) == 0;
+        claimed = __shfl_sync(FULL, claimed, 0);
+        if (!claimed) continue;  // blacklisted: visited by another pass
+        ++nscanned;
+        if (lane == 0) visit_log[(long long)p * table + nscanned - 1] = x;
+        alpha += (long long)deg[x] - 2 * rx;
+        if (nscanned < n && alpha < lam) {
+          lam = alpha;
+          best_alpha = (unsigned long long)alpha;
+          best_len = nscanned;
+          if (lane == 0) atomicMin(&st->lambda, (unsigned long long)alpha);
+        }
+        // ---- scan x's edges
+        for (long long b = rb; b < re; b += 32) {
+          const long long e = b + lane;
+          bool ins = false;
+          if (e < re) {
+            const int y = col[e];
+            if (vowner[y] == 0) {
+              unsigned h = slot_hash(y) & (table - 1);
+              int s = -1;
+              for (int probe = 0; probe < table; ++probe) {
+                const int k = vid[h];
+                if (k == y) { s = h; break; }
+                if (k == -1) {
+                  const int prev = atomicCAS(&vid[h], -1, y);
+                  if (prev == -1) { s = h; ins = true; break; }
+                  if (prev == y) { s = h; break; }
+                }
+                h = (h + 1) & (table - 1);
+              }
+              // a popped slot (priority cleared) belongs to a vertex this pass
+              // already took; the owner check above normally skips it
+              if (s >= 0 && (ins || pk[s] != 0)) {
+                const long long c = (long long)w[e];
+                const long long r0 = (long long)rr[s];
+                const long long r1 = r0 + c;
+                rr[s] = (WT)r1;
+                if (r0 < lam && lam <= r1) {
+                  if (!uf_union(parent, x, y)) uf_fail = true;
+                  ++marks_total;
+                }
+                const unsigned long long np = pack_key(r1 < lam ? r1 : lam, y);
+                if (np > pk[s]) pk[s] = np;
+                atomicMax(&summ[s >> 5], np);
+              }
+            }
+          }
+          count += __popc(__ballot_sync(FULL, ins));
+          __syncwarp();
+        }
+      }
+      scanned_total += nscanned;
+    }
+    if (lane == 0) {
+      pass_best[p] = best_alpha;
+      pass_len[p] = best_len;
+    }
+  }
+  if (uf_fail) set_error(st, ERR_INTERNAL);
+  marks_total = warp_sum(marks_total);
+  if (lane == 0) {
+    if (marks_total) atomicAdd(&st->marks_cf, marks_total);
+    if (scanned_total) atomicAdd((unsigned long long*)&st->claimed, scanned_total);
+  }
+  (void)nwarps;
+}
+
+__global__ void cf_best_kernel(const unsigned long long* __restrict__ pass_best,
+                               const int* __restrict__ pass_len, int passes, DevState* st) {
+  __shared__ unsigned long long sv[32];
+  __shared__ int sp[32];
+  unsigned long long bv = ~0ull;
+  int bp = 0x7fffffff;
+  for (int p = threadIdx.x; p < passes; p += blockDim.x) {
+    const unsigned long long v = pass_best[p];
+    if (v < bv || (v == bv && p < bp)) { bv = v; bp = p; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v2 = __shfl_xor_sync(FULL, bv, o);
+    const int p2 = __shfl_xor_sync(FULL, bp, o);
+    if (v2 < bv || (v2 == bv && p2 < bp)) { bv = v2; bp = p2; }
+  }
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = bv; sp[threadIdx.x >> 5] = bp; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2)
+      if (sv[w2] < bv || (sv[w2] == bv && sp[w2] < bp)) { bv = sv[w2]; bp = sp[w2]; }
+    st->cf_val = bv;
+    st->cf_pass = bv == ~0ull ? -1 : bp;
+    st->cf_len = bv == ~0ull ? 0 : pass_len[bp];
+  }
+}
+
+// ------------------------------------------------------ sequential pass
+// Tree levels: level 0 has the n leaves padded to a multiple of 32; each
+// higher level has one node per 32 nodes below, padded likewise, until a
+// level has at most 32 nodes (the top, reduced by one warp).
+struct TreeLayout {
+  int levels;
+  long long off[8];
+  long long size[8];
+};
+
+__host__ __device__ inline TreeLayout tree_layout(int n) {
+  TreeLayout t{};
+  long long sz = ((long long)n + 31) / 32 * 32;
+  long long off = 0;
+  int l = 0;
+  for (;;) {
+    t.off[l] = off;
+    t.size[l] = sz;
+    off += sz;
+    ++l;
+    if (sz <= 32 || l == 8) break;
+    sz = (sz / 32 + 31) / 32 * 32;
+  }
+  t.levels = l;
+  return t;
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(512)
+    cf_seq_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                  const WT* __restrict__ w, const WT* __restrict__ deg, int start, int* parent,
+                  WT* g_r, uint8_t* g_vis, unsigned long long* g_tree, int* __restrict__ order,
+                  int* __restrict__ marks_out, long long marks_cap, int use_smem,
+                  DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_x;
+  __shared__ long long s_lam;
+  __shared__ int s_done;
+  __shared__ unsigned long long s_nmarks;
+  const TreeLayout tl = tree_layout(n);
+  const long long tree_words = tl.off[tl.levels - 1] + tl.size[tl.levels - 1];
+  volatile unsigned long long* tree;
+  volatile WT* r;
+  volatile uint8_t* vis;
+  if (use_smem) {
+    tree = reinterpret_cast<unsigned long long*>(smem);
+    r = reinterpret_cast<WT*>(smem + tree_words * 8);
+    vis = reinterpret_cast<uint8_t*>(smem + tree_words * 8 + (long long)n * sizeof(WT));
+  } else {
+    tree = g_tree;
+    r = g_r;
+    vis = g_vis;
+  }
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (long long i = tid; i < tree_words; i += blockDim.x) tree[i] = 0;
+  for (long long i = tid; i < n; i += blockDim.x) { r[i] = 0; vis[i] = 0; }
+  if (tid == 0) {
+    s_lam = (long long)st->lambda;
+    s_done = 0;
+    s_nmarks = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned long long k1 = 1;  // key 0 of the start vertex
+    long long idx = start;
+    for (int l = 0; l < tl.levels; ++l) {
+      tree[tl.off[l] + idx] = k1;
+      idx >>= 5;
+    }
+  }
+  __syncthreads();
+  long long alpha = 0, best_alpha = -1;
+  int ns = 0, best_len = 0;
+  bool uf_fail = false;
+  unsigned long long my_marks = 0;
+  for (int it = 0; it < n; ++it) {
+    if (warp == 0) {
+      // ---- descend to the leftmost maximum
+      const int top = tl.levels - 1;
+      const unsigned long long tv = lane < tl.size[top] ? tree[tl.off[top] + lane] : 0;
+      const unsigned long long m = warp_max(tv);
+      if (m == 0) {
+        if (lane == 0) s_done = 1;
+      } else {
+        long long idx = __ffs(__ballot_sync(FULL, tv == m)) - 1;
+        for (int l = top - 1; l >= 0; --l) {
+          const unsigned long long cv = tree[tl.off[l] + idx * 32 + lane];
+          idx = idx * 32 + (__ffs(__ballot_sync(FULL, cv == m)) - 1);
+        }
+        const int x = (int)idx;
+        // ---- pop: clear the leaf and recompute its ancestors
+        if (lane == 0) tree[x] = 0;
+        __syncwarp();
+        long long child = x;
+        for (int l = 1; l < tl.levels; ++l) {
+          const long long node = child >> 5;
+          const unsigned long long cv = tree[tl.off[l - 1] + node * 32 + lane];
+          const unsigned long long nm = warp_max(cv);
+          if (lane == 0) tree[tl.off[l] + node] = nm;
+          __syncwarp();
+          child = node;
+        }
+        if (lane == 0) {
+          vis[x] = 1;
+          order[ns] = x;
+          ++ns;
+          alpha += (long long)deg[x] - 2 * (long long)r[x];
+          if (ns < n && alpha < s_lam) {
+            s_lam = alpha;
+            best_alpha = alpha;
+            best_len = ns;
+          }
+          s_x = x;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_done) break;
+    const int x = s_x;
+    const long long lam = s_lam;
+    const long long rb = rp[x], re = rp[x + 1];
+    for (long long e = rb + tid; e < re; e += blockDim.x) {
+      const int y = col[e];
+      if (vis[y]) continue;
+      const long long c = (long long)w[e];
+      const long long r0 = (long long)r[y];
+      const long long r1 = r0 + c;
+      r[y] = (WT)r1;
+      if (r0 < lam && lam <= r1) {
+        if (!uf_union(parent, x, y)) uf_fail = true;
+        ++my_marks;
+        if (marks_out) {
+          const unsigned long long k = atomicAdd(&s_nmarks, 1ull);
+          if ((long long)k < marks_cap) {
+            marks_out[2 * k] = x;
+            marks_out[2 * k + 1] = y;
+          }
+        }
+      }
+      const unsigned long long key = (unsigned long long)((r1 < lam ? r1 : lam) + 1);
+      long long idx = y;
+      for (int l = 0; l < tl.levels; ++l) {
+        volatile unsigned long long* node = tree + tl.off[l] + idx;
+        if (*node >= key) break;
+        atomicMax((unsigned long long*)node, key);
+        idx >>= 5;
+      }
+    }
+    __syncthreads();
+  }
+  if (uf_fail) set_error(st, ERR_INTERNAL);
+  my_marks = warp_sum(my_marks);
+  if (lane == 0 && my_marks) atomicAdd(&st->marks_cf, my_marks);
+  if (tid == 0) {
+    st->cf_nscanned = ns;
+    if (best_alpha >= 0) {  // below the bound this pass started from
+      st->cf_val = (unsigned long long)best_alpha;
+      st->cf_pass = -1;
+      st->cf_len = best_len;
+      atomicMin(&st->lambda, (unsigned long long)best_alpha);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) st->cf_nmarks = (long long)(*(volatile unsigned long long*)&st->marks_cf);
+}
+
+}  // namespace
+
+template <typename WT>
+cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT* w,
+                             const WT* deg, int* owner, int* parent, int* visit_log,
+                             unsigned long long* pass_best, int* pass_len, int* pass_counter,
+                             PassConfig pc, DevState* st, cudaStream_t s, int* launches) {
+  const int nsum = pc.table >> 5;
+  const size_t per_warp = (size_t)pc.table * (sizeof(int) + sizeof(WT) + 8) + (size_t)nsum * 8;
+  const size_t smem = per_warp * pc.warps_per_block;
+  static size_t attr[2] = {0, 0};
+  const int ai = sizeof(WT) == 8 ? 1 : 0;
+  if (smem > attr[ai]) {
+    cudaFuncSetAttribute(cf_passes_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)std::max<size_t>(smem, 48 * 1024));
+    attr[ai] = std::max<size_t>(smem, 48 * 1024);
+  }
+  cudaMemsetAsync(pass_counter, 0, sizeof(int), s);
+  const int blocks = std::max(1, std::min(pc.passes / pc.warps_per_block + 1,
+                                          num_sms_cf() * 8));
+  cf_passes_kernel<WT><<<blocks, pc.warps_per_block * 32, smem, s>>>(
+      n, rp, col, w, deg, owner, parent, visit_log, pass_best, pass_len, pc.passes, pc.table,
+      pc.seed, pass_counter, st);
+  cf_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, pc.passes, st);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+size_t capforest_pass_smem(int table, int warps_per_block, size_t wt_size) {
+  return ((size_t)table * (sizeof(int) + wt_size + 8) + (size_t)(table >> 5) * 8) *
+         (size_t)warps_per_block;
+}
+
+long long seq_tree_words(int n) {
+  TreeLayout t = tree_layout(n);
+  return t.off[t.levels - 1] + t.size[t.levels - 1];
+}
+
+size_t seq_smem_bytes(int n, size_t wt_size) {
+  return (size_t)seq_tree_words(n) * 8 + (size_t)n * wt_size + (size_t)n + 16;
+}
+
+template <typename WT>
+cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const WT* w,
+                                 const WT* deg, int start, int* parent, WT* r,
+                                 uint8_t* visited, unsigned long long* tree, int* order,
+                                 int* marks_out, long long marks_cap, DevState* st,
+                                 cudaStream_t s, int* launches) {
+  const size_t need = seq_smem_bytes(n, sizeof(WT));
+  const size_t limit = 200 * 1024;
+  const int use_smem = need <= limit ? 1 : 0;
+  static bool attr[2] = {false, false};
+  const int ai = sizeof(WT) == 8 ? 1 : 0;
+  if (!attr[ai]) {
+    cudaFuncSetAttribute(cf_seq_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)limit);
+    attr[ai] = true;
+  }
+  cf_seq_kernel<WT><<<1, 512, use_smem ? need : 0, s>>>(n, rp, col, w, deg, start, parent, r,
+                                                       visited, tree, order, marks_out,
+                                                       marks_cap, use_smem, st);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+#define MC_CF_INST(WT)                                                                        \
+  template cudaError_t capforest_passes<WT>(int, const int64_t*, const int*, const WT*,       \
+                                            const WT*, int*, int*, int*, unsigned long long*, \
+                                            int*, int*, PassConfig, DevState*, cudaStream_t,  \
+                                            int*);                                            \
+  template cudaError_t capforest_sequential<WT>(int, const int64_t*, const int*, const WT*,   \
+                                                const WT*, int, int*, WT*, uint8_t*,          \
+                                                unsigned long long*, int*, int*, long long,   \
+                                                DevState*, cudaStream_t, int*);
+MC_CF_INST(int32_t)
+MC_CF_INST(int64_t)
+
+}  // namespace mc

@@ -1,0 +1,853 @@
+// capi.cu -- C ABI and host driver of the contraction rounds (Algorithm 2).
+//
+// One graph object owns all device memory of a solve, allocated once at
+// creation (sizes only shrink across rounds): the canonical input CSR, two
+// ping-pong CSR buffers for the contracted graphs, sort buffers and the
+// per-vertex arrays of the round kernels.  A round is a fixed sequence of
+// kernels on the graph's stream with a few small device->host reads of the
+// DevState block (bound, mark counts, new sizes) between phases.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mincut.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace mc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return status;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(MINCUT_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,     \
+                  cudaGetErrorString(e_));                                         \
+  } while (0)
+
+int bits_for(long long x) {  // bits to hold values in [0, x)
+  int b = 1;
+  while (b < 62 && (1ll << b) < x) ++b;
+  return b;
+}
+
+__global__ void iota_kernel(int* a, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+__global__ void widen32_kernel(const int32_t* __restrict__ in, int64_t* __restrict__ out, long long M) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (int64_t)in[i];
+}
+// Sum and minimum of the raw input weights; row_ptr monotonicity.
+__global__ void input_stats_kernel(const int64_t* __restrict__ rp, int n, const int32_t* __restrict__ w,
+                                   long long M, unsigned long long* out /* [sum, neg, badrp] */) {
+  unsigned long long s = 0, neg = 0, bad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int32_t x = w[i];
+    if (x < 0) neg = 1; else s += (unsigned long long)x;
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (rp[i] > rp[i + 1] || rp[i] < 0) bad = 1;
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) {
+    if (s) atomicAdd(&out[0], s);
+    if (neg) atomicOr(&out[1], 1ull);
+  }
+  if (bad) atomicOr(&out[2], 1ull);
+}
+__global__ void reset_round_kernel(DevState* st) {
+  st->marks_pr = 0;
+  st->marks_cf = 0;
+  st->emit_count = 0;
+  st->deg_val = ~0ull;
+  st->deg_arg = -1;
+  st->lp_val = ~0ull;
+  st->lp_label = -1;
+  st->cf_val = ~0ull;
+  st->cf_pass = -1;
+  st->cf_len = 0;
+  st->cf_nscanned = 0;
+  st->cf_nmarks = 0;
+  st->claimed = 0;
+}
+
+}  // namespace
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+struct mincut_graph {
+  cudaStream_t stream = nullptr;
+  mincut_allocator alloc{};
+  bool user_alloc = false;
+  std::vector<Alloc> allocs;
+  bool wt64 = false;
+  int sms = 148;
+  // canonical input
+  int n0 = 0;
+  long long M0 = 0, Mraw = 0;
+  int64_t* rp0 = nullptr;
+  int* col0 = nullptr;
+  void* w0 = nullptr;
+  // current state (cur < 0: the input)
+  int n = 0;
+  long long M = 0;
+  int cur = -1;
+  int64_t* rp[2]{};
+  int* col[2]{};
+  void* w[2]{};
+  // scratch
+  u64* keys[2]{};
+  void* vals[2]{};
+  int* tile_row = nullptr;
+  void* deg = nullptr;
+  unsigned long long* blk = nullptr;
+  int *parent = nullptr, *L = nullptr, *flags = nullptr, *rank = nullptr, *part = nullptr,
+      *uid = nullptr, *owner = nullptr, *gmin = nullptr, *map0 = nullptr;
+  uint8_t *side0 = nullptr, *cur_side = nullptr;
+  u64* bitmap_dev = nullptr;
+  // label propagation (allocated on first use)
+  int* lab[2]{};
+  long long* lp_cut = nullptr;
+  int *lp_size = nullptr, *long_rows = nullptr, *long_count = nullptr, *pool_lab = nullptr;
+  long long* pool_sc = nullptr;
+  long long pool_slots = 0;
+  unsigned long long* pool_cursor = nullptr;
+  // CAPFOREST
+  int max_passes = 0, max_table = 0;
+  int* visit_log = nullptr;
+  unsigned long long* pass_best = nullptr;
+  int *pass_len = nullptr, *pass_counter = nullptr;
+  void* seq_r = nullptr;
+  uint8_t* seq_vis = nullptr;
+  unsigned long long* seq_tree = nullptr;
+  int* seq_order = nullptr;
+  // sort
+  SortScratch sort{};
+  // state
+  DevState* st = nullptr;
+  DevState* hst = nullptr;  // pinned mirror
+  int* m2_dev = nullptr;
+  int launches = 0;
+  long long spin_limit = 1ll << 22;
+
+  const int64_t* crp() const { return cur < 0 ? rp0 : rp[cur]; }
+  const int* ccol() const { return cur < 0 ? col0 : col[cur]; }
+  const void* cw() const { return cur < 0 ? w0 : w[cur]; }
+};
+
+namespace {
+
+void* dev_alloc(mincut_graph* g, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  bytes = (bytes + 255) / 256 * 256;
+  void* p = nullptr;
+  if (g->user_alloc) {
+    p = g->alloc.alloc(bytes, (void*)g->stream, g->alloc.ctx);
+  } else if (cudaMallocAsync(&p, bytes, g->stream) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) g->allocs.push_back({p, bytes});
+  return p;
+}
+
+void dev_free(mincut_graph* g, void* p) {
+  for (size_t i = 0; i < g->allocs.size(); ++i)
+    if (g->allocs[i].p == p) {
+      if (g->user_alloc) g->alloc.free(p, g->allocs[i].bytes, (void*)g->stream, g->alloc.ctx);
+      else cudaFreeAsync(p, g->stream);
+      g->allocs.erase(g->allocs.begin() + (long)i);
+      return;
+    }
+}
+
+template <typename T>
+bool galloc(mincut_graph* g, T** out, long long count) {
+  *out = static_cast<T*>(dev_alloc(g, (size_t)std::max<long long>(count, 1) * sizeof(T)));
+  return *out != nullptr;
+}
+
+void free_all(mincut_graph* g) {
+  for (auto& a : g->allocs) {
+    if (g->user_alloc) g->alloc.free(a.p, a.bytes, (void*)g->stream, g->alloc.ctx);
+    else cudaFreeAsync(a.p, g->stream);
+  }
+  g->allocs.clear();
+  if (g->hst) cudaFreeHost(g->hst);
+  g->hst = nullptr;
+}
+
+int sync_state(mincut_graph* g) {
+  CK(cudaMemcpyAsync(g->hst, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+  CK(cudaStreamSynchronize(g->stream));
+  const unsigned e = g->hst->error;
+  if (e & ERR_TIMEOUT) return fail(MINCUT_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
+  if (e & ERR_INPUT) return fail(MINCUT_ERR_INVALID, "index out of range or negative weight");
+  if (e & ERR_ASYM) return fail(MINCUT_ERR_INVALID, "input CSR is not symmetric");
+  if (e & ERR_OVERFLOW) return fail(MINCUT_ERR_OVERFLOW, "a device capacity was exceeded");
+  if (e & ERR_INTERNAL) return fail(MINCUT_ERR_INTERNAL, "internal consistency check failed");
+  return MINCUT_OK;
+}
+
+int set_lambda(mincut_graph* g, long long lam) {
+  unsigned long long v = (unsigned long long)lam;
+  CK(cudaMemcpyAsync(&g->st->lambda, &v, sizeof(v), cudaMemcpyHostToDevice, g->stream));
+  CK(cudaStreamSynchronize(g->stream));
+  return MINCUT_OK;
+}
+
+int ensure_lp(mincut_graph* g) {
+  if (g->lab[0]) return MINCUT_OK;
+  const size_t wsz = g->wt64 ? 8 : 4;
+  (void)wsz;
+  g->pool_slots = 2 * std::max<long long>(g->M0, 1);
+  if (!galloc(g, &g->lab[0], g->n0) || !galloc(g, &g->lab[1], g->n0) ||
+      !galloc(g, &g->lp_cut, g->n0) || !galloc(g, &g->lp_size, g->n0) ||
+      !galloc(g, &g->long_rows, g->n0) || !galloc(g, &g->long_count, 1) ||
+      !galloc(g, &g->pool_lab, g->pool_slots) || !galloc(g, &g->pool_sc, g->pool_slots) ||
+      !galloc(g, &g->pool_cursor, 1))
+    return fail(MINCUT_ERR_OOM, "label propagation buffers");
+  return MINCUT_OK;
+}
+
+// Contraction of the current graph by the union-find state in g->parent:
+// relabel, emit, sort, build; the result becomes the current graph.
+template <typename WT>
+int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compose) {
+  cudaStream_t s = g->stream;
+  const int n = g->n;
+  const long long M = g->M;
+  CK(uf_relabel(g->parent, g->L, g->flags, g->rank, g->part, n, g->st, s, &g->launches));
+  int rc = sync_state(g);
+  if (rc) return rc;
+  const int n2 = g->hst->n_next;
+  const int vbits = bits_for(n2);
+  CK(cudaMemsetAsync(&g->st->emit_count, 0, sizeof(long long), s));
+  CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
+                    g->keys[0], (WT*)g->vals[0], g->st, 0, s, &g->launches));
+  rc = sync_state(g);
+  if (rc) return rc;
+  const long long N = g->hst->emit_count;
+  bool alt = false;
+  CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
+                          2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
+  const int nxt = g->cur == 0 ? 1 : 0;
+  CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
+                   vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], g->st,
+                   g->m2_dev, s, &g->launches));
+  if (compose) CK(compose_map(g->map0, g->L, g->n0, s, &g->launches));
+  int m2 = 0;
+  CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  rc = sync_state(g);
+  if (rc) return rc;
+  g->cur = nxt;
+  g->n = n2;
+  g->M = m2;
+  *n2_out = n2;
+  *m2_out = m2;
+  return MINCUT_OK;
+}
+
+struct RoundCfg {
+  int lp_iters, lp_min_n;
+  bool lp_now;
+  uint32_t pr_mask;
+  long long pr_budget;
+  int capforest;  // 0 none, 1 concurrent (+ sequential fallback), 2 sequential from cf_start
+  int cf_start;
+  int passes, table;
+  unsigned long long seed;
+  uint8_t* pr_flags_host;
+  int* cf_order_host;
+  int* cf_marks_host;
+  long long cf_marks_cap;
+};
+
+struct RoundOut {
+  bool stopped = false;
+  bool seq_pass = false;
+  long long lambda = kInf;
+  long long marks_pr = 0, marks_cf = 0;
+  long long cf_nscanned = 0, cf_nmarks = 0;
+  int src = 0;  // which bound source set lambda this round
+};
+
+// Marking phase of one round on the current graph: degree bound, LP bound,
+// PR marks and CAPFOREST marks (all hooked into g->parent).  Updates g->side0
+// when lambda improves below lambda_before.
+template <typename WT>
+int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, RoundOut* o) {
+  cudaStream_t s = g->stream;
+  const int n = g->n;
+  const long long M = g->M;
+  const int64_t* rp = g->crp();
+  const int* col = g->ccol();
+  const WT* w = (const WT*)g->cw();
+  WT* deg = (WT*)g->deg;
+  reset_round_kernel<<<1, 1, 0, s>>>(g->st);
+  ++g->launches;
+  if (n >= 2) CK(degrees_min<WT>(rp, w, n, deg, g->blk, g->st, s, &g->launches));
+  int rc = sync_state(g);
+  if (rc) return rc;
+  long long lam = (long long)g->hst->lambda;
+  if (lam < lambda_before) {
+    CK(side_from_vertex(g->side0, g->map0, g->n0, g->hst->deg_arg, s, &g->launches));
+    o->src = 1;
+    lambda_before = lam;
+  }
+  o->lambda = lam;
+  if (n <= 2 || lam == 0) {
+    o->stopped = true;
+    return MINCUT_OK;
+  }
+  CK(tile_rows(rp, n, M, g->tile_row, s, &g->launches));
+  const int* lab_final = nullptr;
+  if (c.lp_now && c.lp_iters > 0 && n >= c.lp_min_n) {
+    rc = ensure_lp(g);
+    if (rc) return rc;
+    iota_kernel<<<std::min((n + 255) / 256, g->sms * 8), 256, 0, s>>>(g->lab[0], n);
+    ++g->launches;
+    for (int it = 0; it < c.lp_iters; ++it)
+      CK(lp_sweep<WT>(n, rp, col, w, g->lab[it & 1], g->lab[(it + 1) & 1], it, g->long_rows,
+                      g->long_count, g->pool_lab, g->pool_sc, g->pool_slots, g->pool_cursor,
+                      g->st, s, &g->launches));
+    lab_final = g->lab[c.lp_iters & 1];
+    CK(lp_bound<WT>(n, M, rp, col, w, lab_final, g->tile_row, g->lp_cut, g->lp_size, g->blk,
+                    g->st, s, &g->launches));
+  }
+  CK(uf_init(g->parent, n, s, &g->launches));
+  uint8_t* flags_dev = c.pr_flags_host ? reinterpret_cast<uint8_t*>(g->vals[1]) : nullptr;
+  if (c.pr_mask)
+    CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, c.pr_mask, c.pr_budget, g->parent,
+                    flags_dev, g->st, s, &g->launches));
+  if (c.capforest == 1 && n > 2) {
+    CK(cudaMemsetAsync(g->owner, 0, (size_t)n * sizeof(int), s));
+    PassConfig pc;
+    pc.table = c.table;
+    pc.warps_per_block = 4;
+    pc.passes = std::min(c.passes, g->max_passes);
+    pc.seed = c.seed;
+    CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log,
+                            g->pass_best, g->pass_len, g->pass_counter, pc, g->st, s,
+                            &g->launches));
+  }
+  rc = sync_state(g);
+  if (rc) return rc;
+  if (flags_dev && M > 0)
+    CK(cudaMemcpyAsync(c.pr_flags_host, flags_dev, (size_t)M, cudaMemcpyDeviceToHost, s));
+  long long marks = (long long)(g->hst->marks_pr + g->hst->marks_cf);
+  o->marks_pr = (long long)g->hst->marks_pr;
+  bool need_seq = c.capforest == 2 || (c.capforest == 1 && marks == 0);
+  // the sequential pass is only useful while the bound is positive
+  if (need_seq && (long long)g->hst->lambda > 0) {
+    const long long cap = c.cf_marks_host ? std::min(c.cf_marks_cap, M / 2 + 1) : 0;
+    int* marks_dev = c.cf_marks_host ? reinterpret_cast<int*>(g->keys[1]) : nullptr;
+    const int start = (c.capforest == 2) ? c.cf_start : 0;
+    CK(capforest_sequential<WT>(n, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_vis,
+                                g->seq_tree, g->seq_order, marks_dev, cap, g->st, s,
+                                &g->launches));
+    rc = sync_state(g);
+    if (rc) return rc;
+    o->seq_pass = true;
+    o->cf_nscanned = g->hst->cf_nscanned;
+    o->cf_nmarks = (long long)g->hst->marks_cf;
+    if (c.cf_order_host && o->cf_nscanned > 0)
+      CK(cudaMemcpyAsync(c.cf_order_host, g->seq_order, (size_t)o->cf_nscanned * sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
+    if (marks_dev) {
+      const long long k = std::min<long long>(o->cf_nmarks, cap);
+      if (k > 0)
+        CK(cudaMemcpyAsync(c.cf_marks_host, marks_dev, (size_t)k * 2 * sizeof(int),
+                           cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+  }
+  o->marks_cf = (long long)g->hst->marks_cf;
+  lam = (long long)g->hst->lambda;
+  if (lam < lambda_before) {
+    const DevState& h = *g->hst;
+    if (lab_final && h.lp_val == (unsigned long long)lam) {
+      CK(side_from_label(g->side0, g->map0, g->n0, lab_final, h.lp_label, s, &g->launches));
+      o->src = 2;
+    } else if (h.cf_val == (unsigned long long)lam) {
+      const int* list = h.cf_pass >= 0 ? g->visit_log + (long long)h.cf_pass * c.table
+                                       : g->seq_order;
+      CK(side_from_list(g->side0, g->map0, g->n0, g->cur_side, n, list, h.cf_len, s,
+                        &g->launches));
+      o->src = 3;
+    } else {
+      return fail(MINCUT_ERR_INTERNAL, "bound improved without a witness");
+    }
+  }
+  o->lambda = lam;
+  return MINCUT_OK;
+}
+
+template <typename WT>
+int solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_value,
+               uint64_t* side_bitmap, mincut_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = g->stream;
+  g->launches = 0;
+  g->cur = -1;
+  g->n = g->n0;
+  g->M = g->M0;
+  if (op.spin_limit > 0) g->spin_limit = op.spin_limit;
+  CK(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
+  int rc = set_lambda(g, kInf);
+  if (rc) return rc;
+  iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
+  ++g->launches;
+  long long lambda = kInf;
+  mincut_stats stl{};
+  stl.n_input = g->n0;
+  stl.m_input = g->M0 / 2;
+  RoundCfg c{};
+  c.lp_iters = op.lp_iters;
+  c.lp_min_n = op.lp_min_n;
+  c.pr_mask = op.pr_mask;
+  c.pr_budget = op.pr_budget;
+  c.capforest = op.deterministic ? 2 : 1;
+  c.cf_start = 0;
+  c.table = op.pass_table > 0 ? op.pass_table : g->max_table;
+  c.table = std::min(c.table, g->max_table);
+  c.seed = op.seed;
+  for (int round = 0;; ++round) {
+    if (op.max_rounds > 0 && round >= op.max_rounds) break;
+    c.lp_now = op.lp_every_round || round == 0;
+    c.passes = op.passes > 0 ? op.passes : std::max(32, std::min(g->max_passes, g->n / 4));
+    c.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
+    RoundOut o;
+    rc = mark_round<WT>(g, c, lambda, &o);
+    if (rc) return rc;
+    if (o.src) stl.lambda_source = o.src;
+    const bool improved = o.lambda < lambda;
+    lambda = std::min(lambda, o.lambda);
+    if (o.stopped) break;
+    stl.rounds++;
+    stl.entries_processed += g->M;
+    stl.marks_pr += o.marks_pr;
+    stl.marks_cf += o.marks_cf;
+    if (o.seq_pass) stl.seq_passes++;
+    if (lambda == 0) break;
+    if (o.marks_pr + o.marks_cf == 0) {
+      if (!improved) return fail(MINCUT_ERR_INTERNAL, "round made no progress");
+      continue;
+    }
+    int n2 = 0;
+    long long m2 = 0;
+    rc = contract_current<WT>(g, &n2, &m2, true);
+    if (rc) return rc;
+    if (n2 <= 1) break;
+  }
+  *cut_value = lambda;
+  if (side_bitmap) {
+    cudaPointerAttributes attr{};
+    bool dev = cudaPointerGetAttributes(&attr, side_bitmap) == cudaSuccess &&
+               (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    u64* target = dev ? reinterpret_cast<u64*>(side_bitmap) : g->bitmap_dev;
+    CK(side_to_bitmap(g->side0, g->n0, target, s, &g->launches));
+    if (!dev)
+      CK(cudaMemcpyAsync(side_bitmap, g->bitmap_dev, (size_t)((g->n0 + 63) / 64) * 8,
+                         cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  stl.kernel_launches = g->launches;
+  stl.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = stl;
+  return MINCUT_OK;
+}
+
+template <typename WT>
+int contract_round_impl(mincut_graph* g, const mincut_round_options* ro,
+                        mincut_round_result* res) {
+  cudaStream_t s = g->stream;
+  memset(res, 0, sizeof(*res));
+  res->n_in = g->n;
+  res->m_in = g->M;
+  res->lambda_out = ro->lambda_in;
+  CK(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
+  int rc = set_lambda(g, ro->lambda_in);
+  if (rc) return rc;
+  const int n = g->n;
+  if (ro->groups || ro->pair_u) {
+    CK(uf_init(g->parent, n, s, &g->launches));
+    CK(tile_rows(g->crp(), n, g->M, g->tile_row, s, &g->launches));
+    if (ro->groups) {
+      int* gd = g->flags;  // n ints; consumed before uf_relabel reuses them
+      CK(cudaMemcpyAsync(gd, ro->groups, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(uf_from_groups(g->parent, gd, g->gmin, n, g->st, s, &g->launches));
+    } else {
+      if (ro->npairs < 0 || ro->npairs > g->Mraw) return fail(MINCUT_ERR_INVALID, "npairs");
+      int* pu = reinterpret_cast<int*>(g->keys[1]);
+      int* pv = pu + ro->npairs;
+      if (ro->npairs > 0) {
+        CK(cudaMemcpyAsync(pu, ro->pair_u, (size_t)ro->npairs * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(pv, ro->pair_v, (size_t)ro->npairs * sizeof(int), cudaMemcpyHostToDevice, s));
+      }
+      CK(uf_hook_pairs(g->parent, pu, pv, ro->npairs, n, g->st, s, &g->launches));
+    }
+    rc = sync_state(g);
+    if (rc) return rc;
+    int n2;
+    long long m2;
+    rc = contract_current<WT>(g, &n2, &m2, false);
+    if (rc) return rc;
+    res->n_out = n2;
+    res->m_out = m2;
+    return MINCUT_OK;
+  }
+  RoundCfg c{};
+  c.lp_iters = ro->lp_iters;
+  c.lp_min_n = ro->lp_min_n;
+  c.lp_now = true;
+  c.pr_mask = ro->pr_mask;
+  c.pr_budget = ro->pr_budget;
+  c.capforest = ro->capforest;
+  c.cf_start = ro->cf_start;
+  if (c.capforest == 2 && (c.cf_start < 0 || c.cf_start >= n))
+    return fail(MINCUT_ERR_INVALID, "cf_start out of range");
+  c.table = ro->pass_table > 0 ? std::min(ro->pass_table, g->max_table) : g->max_table;
+  c.passes = ro->passes > 0 ? ro->passes : std::max(32, std::min(g->max_passes, n / 4));
+  c.seed = ro->seed;
+  c.pr_flags_host = ro->pr_flags_out;
+  c.cf_order_host = ro->cf_order_out;
+  c.cf_marks_host = ro->cf_marks_out;
+  c.cf_marks_cap = ro->cf_marks_cap;
+  CK(cudaMemsetAsync(g->side0, 0, (size_t)g->n0, s));
+  iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
+  RoundOut o;
+  rc = mark_round<WT>(g, c, ro->lambda_in, &o);
+  if (rc) return rc;
+  res->lambda_out = o.lambda;
+  res->marks_pr = o.marks_pr;
+  res->marks_cf = o.marks_cf;
+  res->seq_pass = o.seq_pass;
+  res->cf_nscanned = o.cf_nscanned;
+  res->cf_nmarks = o.cf_nmarks;
+  if (o.stopped) {
+    res->stopped = 1;
+    res->n_out = g->n;
+    res->m_out = g->M;
+    return MINCUT_OK;
+  }
+  int n2;
+  long long m2;
+  rc = contract_current<WT>(g, &n2, &m2, false);
+  if (rc) return rc;
+  res->n_out = n2;
+  res->m_out = m2;
+  return MINCUT_OK;
+}
+
+// Canonicalise the raw input already copied to rp[1]/col[1]/w[1] into
+// rp0/col0/w0 (identity labels: sort, sum duplicates, drop self-loops).
+template <typename WT>
+int canonicalize_input(mincut_graph* g, int n, long long Mraw, bool validate) {
+  cudaStream_t s = g->stream;
+  CK(tile_rows(g->rp[1], n, Mraw, g->tile_row, s, &g->launches));
+  const int vbits = bits_for(n);
+  CK(emit_pairs<WT>(n, Mraw, g->rp[1], g->col[1], (const WT*)g->w[1], nullptr, vbits,
+                    g->tile_row, g->keys[0], (WT*)g->vals[0], g->st, 1, s, &g->launches));
+  int rc = sync_state(g);
+  if (rc) return rc;
+  const long long N = g->hst->emit_count;
+  bool alt = false;
+  CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
+                          2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
+  CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
+                   vbits, n, g->uid, g->part, g->rp[0], g->col[0], (WT*)g->w[0], g->st,
+                   g->m2_dev, s, &g->launches));
+  int m2 = 0;
+  CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  rc = sync_state(g);
+  if (rc) return rc;
+  g->M0 = m2;
+  if (validate && m2 > 0) {
+    CK(tile_rows(g->rp[0], n, m2, g->tile_row, s, &g->launches));
+    CK(check_symmetric<WT>(n, m2, g->rp[0], g->col[0], (const WT*)g->w[0], g->tile_row, g->st, s,
+                           &g->launches));
+    rc = sync_state(g);
+    if (rc) return rc;
+  }
+  if (!galloc(g, &g->rp0, n + 1) || !galloc(g, &g->col0, m2) ||
+      !(g->w0 = dev_alloc(g, (size_t)std::max(m2, 1) * sizeof(WT))))
+    return fail(MINCUT_ERR_OOM, "canonical input");
+  CK(cudaMemcpyAsync(g->rp0, g->rp[0], (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  if (m2 > 0) {
+    CK(cudaMemcpyAsync(g->col0, g->col[0], (size_t)m2 * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(g->w0, g->w[0], (size_t)m2 * sizeof(WT), cudaMemcpyDeviceToDevice, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return MINCUT_OK;
+}
+
+int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                uint32_t flags, void* stream, const mincut_allocator* alloc, mincut_graph** out) {
+  if (!out) return fail(MINCUT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!row_ptr || (!col && n64 > 0) || (!w && n64 > 0))
+    return fail(MINCUT_ERR_INVALID, "NULL input array");
+  if (n64 < 2) return fail(MINCUT_ERR_INVALID, "n = %lld: a cut needs n >= 2", (long long)n64);
+  if (n64 > 0x7ffffffell) return fail(MINCUT_ERR_OVERFLOW, "n = %lld exceeds 2^31-2", (long long)n64);
+  if (alloc && (!alloc->alloc || !alloc->free)) return fail(MINCUT_ERR_INVALID, "allocator");
+  const int n = (int)n64;
+  const bool dev_in = (flags & MINCUT_DEVICE_PTRS) != 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t rp_end[2] = {0, 0};
+  if (dev_in) {
+    CK(cudaMemcpyAsync(&rp_end[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&rp_end[1], row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    rp_end[0] = row_ptr[0];
+    rp_end[1] = row_ptr[n];
+  }
+  const long long Mraw = rp_end[1];
+  if (rp_end[0] != 0 || Mraw < 0) return fail(MINCUT_ERR_INVALID, "row_ptr[0] must be 0, row_ptr[n] >= 0");
+  if (Mraw > 0x7fffffffll) return fail(MINCUT_ERR_OVERFLOW, "M = %lld exceeds 2^31-1", Mraw);
+
+  mincut_graph* g = new mincut_graph();
+  g->stream = s;
+  if (alloc) { g->alloc = *alloc; g->user_alloc = true; }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+  auto bail = [&](int rc) {
+    cudaStreamSynchronize(s);
+    free_all(g);
+    delete g;
+    return rc;
+  };
+  if (cudaMallocHost(&g->hst, sizeof(DevState)) != cudaSuccess)
+    return bail(fail(MINCUT_ERR_OOM, "pinned state"));
+  if (!galloc(g, &g->st, 1) || !galloc(g, &g->m2_dev, 1)) return bail(fail(MINCUT_ERR_OOM, "state"));
+  if (cudaMemsetAsync(g->st, 0, sizeof(DevState), s) != cudaSuccess)
+    return bail(fail(MINCUT_ERR_CUDA, "memset state"));
+  // raw copy of row_ptr and the weight statistics decide the weight type
+  int64_t* rp_raw = nullptr;
+  int32_t* w_raw = nullptr;
+  int* col_raw = nullptr;
+  if (!galloc(g, &rp_raw, n + 1) || !galloc(g, &w_raw, Mraw) || !galloc(g, &col_raw, Mraw))
+    return bail(fail(MINCUT_ERR_OOM, "raw input"));
+  const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(rp_raw, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind, s) != cudaSuccess ||
+      (Mraw > 0 && cudaMemcpyAsync(w_raw, w, (size_t)Mraw * sizeof(int32_t), kind, s) != cudaSuccess) ||
+      (Mraw > 0 && cudaMemcpyAsync(col_raw, col, (size_t)Mraw * sizeof(int32_t), kind, s) != cudaSuccess))
+    return bail(fail(MINCUT_ERR_CUDA, "copy input: %s", cudaGetErrorString(cudaGetLastError())));
+  unsigned long long* wst = nullptr;
+  if (!galloc(g, &wst, 4)) return bail(fail(MINCUT_ERR_OOM, "stats"));
+  cudaMemsetAsync(wst, 0, 4 * sizeof(unsigned long long), s);
+  input_stats_kernel<<<std::max(1, std::min(g->sms * 8, (int)((std::max<long long>(Mraw, n) + 255) / 256))), 256, 0, s>>>(
+      rp_raw, n, w_raw, Mraw, wst);
+  unsigned long long hws[4] = {0, 0, 0, 0};
+  cudaMemcpyAsync(hws, wst, sizeof(hws), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess)
+    return bail(fail(MINCUT_ERR_CUDA, "input statistics: %s", cudaGetErrorString(cudaGetLastError())));
+  if (hws[2]) return bail(fail(MINCUT_ERR_INVALID, "row_ptr is not non-decreasing"));
+  if (hws[1]) return bail(fail(MINCUT_ERR_INVALID, "negative weight"));
+  g->wt64 = hws[0] > 0x7fffffffull;
+  const size_t wsz = g->wt64 ? 8 : 4;
+  g->n0 = n;
+  g->Mraw = Mraw;
+  const long long Mb = std::max<long long>(Mraw, 1);
+  // buffers
+  bool ok = true;
+  for (int i = 0; i < 2; ++i) {
+    ok = ok && galloc(g, &g->rp[i], n + 1) && galloc(g, &g->col[i], Mb) &&
+         (g->w[i] = dev_alloc(g, (size_t)Mb * wsz)) && galloc(g, &g->keys[i], Mb) &&
+         (g->vals[i] = dev_alloc(g, (size_t)Mb * wsz));
+  }
+  const long long ntiles = (Mb + kEntryTile - 1) / kEntryTile + 2;
+  const long long scan_parts = (std::max<long long>(Mb, n) + 4095) / 4096 + 2;
+  g->max_table = 1024;
+  g->max_passes = std::max(256, g->sms * 12 * 4);
+  ok = ok && galloc(g, &g->tile_row, ntiles) && (g->deg = dev_alloc(g, (size_t)n * wsz)) &&
+       galloc(g, &g->blk, 2 * 1024) && galloc(g, &g->parent, n) && galloc(g, &g->L, n) &&
+       galloc(g, &g->flags, n) && galloc(g, &g->rank, n) && galloc(g, &g->part, scan_parts) &&
+       galloc(g, &g->uid, Mb) && galloc(g, &g->owner, n) && galloc(g, &g->gmin, n) &&
+       galloc(g, &g->map0, n) && galloc(g, &g->side0, n) && galloc(g, &g->cur_side, n) &&
+       galloc(g, &g->bitmap_dev, (n + 63) / 64) &&
+       galloc(g, &g->visit_log, (long long)g->max_passes * g->max_table) &&
+       galloc(g, &g->pass_best, g->max_passes) && galloc(g, &g->pass_len, g->max_passes) &&
+       galloc(g, &g->pass_counter, 1) && (g->seq_r = dev_alloc(g, (size_t)n * wsz)) &&
+       galloc(g, &g->seq_vis, n) && galloc(g, &g->seq_tree, seq_tree_words(n)) &&
+       galloc(g, &g->seq_order, n) && galloc(g, &g->sort.hist, 8 * 256) &&
+       galloc(g, &g->sort.goff, 8 * 256) &&
+       galloc(g, &g->sort.lookback, sort_lookback_words(Mb));
+  if (!ok) return bail(fail(MINCUT_ERR_OOM, "device buffers for n=%d M=%lld", n, Mraw));
+  g->sort.lookback_words = sort_lookback_words(Mb);
+  // raw input into rp[1]/col[1]/w[1]
+  if (cudaMemcpyAsync(g->rp[1], rp_raw, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      (Mraw > 0 && cudaMemcpyAsync(g->col[1], col_raw, (size_t)Mraw * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess))
+    return bail(fail(MINCUT_ERR_CUDA, "stage input"));
+  if (Mraw > 0) {
+    if (g->wt64) {
+      widen32_kernel<<<std::max(1, std::min(g->sms * 8, (int)((Mraw + 255) / 256))), 256, 0, s>>>(
+          w_raw, (int64_t*)g->w[1], Mraw);
+    } else if (cudaMemcpyAsync(g->w[1], w_raw, (size_t)Mraw * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      return bail(fail(MINCUT_ERR_CUDA, "stage weights"));
+    }
+  }
+  cudaStreamSynchronize(s);
+  dev_free(g, rp_raw);
+  dev_free(g, w_raw);
+  dev_free(g, col_raw);
+  dev_free(g, wst);
+  const bool validate = (flags & MINCUT_SKIP_VALIDATE) == 0;
+  int rc = g->wt64 ? canonicalize_input<int64_t>(g, n, Mraw, validate)
+                   : canonicalize_input<int32_t>(g, n, Mraw, validate);
+  if (rc) return bail(rc);
+  g->cur = -1;
+  g->n = n;
+  g->M = g->M0;
+  *out = g;
+  return MINCUT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mincut_default_options(mincut_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->lp_iters = 2;
+  o->lp_min_n = 10000;
+  o->lp_every_round = 1;
+  o->pr_mask = 0xF;
+  o->pr_budget = 64;
+  o->seed = 0x5eed;
+}
+
+void mincut_default_round_options(mincut_round_options* ro) {
+  if (!ro) return;
+  memset(ro, 0, sizeof(*ro));
+  ro->lambda_in = kInf;
+  ro->lp_iters = 2;
+  ro->lp_min_n = 10000;
+  ro->pr_mask = 0xF;
+  ro->pr_budget = 64;
+  ro->capforest = 1;
+  ro->seed = 0x5eed;
+}
+
+int mincut_graph_from_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                          uint32_t flags, void* cuda_stream, const mincut_allocator* alloc,
+                          mincut_graph** out) {
+  g_last_error.clear();
+  return create_impl(n, row_ptr, col, w, flags, cuda_stream, alloc, out);
+}
+
+int mincut_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_value,
+                 uint64_t* side_bitmap, mincut_stats* stats) {
+  g_last_error.clear();
+  if (!g || !cut_value) return fail(MINCUT_ERR_INVALID, "NULL graph or cut_value");
+  mincut_options op;
+  if (opts) op = *opts; else mincut_default_options(&op);
+  if (op.pass_table != 0 && (op.pass_table < 256 || op.pass_table > 2048 ||
+                             (op.pass_table & (op.pass_table - 1))))
+    return fail(MINCUT_ERR_INVALID, "pass_table must be a power of two in [256, 2048]");
+  const int rc = g->wt64 ? solve_impl<int64_t>(g, op, cut_value, side_bitmap, stats)
+                         : solve_impl<int32_t>(g, op, cut_value, side_bitmap, stats);
+  g->cur = -1;
+  g->n = g->n0;
+  g->M = g->M0;
+  return rc;
+}
+
+int mincut_contract_round(mincut_graph* g, const mincut_round_options* ro,
+                          mincut_round_result* res) {
+  g_last_error.clear();
+  if (!g || !ro || !res) return fail(MINCUT_ERR_INVALID, "NULL argument");
+  if (ro->pass_table != 0 && (ro->pass_table < 256 || ro->pass_table > 2048 ||
+                              (ro->pass_table & (ro->pass_table - 1))))
+    return fail(MINCUT_ERR_INVALID, "pass_table must be a power of two in [256, 2048]");
+  if (ro->capforest < 0 || ro->capforest > 2) return fail(MINCUT_ERR_INVALID, "capforest mode");
+  return g->wt64 ? contract_round_impl<int64_t>(g, ro, res) : contract_round_impl<int32_t>(g, ro, res);
+}
+
+int mincut_graph_info(const mincut_graph* g, int64_t* n, int64_t* m_directed) {
+  if (!g) return fail(MINCUT_ERR_INVALID, "NULL graph");
+  if (n) *n = g->n;
+  if (m_directed) *m_directed = g->M;
+  return MINCUT_OK;
+}
+
+int mincut_graph_export_csr(const mincut_graph* g, int64_t* row_ptr, int32_t* col, int64_t* w) {
+  if (!g || !row_ptr) return fail(MINCUT_ERR_INVALID, "NULL argument");
+  mincut_graph* gg = const_cast<mincut_graph*>(g);
+  cudaStream_t s = gg->stream;
+  CK(cudaMemcpyAsync(row_ptr, g->crp(), (size_t)(g->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (g->M > 0) {
+    if (col) CK(cudaMemcpyAsync(col, g->ccol(), (size_t)g->M * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (w) {
+      if (g->wt64) {
+        CK(cudaMemcpyAsync(w, g->cw(), (size_t)g->M * 8, cudaMemcpyDeviceToHost, s));
+      } else {
+        int64_t* tmp = reinterpret_cast<int64_t*>(gg->keys[1]);
+        widen32_kernel<<<std::max(1, std::min(g->sms * 8, (int)((g->M + 255) / 256))), 256, 0, s>>>(
+            (const int32_t*)g->cw(), tmp, g->M);
+        CK(cudaMemcpyAsync(w, tmp, (size_t)g->M * 8, cudaMemcpyDeviceToHost, s));
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  return MINCUT_OK;
+}
+
+int mincut_graph_reset(mincut_graph* g) {
+  if (!g) return fail(MINCUT_ERR_INVALID, "NULL graph");
+  g->cur = -1;
+  g->n = g->n0;
+  g->M = g->M0;
+  return MINCUT_OK;
+}
+
+void mincut_graph_destroy(mincut_graph* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  free_all(g);
+  cudaStreamSynchronize(g->stream);
+  delete g;
+}
+
+const char* mincut_status_string(int status) {
+  switch (status) {
+    case MINCUT_OK: return "ok";
+    case MINCUT_ERR_INVALID: return "invalid argument or graph";
+    case MINCUT_ERR_OOM: return "device allocation failed";
+    case MINCUT_ERR_OVERFLOW: return "size or sum out of the supported range";
+    case MINCUT_ERR_DEVICE_TIMEOUT: return "bounded device wait ran out";
+    case MINCUT_ERR_CUDA: return "CUDA runtime error";
+    case MINCUT_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+const char* mincut_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

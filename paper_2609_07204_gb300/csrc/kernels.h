@@ -1,0 +1,133 @@
+// kernels.h -- host-side launchers of the device kernels (internal interface
+// between the C-ABI driver and the kernel translation units).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mc {
+
+using u64 = unsigned long long;
+
+// ------------------------------------------------------------- sort.cu
+// Onesweep LSD radix sort of N (key, value) pairs on the low `bits` bits of
+// the keys, 8 bits per pass.  Ping-pongs between (k0, v0) and (k1, v1);
+// returns in *in_alt whether the result ended in (k1, v1).  hist and goff
+// hold 8*256 unsigned, lookback sort_lookback_words(N) u64.
+struct SortScratch {
+  unsigned* hist;
+  unsigned* goff;
+  u64* lookback;
+  long long lookback_words;
+};
+long long sort_lookback_words(long long maxN);
+template <typename WT>
+cudaError_t radix_sort_pairs(u64* k0, WT* v0, u64* k1, WT* v1, int N, int bits, SortScratch sc, DevState* st, long long spin_limit,
+                             cudaStream_t s, bool* in_alt, int* launches);
+
+// Exclusive scan of int flags/counts: out[i] = sum_{j<i} in[j]; *total = sum.
+// part must hold ceil(N/4096)+1 ints.
+cudaError_t scan_exclusive_i32(const int* in, int* out, int N, int* part, int* total,
+                               cudaStream_t s, int* launches);
+
+// ------------------------------------------------------------- round.cu
+constexpr int kEntryTile = 2048;  // entries per block of the entry-parallel kernels
+
+cudaError_t tile_rows(const int64_t* rp, int n, long long M, int* tile_row, cudaStream_t s,
+                      int* launches);
+
+template <typename WT>
+cudaError_t degrees_min(const int64_t* rp, const WT* w, int n, WT* deg, unsigned long long* blk,
+                        DevState* st, cudaStream_t s, int* launches);
+
+template <typename WT>
+cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                       const int* L, int vbits, const int* tile_row, u64* keys, WT* vals,
+                       DevState* st, int validate, cudaStream_t s, int* launches);
+
+// After sorting: unique keys -> canonical CSR (rp2[n2+1], col2, w2); the
+// number of unique entries goes to *m2_dev.  uid/part: N and N/4096+1 ints.
+template <typename WT>
+cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
+                      int* part, int64_t* rp2, int* col2, WT* w2, DevState* st, int* m2_dev,
+                      cudaStream_t s, int* launches);
+
+template <typename WT>
+cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                            const int* tile_row, DevState* st, cudaStream_t s, int* launches);
+
+template <typename WT>
+cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                     const WT* deg, const int* tile_row, uint32_t mask, long long budget,
+                     int* parent, uint8_t* flags_out, DevState* st, cudaStream_t s,
+                     int* launches);
+
+// One label-propagation sweep (vertices with ((v ^ sweep) & 1) == 0 update).
+// Rows longer than 128 entries use tables of 2d slots from the pool.
+template <typename WT>
+cudaError_t lp_sweep(int n, const int64_t* rp, const int* col, const WT* w, const int* lab_in,
+                     int* lab_out, int sweep, int* long_rows, int* long_count, int* pool_lab,
+                     long long* pool_sc, long long pool_slots, unsigned long long* pool_cursor,
+                     DevState* st, cudaStream_t s, int* launches);
+
+// Minimum cut value over the proper clusters of `lab` -> st->lp_val/lp_label.
+template <typename WT>
+cudaError_t lp_bound(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                     const int* lab, const int* tile_row, long long* cut, int* size,
+                     unsigned long long* blk, DevState* st, cudaStream_t s, int* launches);
+
+// union-find / relabel
+cudaError_t uf_init(int* parent, int n, cudaStream_t s, int* launches);
+cudaError_t uf_hook_pairs(int* parent, const int* pu, const int* pv, long long np, int n,
+                          DevState* st, cudaStream_t s, int* launches);
+cudaError_t uf_from_groups(int* parent, const int* group, int* gmin, int n, DevState* st,
+                           cudaStream_t s, int* launches);
+// L[v] = dense rank of find(v); st->n_next = number of roots.
+cudaError_t uf_relabel(int* parent, int* L, int* flags, int* rank, int* part, int n,
+                       DevState* st, cudaStream_t s, int* launches);
+cudaError_t compose_map(int* map0, const int* L, int n0, cudaStream_t s, int* launches);
+
+// witness sides over the original vertices
+cudaError_t side_from_vertex(uint8_t* side0, const int* map0, int n0, int x, cudaStream_t s,
+                             int* launches);
+cudaError_t side_from_label(uint8_t* side0, const int* map0, int n0, const int* lab, int l,
+                            cudaStream_t s, int* launches);
+cudaError_t side_from_list(uint8_t* side0, const int* map0, int n0, uint8_t* cur, int n,
+                           const int* list, int len, cudaStream_t s, int* launches);
+cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream_t s,
+                           int* launches);
+
+// ---------------------------------------------------------- capforest.cu
+struct PassConfig {
+  int passes;           // total passes run by the persistent warps
+  int table;            // slots per pass (power of two, 256..2048)
+  int warps_per_block;
+  unsigned long long seed;
+};
+// Concurrent CAPFOREST passes (Algorithm 1).  owner[n] must be zero on entry
+// (the shared visit array T); visit_log[passes*table], pass_best/pass_len
+// [passes]; pass_counter is one int of scratch.  Marks are hooked in parent;
+// the best alpha goes to st->cf_val/cf_pass/cf_len.
+template <typename WT>
+cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT* w,
+                             const WT* deg, int* owner, int* parent, int* visit_log,
+                             unsigned long long* pass_best, int* pass_len, int* pass_counter,
+                             PassConfig pc, DevState* st, cudaStream_t s, int* launches);
+size_t capforest_pass_smem(int table, int warps_per_block, size_t wt_size);
+
+// One sequential CAPFOREST pass over the whole graph from `start` (one block).
+// r[n], visited[n], tree[seq_tree_words(n)] are scratch (unused when the pass
+// fits in shared memory); order[n] receives the visit order; marks_out
+// (nullable) up to marks_cap pairs.  The best alpha goes to st->cf_val/cf_len
+// with st->cf_pass = -1; st->cf_nscanned counts the visited vertices.
+template <typename WT>
+cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const WT* w,
+                                 const WT* deg, int start, int* parent, WT* r,
+                                 uint8_t* visited, unsigned long long* tree, int* order,
+                                 int* marks_out, long long marks_cap, DevState* st,
+                                 cudaStream_t s, int* launches);
+long long seq_tree_words(int n);
+
+}  // namespace mc

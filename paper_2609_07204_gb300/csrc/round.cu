@@ -1,0 +1,923 @@
+// round.cu -- the bandwidth-bound kernels of one contraction round.
+//
+//   degrees_min   trivial-cut / collapsed-vertex bound (Sec. 2, Sec. 2.1)
+//   lp_sweep      label propagation sweeps (Sec. 2.1, "Lowering the upper bound")
+//   lp_bound      cluster cut values of the LP labelling
+//   pr_marks      Padberg-Rinaldi tests PR1-PR4 (Sec. 2.1, App. A)
+//   uf_*          union-find over marked edges and canonical relabel (Alg. 1 "U")
+//   emit_pairs    relabel endpoints and drop self-loops (contraction, Sec. 2)
+//   build_csr     sum parallel edges after the sort and rebuild the CSR
+//   side_*        materialise the side of the best cut over the input vertices
+//
+// Entry-parallel kernels work on tiles of kEntryTile consecutive CSR entries;
+// tile_rows() records the row of each tile's first entry so a block finds the
+// rows of its entries with a binary search in shared memory.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mc {
+
+namespace {
+
+constexpr int kET = kEntryTile;
+constexpr int kETThreads = 256;
+constexpr int kETItems = kET / kETThreads;  // 8
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+template <typename P>
+__device__ __forceinline__ int row_in(const P* a, int lo, int hi, long long x) {
+  while (hi - lo > 1) {
+    int mid = lo + ((hi - lo) >> 1);
+    if ((long long)a[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Shared-memory description of the rows covering one entry tile.
+struct TileRowsSmem {
+  long long rp[kET + 2];
+  int r0, r1, use;
+};
+
+__device__ __forceinline__ void tile_rows_load(TileRowsSmem& s, const int64_t* rp, int n,
+                                               const int* tile_row, int ntiles, int t) {
+  if (threadIdx.x == 0) {
+    s.r0 = tile_row[t];
+    s.r1 = (t + 1 < ntiles) ? tile_row[t + 1] : n - 1;
+    s.use = (s.r1 - s.r0 + 2) <= (kET + 2);
+  }
+  __syncthreads();
+  if (s.use)
+    for (int i = threadIdx.x; i < s.r1 - s.r0 + 2; i += blockDim.x) s.rp[i] = rp[s.r0 + i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ int tile_row_of(const TileRowsSmem& s, const int64_t* rp, long long e) {
+  return s.use ? s.r0 + row_in(s.rp, 0, s.r1 - s.r0 + 1, e) : row_in(rp, s.r0, s.r1 + 1, e);
+}
+
+__global__ void tile_rows_kernel(const int64_t* __restrict__ rp, int n, int* __restrict__ tile_row) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    long long b = rp[u], e = rp[u + 1];
+    if (e <= b) continue;
+    long long t0 = (b + kET - 1) / kET, t1 = (e + kET - 1) / kET;
+    for (long long t = t0; t < t1; ++t) tile_row[t] = u;
+  }
+}
+
+// ------------------------------------------------------------ degrees / bound
+struct ValArg {
+  unsigned long long v;
+  int a;
+};
+__device__ __forceinline__ ValArg va_min(ValArg x, ValArg y) {
+  return (y.v < x.v || (y.v == x.v && y.a < x.a)) ? y : x;
+}
+__device__ __forceinline__ ValArg warp_va_min(ValArg x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ValArg y;
+    y.v = __shfl_xor_sync(FULL, x.v, o);
+    y.a = __shfl_xor_sync(FULL, x.a, o);
+    x = va_min(x, y);
+  }
+  return x;
+}
+// Block-wide (value, arg) minimum; result valid in thread 0.
+__device__ __forceinline__ ValArg block_va_min(ValArg x) {
+  __shared__ unsigned long long sv[32];
+  __shared__ int sa[32];
+  x = warp_va_min(x);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sv[warp] = x.v; sa[warp] = x.a; }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    ValArg y{~0ull, 0x7fffffff};
+    if (lane < nw) { y.v = sv[lane]; y.a = sa[lane]; }
+    x = warp_va_min(y);
+  }
+  __syncthreads();
+  return x;
+}
+
+// deg[v] = sum of w over row v (one warp per row); per-block (min, argmin).
+template <typename WT>
+__global__ void degrees_kernel(const int64_t* __restrict__ rp, const WT* __restrict__ w, int n,
+                               WT* __restrict__ deg, unsigned long long* __restrict__ blk) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  ValArg best{~0ull, 0x7fffffff};
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const long long b = rp[v], e = rp[v + 1];
+    long long s = 0;
+    for (long long i = b + lane; i < e; i += 32) s += (long long)w[i];
+    s = warp_sum(s);
+    if (lane == 0) deg[v] = (WT)s;
+    best = va_min(best, ValArg{(unsigned long long)s, v});
+  }
+  ValArg r = block_va_min(best);
+  if (threadIdx.x == 0) {
+    blk[2 * blockIdx.x] = r.v;
+    blk[2 * blockIdx.x + 1] = (unsigned long long)(unsigned)r.a;
+  }
+}
+
+__global__ void degmin_final_kernel(const unsigned long long* __restrict__ blk, int nb,
+                                    DevState* st) {
+  ValArg best{~0ull, 0x7fffffff};
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    best = va_min(best, ValArg{blk[2 * i], (int)blk[2 * i + 1]});
+  ValArg r = block_va_min(best);
+  if (threadIdx.x == 0) {
+    st->deg_val = r.v;
+    st->deg_arg = r.a;
+    atomicMin(&st->lambda, r.v);
+  }
+}
+
+// ---------------------------------------------------------------- emit
+// Relabel every entry (u, v, w) to the key (L[u] << vbits) | L[v]; drop
+// self-loops (L[u] == L[v]) and zero weights.  With `validate`, also flag
+// out-of-range indices and negative weights (input canonicalisation).
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    emit_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                const WT* __restrict__ w, const int* __restrict__ L, int vbits,
+                const int* __restrict__ tile_row, int ntiles, u64* __restrict__ keys,
+                WT* __restrict__ vals, DevState* st, int validate) {
+  __shared__ TileRowsSmem tr;
+  __shared__ int s_cnt[kETItems][kETThreads / 32];
+  __shared__ long long s_base;
+  const int t = blockIdx.x;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, t);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long e0 = (long long)t * kET;
+  u64 key[kETItems];
+  WT val[kETItems];
+  unsigned ball[kETItems];
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    bool keep = false;
+    if (e < M) {
+      const int u = tile_row_of(tr, rp, e);
+      const int v = col[e];
+      const WT c = w[e];
+      if (validate && (v < 0 || v >= n || c < 0)) {
+        bad = true;
+      } else {
+        const int lu = L ? L[u] : u;
+        const int lv = L ? L[v] : v;
+        keep = (lu != lv) && (c != 0);
+        key[i] = ((u64)(unsigned)lu << vbits) | (u64)(unsigned)lv;
+        val[i] = c;
+      }
+    }
+    ball[i] = __ballot_sync(FULL, keep);
+    if (lane == 0) s_cnt[i][warp] = __popc(ball[i]);
+  }
+  if (bad) set_error(st, ERR_INPUT);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int i = 0; i < kETItems; ++i)
+      for (int w2 = 0; w2 < kETThreads / 32; ++w2) {
+        int c = s_cnt[i][w2];
+        s_cnt[i][w2] = s;
+        s += c;
+      }
+    s_base = s ? (long long)atomicAdd((unsigned long long*)&st->emit_count, (unsigned long long)s) : 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kETItems; ++i) {
+    if ((ball[i] >> lane) & 1u) {
+      const long long o = s_base + s_cnt[i][warp] + __popc(ball[i] & lanemask_lt());
+      keys[o] = key[i];
+      vals[o] = val[i];
+    }
+  }
+}
+
+// ----------------------------------------------------------- build CSR
+__global__ void head_flags_kernel(const u64* __restrict__ keys, int N, int* __restrict__ flag) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+// Each thread owns 8 consecutive sorted entries.  Runs of equal keys are
+// summed locally; a run that crosses a chunk boundary is finished with
+// atomics (w2 starts at zero), a run inside the chunk with a plain store.
+// Heads also write col2 and the row pointers of their row and of any empty
+// rows before it.
+template <typename WT>
+__global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict__ vals, int N,
+                              const int* __restrict__ uid, int vbits, int n2,
+                              const int* __restrict__ m2p, int64_t* __restrict__ rp2,
+                              int* __restrict__ col2, WT* __restrict__ w2) {
+  const u64 vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
+  const long long nchunks = ((long long)N + 7) / 8;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = c * 8, i1 = min(i0 + 8, (long long)N);
+    u64 prev = i0 > 0 ? keys[i0 - 1] : ~0ull;
+    long long acc = 0;
+    bool run_started_here = false;
+    int cur_uid = -1;
+    for (long long i = i0; i < i1; ++i) {
+      const u64 k = keys[i];
+      const bool head = (i == 0) || (k != prev);
+      if (head) {
+        if (cur_uid >= 0) {
+          if (run_started_here) w2[cur_uid] = (WT)acc;
+          else atomic_add_w(&w2[cur_uid], (WT)acc);
+        }
+        cur_uid = uid[i];
+        acc = 0;
+        run_started_here = true;
+        col2[cur_uid] = (int)(k & vmask);
+        const int cu = (int)(k >> vbits);
+        const int pu = (i == 0) ? -1 : (int)(prev >> vbits);
+        for (int r = pu + 1; r <= cu; ++r) rp2[r] = cur_uid;
+      } else if (cur_uid < 0) {
+        // run continues from the previous chunk; uid is an exclusive scan of
+        // head flags, so a non-head entry of run k holds k + 1
+        cur_uid = uid[i] - 1;
+        run_started_here = false;
+      }
+      acc += (long long)vals[i];
+      prev = k;
+    }
+    if (cur_uid >= 0) {
+      const bool run_ends_here = (i1 == N) || (keys[i1] != prev);
+      if (run_started_here && run_ends_here) w2[cur_uid] = (WT)acc;
+      else atomic_add_w(&w2[cur_uid], (WT)acc);
+    }
+    if (i1 == N) {
+      const int cu = (int)(prev >> vbits);
+      const int m2 = *m2p;
+      for (int r = cu + 1; r <= n2; ++r) rp2[r] = m2;
+    }
+  }
+}
+
+__global__ void rp_fill_kernel(int64_t* rp2, int n2) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= n2; r += gridDim.x * blockDim.x)
+    rp2[r] = 0;
+}
+
+// Symmetry: every entry (u, v, W) has the entry (v, u, W) (binary search in
+// the sorted row v).
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    symmetric_kernel(int n, long long M, const int64_t* __restrict__ rp,
+                     const int* __restrict__ col, const WT* __restrict__ w,
+                     const int* __restrict__ tile_row, int ntiles, DevState* st) {
+  __shared__ TileRowsSmem tr;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  const long long e0 = (long long)blockIdx.x * kET;
+  bool bad = false;
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    if (e >= M) break;
+    const int u = tile_row_of(tr, rp, e);
+    const int v = col[e];
+    long long lo = rp[v], hi = rp[v + 1];
+    while (lo < hi) {
+      long long mid = (lo + hi) >> 1;
+      if (col[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= rp[v + 1] || col[lo] != u || w[lo] != w[e]) bad = true;
+  }
+  if (bad) set_error(st, ERR_ASYM);
+}
+
+// ------------------------------------------------------------------ PR tests
+// PR1-PR4 on every canonical edge {u, v} (u < v), with the bound lambda read
+// at kernel start and c(.) the weighted degrees:
+//   PR1 c(u,v) >= lambda; PR2 c(u) < 2c(u,v) or c(v) < 2c(u,v);
+//   PR3 a common neighbour x with c(u) < 2(c(u,v)+c(u,x)) and
+//       c(v) < 2(c(u,v)+c(v,x)); PR4 c(u,v) + sum_x min(c(u,x), c(v,x)) >= lambda.
+// PR3/PR4 only when min(|N(u)|, |N(v)|) <= budget (budget < 0: always); the
+// shorter row is walked and each neighbour binary-searched in the longer one.
+// A passing edge is hooked in the union-find.  With flags_out every directed
+// entry gets its flag byte (both directions evaluated).
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    pr_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
+              const WT* __restrict__ w, const WT* __restrict__ deg,
+              const int* __restrict__ tile_row, int ntiles, uint32_t mask, long long budget,
+              int* parent, uint8_t* __restrict__ flags_out, DevState* st) {
+  __shared__ TileRowsSmem tr;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  const long long lam = (long long)*(volatile unsigned long long*)&st->lambda;
+  const long long e0 = (long long)blockIdx.x * kET;
+  unsigned long long nmarks = 0;
+  bool uf_fail = false;
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    if (e >= M) break;
+    const int u = tile_row_of(tr, rp, e);
+    const int v = col[e];
+    if (u > v && !flags_out) continue;
+    const long long c = (long long)w[e];
+    const long long du = (long long)deg[u], dv = (long long)deg[v];
+    uint8_t f = 0;
+    if ((mask & 1u) && c >= lam) f |= 1;
+    if ((mask & 2u) && (du < 2 * c || dv < 2 * c)) f |= 2;
+    if (mask & 12u) {
+      const long long bu = rp[u], eu = rp[u + 1], bv = rp[v], ev = rp[v + 1];
+      const long long lu = eu - bu, lv = ev - bv;
+      if (budget < 0 || min(lu, lv) <= budget) {
+        const bool a_is_u = lu <= lv;
+        const long long ab = a_is_u ? bu : bv, ae = a_is_u ? eu : ev;
+        const long long bb = a_is_u ? bv : bu, be = a_is_u ? ev : eu;
+        long long sum = c;
+        bool pr3 = false;
+        long long lo = bb;
+        for (long long ea = ab; ea < ae; ++ea) {
+          const int x = col[ea];
+          if (x == u || x == v) continue;
+          // neighbours of the shorter row ascend, so the search window only
+          // moves right
+          long long hi = be;
+          while (lo < hi) {
+            long long mid = (lo + hi) >> 1;
+            if (col[mid] < x) lo = mid + 1; else hi = mid;
+          }
+          if (lo >= be) break;
+          if (col[lo] != x) continue;
+          const long long ca = (long long)w[ea], cb = (long long)w[lo];
+          const long long cux = a_is_u ? ca : cb, cvx = a_is_u ? cb : ca;
+          sum += cux < cvx ? cux : cvx;
+          if (du < 2 * (c + cux) && dv < 2 * (c + cvx)) pr3 = true;
+        }
+        if ((mask & 4u) && pr3) f |= 4;
+        if ((mask & 8u) && sum >= lam) f |= 8;
+      }
+    }
+    if (flags_out) flags_out[e] = f;
+    if (f && u < v) {
+      if (!uf_union(parent, u, v)) uf_fail = true;
+      ++nmarks;
+    }
+  }
+  if (uf_fail) set_error(st, ERR_INTERNAL);
+  nmarks = warp_sum(nmarks);
+  if ((threadIdx.x & 31) == 0 && nmarks) atomicAdd(&st->marks_pr, nmarks);
+}
+
+// -------------------------------------------------------- label propagation
+constexpr int kLpShort = 128;       // rows up to this length use a warp table
+constexpr int kLpSlots = 256;       // slots of a warp table (power of two)
+constexpr int kLpWarps = 8;
+
+__device__ __forceinline__ unsigned lp_hash(int l) { return (unsigned)l * 0x9E3779B1u; }
+
+struct LabScore {
+  long long s;
+  int l;
+};
+__device__ __forceinline__ LabScore ls_best(LabScore a, LabScore b) {
+  return (b.s > a.s || (b.s == a.s && (unsigned)b.l < (unsigned)a.l)) ? b : a;
+}
+__device__ __forceinline__ LabScore warp_ls_best(LabScore x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    LabScore y;
+    y.s = __shfl_xor_sync(FULL, x.s, o);
+    y.l = __shfl_xor_sync(FULL, x.l, o);
+    x = ls_best(x, y);
+  }
+  return x;
+}
+
+// One LP sweep for the vertices v with ((v ^ sweep) & 1) == 0: v adopts the
+// neighbour label of largest total weight (ties: smaller label) if it beats
+// the weight of v's own label; labels are read from lab_in only.  Rows longer
+// than kLpShort are queued for lp_long_kernel.
+template <typename WT>
+__global__ void __launch_bounds__(kLpWarps * 32)
+    lp_short_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                    const WT* __restrict__ w, const int* __restrict__ lab_in,
+                    int* __restrict__ lab_out, int sweep, int* __restrict__ long_rows,
+                    int* long_count) {
+  __shared__ int s_key[kLpWarps][kLpSlots];
+  __shared__ long long s_sc[kLpWarps][kLpSlots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* key = s_key[warp];
+  long long* sc = s_sc[warp];
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+    const int own = lab_in[v];
+    if (((v ^ sweep) & 1) != 0) {
+      if (lane == 0) lab_out[v] = own;
+      continue;
+    }
+    const long long b = rp[v], e = rp[v + 1];
+    const long long d = e - b;
+    if (d == 0) {
+      if (lane == 0) lab_out[v] = own;
+      continue;
+    }
+    if (d > kLpShort) {
+      if (lane == 0) long_rows[atomicAdd(long_count, 1)] = v;
+      continue;
+    }
+    for (int i = lane; i < kLpSlots; i += 32) { key[i] = -1; sc[i] = 0; }
+    __syncwarp();
+    for (long long i = b + lane; i < e; i += 32) {
+      const int l = lab_in[col[i]];
+      const long long c = (long long)w[i];
+      unsigned h = lp_hash(l) & (kLpSlots - 1);
+      for (int p = 0; p < kLpSlots; ++p) {
+        int prev = atomicCAS(&key[h], -1, l);
+        if (prev == -1 || prev == l) {
+          atomicAdd((unsigned long long*)&sc[h], (unsigned long long)c);
+          break;
+        }
+        h = (h + 1) & (kLpSlots - 1);
+      }
+    }
+    __syncwarp();
+    LabScore best{-1, 0x7fffffff};
+    long long own_s = 0;
+    for (int i = lane; i < kLpSlots; i += 32) {
+      const int l = key[i];
+      if (l < 0) continue;
+      best = ls_best(best, LabScore{sc[i], l});
+      if (l == own) own_s = sc[i];
+    }
+    best = warp_ls_best(best);
+    own_s = warp_sum(own_s);
+    if (lane == 0) lab_out[v] = (best.s > own_s) ? best.l : own;
+    __syncwarp();
+  }
+}
+
+// Long rows: one block per row with an open-addressing table of 2d slots
+// taken from a global pool.
+template <typename WT>
+__global__ void lp_long_kernel(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                               const WT* __restrict__ w, const int* __restrict__ lab_in,
+                               int* __restrict__ lab_out, const int* __restrict__ long_rows,
+                               const int* long_count, int* pool_lab, long long* pool_sc,
+                               long long pool_slots, unsigned long long* pool_cursor,
+                               DevState* st) {
+  __shared__ long long s_base;
+  __shared__ long long s_bs[32];
+  __shared__ int s_bl[32];
+  __shared__ long long s_own[32];
+  const int cnt = *long_count;
+  for (int r = blockIdx.x; r < cnt; r += gridDim.x) {
+    const int v = long_rows[r];
+    const int own = lab_in[v];
+    const long long b = rp[v], e = rp[v + 1];
+    const long long slots = 2 * (e - b);
+    if (threadIdx.x == 0) {
+      unsigned long long base = atomicAdd(pool_cursor, (unsigned long long)slots);
+      s_base = (base + slots <= (unsigned long long)pool_slots) ? (long long)base : -1;
+    }
+    __syncthreads();
+    const long long base = s_base;
+    if (base < 0) {
+      if (threadIdx.x == 0) {
+        lab_out[v] = own;
+        set_error(st, ERR_OVERFLOW);
+      }
+      __syncthreads();
+      continue;
+    }
+    volatile int* key = pool_lab + base;
+    long long* sc = pool_sc + base;
+    for (long long i = threadIdx.x; i < slots; i += blockDim.x) { key[i] = -1; sc[i] = 0; }
+    __threadfence_block();
+    __syncthreads();
+    for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+      const int l = lab_in[col[i]];
+      const long long c = (long long)w[i];
+      long long h = (long long)(lp_hash(l) % (unsigned long long)slots);
+      for (long long p = 0; p < slots; ++p) {
+        int prev = atomicCAS((int*)&key[h], -1, l);
+        if (prev == -1 || prev == l) {
+          atomicAdd((unsigned long long*)&sc[h], (unsigned long long)c);
+          break;
+        }
+        h = (h + 1 == slots) ? 0 : h + 1;
+      }
+    }
+    __threadfence_block();
+    __syncthreads();
+    LabScore best{-1, 0x7fffffff};
+    long long own_s = 0;
+    volatile long long* vsc = sc;
+    for (long long i = threadIdx.x; i < slots; i += blockDim.x) {
+      const int l = key[i];
+      if (l < 0) continue;
+      const long long s = vsc[i];
+      best = ls_best(best, LabScore{s, l});
+      if (l == own) own_s = s;
+    }
+    best = warp_ls_best(best);
+    own_s = warp_sum(own_s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_bs[warp] = best.s; s_bl[warp] = best.l; s_own[warp] = own_s; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      LabScore bb{-1, 0x7fffffff};
+      long long os = 0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+        bb = ls_best(bb, LabScore{s_bs[w2], s_bl[w2]});
+        os += s_own[w2];
+      }
+      lab_out[v] = (bb.s > os) ? bb.l : own;
+    }
+    __syncthreads();
+  }
+}
+
+// Cluster cut values: cut[l] += w for every entry (u, v) with lab[u] = l != lab[v].
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    lp_cut_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                  const WT* __restrict__ w, const int* __restrict__ lab,
+                  const int* __restrict__ tile_row, int ntiles, long long* __restrict__ cut) {
+  __shared__ TileRowsSmem tr;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  const int lane = threadIdx.x & 31;
+  const long long e0 = (long long)blockIdx.x * kET;
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    int key = -1;
+    long long val = 0;
+    if (e < M) {
+      const int u = tile_row_of(tr, rp, e);
+      const int lu = lab[u];
+      if (lu != lab[col[e]]) { key = lu; val = (long long)w[e]; }
+    }
+    const unsigned peers = __match_any_sync(FULL, key);
+    long long s = 0;
+    for (int b2 = 0; b2 < 32; ++b2) {
+      long long x = __shfl_sync(FULL, val, b2);
+      if ((peers >> b2) & 1u) s += x;
+    }
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd((unsigned long long*)&cut[key], (unsigned long long)s);
+  }
+}
+
+__global__ void lp_size_kernel(const int* __restrict__ lab, int n, int* __restrict__ size) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    atomicAdd(&size[lab[v]], 1);
+}
+
+__global__ void lp_min_kernel(const long long* __restrict__ cut, const int* __restrict__ size,
+                              int n, unsigned long long* __restrict__ blk) {
+  ValArg best{~0ull, 0x7fffffff};
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+    const int s = size[l];
+    if (s > 0 && s < n) best = va_min(best, ValArg{(unsigned long long)cut[l], l});
+  }
+  ValArg r = block_va_min(best);
+  if (threadIdx.x == 0) {
+    blk[2 * blockIdx.x] = r.v;
+    blk[2 * blockIdx.x + 1] = (unsigned long long)(unsigned)r.a;
+  }
+}
+
+__global__ void lp_final_kernel(const unsigned long long* __restrict__ blk, int nb, DevState* st) {
+  ValArg best{~0ull, 0x7fffffff};
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    best = va_min(best, ValArg{blk[2 * i], (int)blk[2 * i + 1]});
+  ValArg r = block_va_min(best);
+  if (threadIdx.x == 0) {
+    st->lp_val = r.v;
+    st->lp_label = r.a;
+    if (r.v != ~0ull) atomicMin(&st->lambda, r.v);
+  }
+}
+
+// ---------------------------------------------------------------- union-find
+__global__ void uf_init_kernel(int* parent, int n) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    parent[v] = v;
+}
+
+__global__ void uf_pairs_kernel(int* parent, const int* __restrict__ pu, const int* __restrict__ pv,
+                                long long np, int n, DevState* st) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int a = pu[i], b = pv[i];
+    if (a < 0 || a >= n || b < 0 || b >= n) { set_error(st, ERR_INPUT); continue; }
+    if (!uf_union(parent, a, b)) set_error(st, ERR_INTERNAL);
+  }
+}
+
+__global__ void group_min_kernel(const int* __restrict__ group, int n, int* gmin, DevState* st) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int g = group[v];
+    if (g < 0 || g >= n) { set_error(st, ERR_INPUT); continue; }
+    atomicMin(&gmin[g], v);
+  }
+}
+
+__global__ void group_parent_kernel(const int* __restrict__ group, const int* __restrict__ gmin,
+                                    int n, int* parent) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int g = group[v];
+    parent[v] = (g >= 0 && g < n) ? gmin[g] : v;
+  }
+}
+
+__global__ void fill_i32_kernel(int* a, int n, int val) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) a[v] = val;
+}
+
+__global__ void uf_roots_kernel(int* parent, int n, int* __restrict__ flags) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int r = uf_find(parent, v);
+    flags[v] = (r == v) ? 1 : 0;
+  }
+}
+
+// After uf_roots every path has been compressed at least once; finish with
+// a full find (no writes) and map to the dense rank of the root.
+__global__ void uf_label_kernel(int* parent, int n, const int* __restrict__ rank,
+                                int* __restrict__ L) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int r = v;
+    volatile int* vp = parent;
+    while (vp[r] != r) r = vp[r];
+    L[v] = rank[r];
+  }
+}
+
+__global__ void compose_map_kernel(int* map0, const int* __restrict__ L, int n0) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x)
+    map0[i] = L[map0[i]];
+}
+
+// ----------------------------------------------------------------- witness
+__global__ void side_vertex_kernel(uint8_t* side0, const int* __restrict__ map0, int n0, int x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x)
+    side0[i] = map0[i] == x ? 1 : 0;
+}
+__global__ void side_label_kernel(uint8_t* side0, const int* __restrict__ map0, int n0,
+                                  const int* __restrict__ lab, int l) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x)
+    side0[i] = lab[map0[i]] == l ? 1 : 0;
+}
+__global__ void mark_list_kernel(uint8_t* cur, const int* __restrict__ list, int len) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x)
+    cur[list[i]] = 1;
+}
+__global__ void side_cur_kernel(uint8_t* side0, const int* __restrict__ map0, int n0,
+                                const uint8_t* __restrict__ cur) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x)
+    side0[i] = cur[map0[i]];
+}
+// bit v = side0[v] xor side0[0]: 1 on the side that does not hold vertex 0.
+__global__ void bitmap_kernel(const uint8_t* __restrict__ side0, int n0, u64* __restrict__ bitmap) {
+  const int words = (n0 + 63) / 64;
+  const uint8_t flip = side0[0];
+  for (int wd = blockIdx.x * blockDim.x + threadIdx.x; wd < words; wd += gridDim.x * blockDim.x) {
+    u64 x = 0;
+    for (int b = 0; b < 64; ++b) {
+      const int v = wd * 64 + b;
+      if (v < n0 && (side0[v] ^ flip)) x |= 1ull << b;
+    }
+    bitmap[wd] = x;
+  }
+}
+
+int grid_for(long long work, int block) {
+  long long g = (work + block - 1) / block;
+  long long cap = (long long)num_sms() * 32;
+  return (int)std::max<long long>(1, std::min(g, cap));
+}
+
+}  // namespace
+
+// ================================================================= launchers
+cudaError_t tile_rows(const int64_t* rp, int n, long long M, int* tile_row, cudaStream_t s,
+                      int* launches) {
+  if (M <= 0 || n <= 0) return cudaSuccess;
+  tile_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(rp, n, tile_row);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t degrees_min(const int64_t* rp, const WT* w, int n, WT* deg, unsigned long long* blk,
+                        DevState* st, cudaStream_t s, int* launches) {
+  const int nb = std::min(grid_for((long long)n * 32, 256), 1024);
+  degrees_kernel<WT><<<nb, 256, 0, s>>>(rp, w, n, deg, blk);
+  degmin_final_kernel<<<1, 1024, 0, s>>>(blk, nb, st);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                       const int* L, int vbits, const int* tile_row, u64* keys, WT* vals,
+                       DevState* st, int validate, cudaStream_t s, int* launches) {
+  if (M <= 0) return cudaSuccess;
+  const int ntiles = (int)((M + kET - 1) / kET);
+  emit_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, L, vbits, tile_row, ntiles,
+                                                 keys, vals, st, validate);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
+                      int* part, int64_t* rp2, int* col2, WT* w2, DevState* st, int* m2_dev,
+                      cudaStream_t s, int* launches) {
+  if (N <= 0) {
+    rp_fill_kernel<<<grid_for(n2 + 1, 256), 256, 0, s>>>(rp2, n2);
+    cudaMemsetAsync(m2_dev, 0, sizeof(int), s);
+    ++*launches;
+    return cudaGetLastError();
+  }
+  head_flags_kernel<<<grid_for(N, 256), 256, 0, s>>>(keys, N, uid);
+  ++*launches;
+  cudaError_t err = scan_exclusive_i32(uid, uid, N, part, m2_dev, s, launches);
+  if (err != cudaSuccess) return err;
+  cudaMemsetAsync(w2, 0, (size_t)N * sizeof(WT), s);
+  segsum_kernel<WT><<<grid_for((N + 7) / 8, 256), 256, 0, s>>>(keys, vals, N, uid, vbits, n2,
+                                                               m2_dev, rp2, col2, w2);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                            const int* tile_row, DevState* st, cudaStream_t s, int* launches) {
+  if (M <= 0) return cudaSuccess;
+  const int ntiles = (int)((M + kET - 1) / kET);
+  symmetric_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, tile_row, ntiles, st);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                     const WT* deg, const int* tile_row, uint32_t mask, long long budget,
+                     int* parent, uint8_t* flags_out, DevState* st, cudaStream_t s,
+                     int* launches) {
+  if (M <= 0 || mask == 0) return cudaSuccess;
+  const int ntiles = (int)((M + kET - 1) / kET);
+  pr_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, deg, tile_row, ntiles, mask,
+                                               budget, parent, flags_out, st);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t lp_sweep(int n, const int64_t* rp, const int* col, const WT* w, const int* lab_in,
+                     int* lab_out, int sweep, int* long_rows, int* long_count, int* pool_lab,
+                     long long* pool_sc, long long pool_slots, unsigned long long* pool_cursor,
+                     DevState* st, cudaStream_t s, int* launches) {
+  cudaMemsetAsync(long_count, 0, sizeof(int), s);
+  cudaMemsetAsync(pool_cursor, 0, sizeof(unsigned long long), s);
+  lp_short_kernel<WT><<<grid_for((long long)n * 32, kLpWarps * 32), kLpWarps * 32, 0, s>>>(
+      n, rp, col, w, lab_in, lab_out, sweep, long_rows, long_count);
+  lp_long_kernel<WT><<<num_sms() * 2, 512, 0, s>>>(rp, col, w, lab_in, lab_out, long_rows,
+                                                   long_count, pool_lab, pool_sc, pool_slots,
+                                                   pool_cursor, st);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t lp_bound(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                     const int* lab, const int* tile_row, long long* cut, int* size,
+                     unsigned long long* blk, DevState* st, cudaStream_t s, int* launches) {
+  cudaMemsetAsync(cut, 0, (size_t)n * sizeof(long long), s);
+  cudaMemsetAsync(size, 0, (size_t)n * sizeof(int), s);
+  if (M > 0) {
+    const int ntiles = (int)((M + kET - 1) / kET);
+    lp_cut_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, lab, tile_row, ntiles, cut);
+    ++*launches;
+  }
+  lp_size_kernel<<<grid_for(n, 256), 256, 0, s>>>(lab, n, size);
+  const int nb = std::min(grid_for(n, 256), 1024);
+  lp_min_kernel<<<nb, 256, 0, s>>>(cut, size, n, blk);
+  lp_final_kernel<<<1, 1024, 0, s>>>(blk, nb, st);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t uf_init(int* parent, int n, cudaStream_t s, int* launches) {
+  uf_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(parent, n);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t uf_hook_pairs(int* parent, const int* pu, const int* pv, long long np, int n,
+                          DevState* st, cudaStream_t s, int* launches) {
+  if (np <= 0) return cudaSuccess;
+  uf_pairs_kernel<<<grid_for(np, 256), 256, 0, s>>>(parent, pu, pv, np, n, st);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t uf_from_groups(int* parent, const int* group, int* gmin, int n, DevState* st,
+                           cudaStream_t s, int* launches) {
+  fill_i32_kernel<<<grid_for(n, 256), 256, 0, s>>>(gmin, n, 0x7fffffff);
+  group_min_kernel<<<grid_for(n, 256), 256, 0, s>>>(group, n, gmin, st);
+  group_parent_kernel<<<grid_for(n, 256), 256, 0, s>>>(group, gmin, n, parent);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t uf_relabel(int* parent, int* L, int* flags, int* rank, int* part, int n,
+                       DevState* st, cudaStream_t s, int* launches) {
+  uf_roots_kernel<<<grid_for(n, 256), 256, 0, s>>>(parent, n, flags);
+  ++*launches;
+  cudaError_t err = scan_exclusive_i32(flags, rank, n, part, &st->n_next, s, launches);
+  if (err != cudaSuccess) return err;
+  uf_label_kernel<<<grid_for(n, 256), 256, 0, s>>>(parent, n, rank, L);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t compose_map(int* map0, const int* L, int n0, cudaStream_t s, int* launches) {
+  compose_map_kernel<<<grid_for(n0, 256), 256, 0, s>>>(map0, L, n0);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t side_from_vertex(uint8_t* side0, const int* map0, int n0, int x, cudaStream_t s,
+                             int* launches) {
+  side_vertex_kernel<<<grid_for(n0, 256), 256, 0, s>>>(side0, map0, n0, x);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t side_from_label(uint8_t* side0, const int* map0, int n0, const int* lab, int l,
+                            cudaStream_t s, int* launches) {
+  side_label_kernel<<<grid_for(n0, 256), 256, 0, s>>>(side0, map0, n0, lab, l);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t side_from_list(uint8_t* side0, const int* map0, int n0, uint8_t* cur, int n,
+                           const int* list, int len, cudaStream_t s, int* launches) {
+  cudaMemsetAsync(cur, 0, (size_t)n, s);
+  if (len > 0) {
+    mark_list_kernel<<<grid_for(len, 256), 256, 0, s>>>(cur, list, len);
+    ++*launches;
+  }
+  side_cur_kernel<<<grid_for(n0, 256), 256, 0, s>>>(side0, map0, n0, cur);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream_t s,
+                           int* launches) {
+  bitmap_kernel<<<grid_for((n0 + 63) / 64, 256), 256, 0, s>>>(side0, n0, bitmap);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------- explicit instances
+#define MC_INST(WT)                                                                              \
+  template cudaError_t degrees_min<WT>(const int64_t*, const WT*, int, WT*, unsigned long long*, \
+                                       DevState*, cudaStream_t, int*);                           \
+  template cudaError_t emit_pairs<WT>(int, long long, const int64_t*, const int*, const WT*,     \
+                                      const int*, int, const int*, u64*, WT*, DevState*, int,    \
+                                      cudaStream_t, int*);                                       \
+  template cudaError_t build_csr<WT>(const u64*, const WT*, int, int, int, int*, int*, int64_t*, \
+                                     int*, WT*, DevState*, int*, cudaStream_t, int*);            \
+  template cudaError_t check_symmetric<WT>(int, long long, const int64_t*, const int*,           \
+                                           const WT*, const int*, DevState*, cudaStream_t,       \
+                                           int*);                                                \
+  template cudaError_t pr_marks<WT>(int, long long, const int64_t*, const int*, const WT*,       \
+                                    const WT*, const int*, uint32_t, long long, int*, uint8_t*,  \
+                                    DevState*, cudaStream_t, int*);                              \
+  template cudaError_t lp_sweep<WT>(int, const int64_t*, const int*, const WT*, const int*,      \
+                                    int*, int, int*, int*, int*, long long*, long long,          \
+                                    unsigned long long*, DevState*, cudaStream_t, int*);         \
+  template cudaError_t lp_bound<WT>(int, long long, const int64_t*, const int*, const WT*,       \
+                                    const int*, const int*, long long*, int*,                    \
+                                    unsigned long long*, DevState*, cudaStream_t, int*);
+
+MC_INST(int32_t)
+MC_INST(int64_t)
+
+}  // namespace mc

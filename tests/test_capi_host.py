@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI (CPU only): the library loads, exports every
+function include/mincut.h declares, and rejects bad arguments before any
+device work."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import paper_2609_07204_gb300 as mc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(mc.LIB_PATH):
+        from paper_2609_07204_gb300 import _build
+        _build.build()
+    return mc.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = mc.exported_symbols()
+    assert "mincut_graph_from_csr" in syms and "mincut_solve" in syms
+    assert "mincut_contract_round" in syms
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_struct_sizes_match_header(lib):
+    # the ctypes mirrors must match the C layout field by field
+    assert ctypes.sizeof(mc.MincutOptions) == 64
+    assert ctypes.sizeof(mc.MincutStats) == 64
+    o = mc.default_options()
+    assert (o.lp_iters, o.lp_min_n, o.lp_every_round, o.pr_mask, o.pr_budget) == (2, 10000, 1, 0xF, 64)
+    ro = mc.default_round_options()
+    assert ro.lambda_in == mc.INT64_MAX and ro.capforest == 1
+
+
+def test_status_strings(lib):
+    for s in range(-6, 1):
+        assert mc.mincut_status_string(s)
+    assert mc.mincut_status_string(-99) == "unknown status"
+
+
+def test_rejects_n_below_2_without_device_work(lib):
+    rp = np.zeros(2, np.int64)
+    with pytest.raises(mc.MincutError) as e:
+        mc.mincut_graph_from_csr(1, rp, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert e.value.status == mc.MINCUT_ERR_INVALID
+    assert "n >= 2" in mc.mincut_last_error()
+
+
+def test_rejects_bad_row_ptr_start(lib):
+    rp = np.array([1, 1, 1], np.int64)
+    with pytest.raises(mc.MincutError) as e:
+        mc.mincut_graph_from_csr(2, rp, np.zeros(1, np.int32), np.zeros(1, np.int32))
+    assert e.value.status == mc.MINCUT_ERR_INVALID
+
+
+def test_null_arguments(lib):
+    out = ctypes.c_void_p(0)
+    rc = lib.mincut_graph_from_csr(4, None, None, None, 0, None, None, ctypes.byref(out))
+    assert rc == mc.MINCUT_ERR_INVALID
+    v = ctypes.c_int64(0)
+    assert lib.mincut_solve(None, None, ctypes.byref(v), None, None) == mc.MINCUT_ERR_INVALID
+    assert lib.mincut_graph_reset(None) == mc.MINCUT_ERR_INVALID
+    lib.mincut_graph_destroy(None)  # ignored
+
+
+def test_package_fails_loudly_without_library(tmp_path):
+    with pytest.raises(RuntimeError, match="missing"):
+        mc.load_library(str(tmp_path / "nope.so"))
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2609_07204_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "oracle.c" not in text and "liboracle" not in text, f

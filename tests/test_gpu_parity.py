@@ -1,0 +1,348 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work, so the bar is bit-exact: canonical CSRs, PR flags, the
+deterministic CAPFOREST pass (visit order, mark set, bound), label
+propagation bounds and every cut value.  Where several answers are correct
+(the side of a minimum cut, the marks of concurrent passes) the tests check
+what is unique (the value) and that the rest is valid (the side's cut weight
+equals the value; every contraction keeps min(bound, lambda(G')) = lambda(G)).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2609_07204_gb300 as mc  # noqa: E402
+
+INF = mc.INT64_MAX
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mc.load_library()
+
+
+def canon(n, rp, col, w):
+    return oracle.canonicalize(n, rp, col, w)
+
+
+def make(n, rp, col, w, **kw):
+    return mc.mincut_graph_from_csr(n, np.asarray(rp, np.int64), np.asarray(col, np.int32),
+                                    np.asarray(w, np.int32), **kw)
+
+
+def assert_csr_equal(a, b):
+    assert np.array_equal(a[0], b[0]), "row_ptr differs"
+    assert np.array_equal(a[1], b[1]), "col differs"
+    assert np.array_equal(np.asarray(a[2], np.int64), np.asarray(b[2], np.int64)), "w differs"
+
+
+def noncanonical(n, rng, m, wmax=9):
+    """Symmetric multigraph with duplicates, self-loops, zero weights, rows
+    in random order."""
+    e = [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(m)]
+    w = [int(x) for x in rng.integers(0, wmax + 1, size=m)]
+    rp, col, ww = G.from_edges(n, e, w)
+    # shuffle inside rows
+    col = col.copy()
+    ww = ww.copy()
+    for u in range(n):
+        b, en = rp[u], rp[u + 1]
+        perm = rng.permutation(en - b)
+        col[b:en] = col[b:en][perm]
+        ww[b:en] = ww[b:en][perm]
+    return rp, col, ww
+
+
+# ----------------------------------------------------------- canonical input
+@pytest.mark.parametrize("n,m,seed", [(2, 1, 0), (17, 60, 1), (300, 3000, 2), (5000, 90000, 3)])
+def test_from_csr_canonicalises_like_oracle(n, m, seed):
+    rng = np.random.default_rng(seed)
+    rp, col, w = noncanonical(n, rng, m)
+    g = make(n, rp, col, w)
+    got = mc.mincut_graph_export_csr(g)
+    assert_csr_equal(got, canon(n, rp, col, w))
+
+
+def test_from_csr_large_multi_tile_multi_pass():
+    # ~1.3M raw entries: many sort tiles, 4 radix passes (n = 2^17 -> 34 key bits)
+    rng = np.random.default_rng(4)
+    n, m = 1 << 17, 650_000
+    u = rng.integers(0, n, size=m)
+    v = rng.integers(0, n, size=m)
+    w = rng.integers(1, 5, size=m)
+    src = np.concatenate([u, v]); dst = np.concatenate([v, u]); ww = np.concatenate([w, w])
+    order = rng.permutation(src.size)  # rows out of order inside
+    src, dst, ww = src[order], dst[order], ww[order]
+    o2 = np.argsort(src, kind="stable")
+    src, dst, ww = src[o2], dst[o2], ww[o2]
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, src + 1, 1)
+    rp = np.cumsum(rp)
+    g = make(n, rp, dst, ww)
+    assert_csr_equal(mc.mincut_graph_export_csr(g), canon(n, rp, dst.astype(np.int32), ww))
+
+
+def test_from_csr_device_pointers_and_torch_allocator():
+    rng = np.random.default_rng(5)
+    rp, col, w = noncanonical(400, rng, 5000)
+    t = [torch.from_numpy(np.asarray(x)).cuda() for x in (rp, col.astype(np.int32), w.astype(np.int32))]
+    g = mc.mincut_graph_from_csr(400, t[0], t[1], t[2], use_torch_allocator=True)
+    assert_csr_equal(mc.mincut_graph_export_csr(g), canon(400, rp, col, w))
+    v, bm, _ = mc.mincut_solve(g)
+    c = canon(400, rp, col, w)
+    assert v == oracle.stoer_wagner(400, *c)[0]
+    g.destroy()
+
+
+@pytest.mark.parametrize("case", ["asym", "neg", "range", "weight_asym"])
+def test_from_csr_rejects_malformed(case):
+    rp, col, w = G.from_edges(4, [(0, 1), (1, 2), (2, 3)], [1, 2, 3])
+    col = col.copy(); w = w.copy()
+    if case == "asym":
+        col[0] = 3  # 0->3 without 3->0
+    elif case == "neg":
+        w[0] = -1
+    elif case == "range":
+        col[0] = 7
+    elif case == "weight_asym":
+        w[0] = 5
+    with pytest.raises(mc.MincutError) as e:
+        make(4, rp, col, w)
+    assert e.value.status == mc.MINCUT_ERR_INVALID
+
+
+# -------------------------------------------------------------- contraction
+@pytest.mark.parametrize("n,p,seed", [(3, 0.9, 0), (60, 0.2, 1), (700, 0.05, 2), (3000, 0.01, 3)])
+def test_contract_by_groups_bit_exact(n, p, seed):
+    rng = np.random.default_rng(seed)
+    g0 = synth.er(n, int(p * n * (n - 1) / 2), 1, 50, seed + 10)
+    groups = rng.integers(0, max(1, n // 3), size=n).astype(np.int32)
+    g = make(n, g0.row_ptr, g0.col, g0.w)
+    ro = mc.default_round_options()
+    ro.groups = groups.ctypes.data
+    res = mc.mincut_contract_round(g, ro)
+    n2, L = oracle.labels_from_groups(groups)
+    exp = oracle.contract(n, g0.row_ptr, g0.col, g0.w, L, n2)
+    assert res["n_out"] == n2
+    assert_csr_equal(mc.mincut_graph_export_csr(g), exp)
+
+
+def test_contract_by_pairs_bit_exact_and_chained():
+    rng = np.random.default_rng(8)
+    g0 = synth.er(4000, 40000, 1, 20, 8)
+    g = make(g0.n, g0.row_ptr, g0.col, g0.w)
+    n, rp, col, w = g0.n, g0.row_ptr, g0.col, g0.w.astype(np.int64)
+    for step in range(4):
+        k = n // 2
+        pu = rng.integers(0, n, size=k).astype(np.int32)
+        pv = rng.integers(0, n, size=k).astype(np.int32)
+        ro = mc.default_round_options()
+        ro.npairs = k
+        ro.pair_u = pu.ctypes.data
+        ro.pair_v = pv.ctypes.data
+        res = mc.mincut_contract_round(g, ro)
+        n2, L = oracle.labels_from_pairs(n, pu, pv)
+        rp, col, w = oracle.contract(n, rp, col, w, L, n2)
+        n = n2
+        assert res["n_out"] == n2
+        assert_csr_equal(mc.mincut_graph_export_csr(g), (rp, col, w))
+    mc.mincut_graph_reset(g)
+    assert mc.mincut_graph_info(g) == (g0.n, g0.M)
+
+
+# ------------------------------------------------------------------ PR flags
+@pytest.mark.parametrize("budget", [-1, 3])
+def test_pr_flags_bit_exact(budget):
+    rng = np.random.default_rng(12)
+    for trial in range(6):
+        n = int(rng.integers(30, 400))
+        g0 = G.random_graph(n, float(rng.uniform(0.02, 0.3)), rng, 1, int(rng.integers(1, 20)))
+        c = canon(n, *g0)
+        lam = int(oracle.degrees(n, *c).min())
+        g = make(n, c[0], c[1], c[2])
+        M = int(c[0][-1])
+        flags = np.zeros(max(M, 1), np.uint8)
+        ro = mc.default_round_options()
+        ro.capforest = 0
+        ro.lp_iters = 0
+        ro.pr_budget = budget
+        ro.pr_flags_out = flags.ctypes.data
+        res = mc.mincut_contract_round(g, ro)
+        if res["stopped"]:
+            continue
+        exp = oracle.pr_marks(n, *c, lam, 0xF, budget)
+        assert np.array_equal(flags[:M], exp)
+
+
+# ------------------------------------------------ deterministic CAPFOREST pass
+def _det_round(n, c, lam_in=INF, start=0, lp_iters=0, lp_min_n=10000, pr_mask=0xF):
+    g = make(n, c[0], c[1], c[2])
+    M = int(c[0][-1])
+    order = np.zeros(n, np.int32)
+    marks = np.zeros(2 * (M // 2 + 1), np.int32)
+    ro = mc.default_round_options()
+    ro.lambda_in = lam_in
+    ro.capforest = 2
+    ro.cf_start = start
+    ro.lp_iters = lp_iters
+    ro.lp_min_n = lp_min_n
+    ro.pr_mask = pr_mask
+    ro.pr_budget = -1
+    ro.cf_order_out = order.ctypes.data
+    ro.cf_marks_out = marks.ctypes.data
+    ro.cf_marks_cap = M // 2 + 1
+    res = mc.mincut_contract_round(g, ro)
+    return g, res, order[:res["cf_nscanned"]], marks[:2 * res["cf_nmarks"]].reshape(-1, 2)
+
+
+@pytest.mark.parametrize("name", ["capforest_two_triangles.json", "capforest_chain.json"])
+def test_sequential_pass_golden(name):
+    import json, os
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", name)))
+    c = G.from_edges(d["n"], d["edges"], d["weights"])
+    g, res, order, marks = _det_round(d["n"], c, d["lambda_in"], d["start"], pr_mask=0)
+    assert order.tolist() == d["expect"]["order"]
+    assert sorted(map(tuple, marks.tolist())) == sorted(map(tuple, d["expect"]["marks"]))
+    assert res["lambda_out"] == d["expect"]["lambda_out"]
+
+
+def test_sequential_pass_bit_exact_random():
+    rng = np.random.default_rng(31)
+    for trial in range(25):
+        n = int(rng.integers(3, 3000))
+        p = min(0.9, float(rng.uniform(2, 20)) / n)
+        g0 = G.random_graph(n, p, rng, 1, int(rng.integers(1, 30))) if n < 200 else None
+        if g0 is None:
+            s = synth.er(n, int(p * n * (n - 1) / 2), 1, int(rng.integers(1, 30)), trial)
+            g0 = (s.row_ptr, s.col, s.w)
+        c = canon(n, *g0)
+        deg = oracle.degrees(n, *c)
+        lam = int(deg.min()) if n >= 2 else INF
+        start = int(rng.integers(0, n))
+        g, res, order, marks = _det_round(n, c, INF, start, pr_mask=0)
+        if res["stopped"]:
+            assert lam == 0 or n <= 2
+            continue
+        r = oracle.capforest(n, *c, lam, start)
+        assert order.tolist() == r["order"].tolist(), trial
+        assert sorted(map(tuple, marks.tolist())) == sorted(map(tuple, r["marks"].tolist())), trial
+        assert res["lambda_out"] == r["lambda"]
+
+
+def test_deterministic_round_bit_exact_with_pr_and_lp():
+    rng = np.random.default_rng(41)
+    for trial in range(12):
+        n = int(rng.integers(40, 2500))
+        s = synth.er_connected(n, int(n * rng.uniform(2, 8)), 1, int(rng.integers(1, 40)), trial + 100)
+        c = (s.row_ptr, s.col, s.w.astype(np.int64))
+        lp_iters = int(rng.integers(0, 4))
+        g, res, _, _ = _det_round(n, c, INF, 0, lp_iters=lp_iters, lp_min_n=10)
+        n2, rp2, col2, w2, info = oracle.round_(n, *c, lambda_in=INF, lp_iters=lp_iters,
+                                                lp_min_n=10, pr_mask=0xF, pr_budget=-1,
+                                                capforest=True, cf_start=0)
+        assert res["lambda_out"] == info["lambda"], trial
+        assert res["n_out"] == n2
+        assert res["marks_pr"] == info["marks_pr"]
+        assert_csr_equal(mc.mincut_graph_export_csr(g), (rp2, col2, w2))
+
+
+# ---------------------------------------------------------- concurrent passes
+def test_concurrent_round_sound_brute_force():
+    rng = np.random.default_rng(51)
+    for trial in range(60):
+        n = int(rng.integers(4, 15))
+        g0 = G.random_graph(n, float(rng.uniform(0.2, 1.0)), rng, 1, int(rng.integers(1, 9)))
+        c = canon(n, *g0)
+        lam_true, _ = oracle.mincut_brute(n, *c)
+        g = make(n, c[0], c[1], c[2])
+        ro = mc.default_round_options()
+        ro.capforest = 1
+        ro.passes = int(rng.integers(1, 8))
+        ro.seed = trial
+        ro.lp_min_n = 4
+        res = mc.mincut_contract_round(g, ro)
+        rp2, col2, w2 = mc.mincut_graph_export_csr(g)
+        n2 = res["n_out"]
+        lam2 = oracle.mincut_brute(n2, rp2, col2, w2)[0] if n2 >= 2 else INF
+        assert min(res["lambda_out"], lam2) == lam_true, trial
+
+
+# ---------------------------------------------------------------- full solve
+def _check_solve(n, c, opts=None, expect=None):
+    g = make(n, c[0], c[1], c[2])
+    v, bm, st = mc.mincut_solve(g, opts)
+    if expect is None:
+        expect = oracle.stoer_wagner(n, *c)[0]
+    assert v == expect, (v, expect, st)
+    side = mc.bitmap_to_side(bm, n)
+    assert side[0] == 0 and 0 < side.sum() < n
+    assert oracle.cut_weight(n, *c, side) == v
+    g.destroy()
+    return st
+
+
+def test_solve_closed_forms():
+    cases = [(G.cycle(50), 50, 2), (G.complete(12), 12, 11), (G.hypercube(6), 64, 6),
+             (G.grid(9, 11), 99, 2), (G.complete_bipartite(3, 9), 12, 3),
+             (G.two_cliques(8, 1, 5, 3), 16, 3)]
+    for c, n, lam in cases:
+        _check_solve(n, canon(n, *c), expect=lam)
+
+
+def test_solve_disconnected_and_isolated():
+    rp, col, w = G.from_edges(9, [(0, 1), (1, 2), (3, 4), (4, 5), (5, 3), (6, 7)], [4, 4, 2, 2, 2, 9])
+    _check_solve(9, canon(9, rp, col, w), expect=0)
+
+
+def test_solve_random_small_vs_stoer_wagner():
+    rng = np.random.default_rng(61)
+    for trial in range(40):
+        n = int(rng.integers(2, 60))
+        g0 = G.random_graph(n, float(rng.uniform(0.05, 0.8)), rng, 1, int(rng.integers(1, 50)))
+        c = canon(n, *g0)
+        if int(c[0][-1]) == 0:
+            continue
+        opts = mc.default_options(lp_min_n=8, seed=trial, deterministic=trial % 3 == 0)
+        _check_solve(n, c, opts)
+
+
+def test_solve_er2000_workload():
+    s = synth.workload_er2000()
+    c = (s.row_ptr, s.col, s.w.astype(np.int64))
+    sw = oracle.stoer_wagner(s.n, *c)[0]
+    st = _check_solve(s.n, c, mc.default_options(), expect=sw)
+    st2 = _check_solve(s.n, c, mc.default_options(deterministic=1), expect=sw)
+    assert st["rounds"] >= 1 and st2["rounds"] >= 1
+
+
+def test_solve_int64_weights():
+    rng = np.random.default_rng(71)
+    for trial in range(4):
+        n = 120
+        g0 = G.random_graph(n, 0.1, rng, 2 ** 28, 2 ** 31 - 1, connected=True)
+        c = canon(n, *g0)
+        assert int(c[2].sum()) > 2 ** 31
+        _check_solve(n, c, mc.default_options(lp_min_n=10, seed=trial))
+
+
+def test_solve_rmat_core_small():
+    s = synth.workload_rmat_core(scale=14, k=10, seed=2)
+    c = (s.row_ptr, s.col, s.w.astype(np.int64))
+    lam, _, _ = oracle.noi(s.n, *c)
+    _check_solve(s.n, c, mc.default_options(lp_min_n=1000), expect=lam)
+
+
+def test_solve_planted_small():
+    s = synth.planted(1 << 12, 21 << 12, 30, 25, 1, 5)
+    c = (s.row_ptr, s.col, s.w.astype(np.int64))
+    _check_solve(s.n, c, mc.default_options(lp_min_n=1000), expect=25)
