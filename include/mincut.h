@@ -80,6 +80,8 @@ typedef struct mincut_options {
     int32_t deterministic;   /* 1: one sequential CAPFOREST pass from vertex 0 per round */
     int32_t max_rounds;      /* 0 = unlimited */
     int64_t spin_limit;      /* iteration limit of bounded device waits (0 = default) */
+    int32_t profile;         /* 1: time every kernel with CUDA events (mincut_profile_read) */
+    int32_t reserved;
 } mincut_options;
 
 /* Statistics of a solve (all optional to read). */
@@ -173,6 +175,21 @@ int mincut_graph_reset(mincut_graph* g);
 
 /* Release a graph and its device memory (NULL is ignored). */
 void mincut_graph_destroy(mincut_graph* g);
+
+/* Per-kernel-category timing collected by solves run with opts->profile = 1
+ * (CUDA events recorded on the graph's stream around each launch).  Fills up
+ * to `cap` entries (out may be NULL to count), sets *count to the number of
+ * categories with at least one launch; reset != 0 clears the totals.
+ * `units` is the work each launch was given (directed entries for the edge
+ * kernels, vertices for the vertex kernels). */
+typedef struct mincut_profile_entry {
+    char name[24];
+    int64_t launches;
+    int64_t units;
+    double ms;
+} mincut_profile_entry;
+int mincut_profile_read(mincut_graph* g, mincut_profile_entry* out, int32_t cap, int32_t* count,
+                        int32_t reset);
 
 /* Static description of a status code. */
 const char* mincut_status_string(int status);

@@ -50,7 +50,8 @@ class MincutOptions(ctypes.Structure):
                 ("pr_budget", ctypes.c_int64), ("passes", ctypes.c_int32),
                 ("pass_table", ctypes.c_int32), ("waves", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("deterministic", ctypes.c_int32),
-                ("max_rounds", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+                ("max_rounds", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class MincutStats(ctypes.Structure):
@@ -97,6 +98,11 @@ class MincutAllocator(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
 
 
+class MincutProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64),
+                ("units", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -135,6 +141,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mincut_status_string.restype = ctypes.c_char_p
     lib.mincut_last_error.argtypes = []
     lib.mincut_last_error.restype = ctypes.c_char_p
+    lib.mincut_profile_read.argtypes = [vp, ctypes.POINTER(MincutProfileEntry), i32,
+                                        ctypes.POINTER(i32), i32]
+    lib.mincut_profile_read.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -321,6 +330,17 @@ def mincut_graph_reset(g: Graph) -> None:
 
 def mincut_graph_destroy(g: Graph) -> None:
     g.destroy()
+
+
+def mincut_profile_read(g: Graph, reset: bool = False) -> dict:
+    """Per-kernel-category device time of profiled solves:
+    {name: {"launches", "units", "ms"}}."""
+    lib = load_library()
+    buf = (MincutProfileEntry * 32)()
+    cnt = ctypes.c_int32(0)
+    _check(lib.mincut_profile_read(g.handle, buf, 32, ctypes.byref(cnt), 1 if reset else 0))
+    return {buf[i].name.decode(): {"launches": int(buf[i].launches), "units": int(buf[i].units),
+                                   "ms": float(buf[i].ms)} for i in range(cnt.value)}
 
 
 def mincut_status_string(status: int) -> str:

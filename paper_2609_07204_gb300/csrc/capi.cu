@@ -151,6 +151,7 @@ struct mincut_graph {
   DevState* hst = nullptr;  // pinned mirror
   int* m2_dev = nullptr;
   int launches = 0;
+  Profiler* prof = nullptr;
   long long spin_limit = 1ll << 22;
 
   const int64_t* crp() const { return cur < 0 ? rp0 : rp[cur]; }
@@ -158,7 +159,34 @@ struct mincut_graph {
   const void* cw() const { return cur < 0 ? w0 : w[cur]; }
 };
 
+namespace mc {
+Profiler* prof_create();
+void prof_destroy(Profiler* p);
+void prof_flush(Profiler* p);
+void prof_read(const Profiler* p, int cat, double* ms, long long* launches, long long* units);
+void prof_reset(Profiler* p);
+}  // namespace mc
+
 namespace {
+
+// Installs the graph's profiler on this thread for the duration of a call.
+struct ProfGuard {
+  mincut_graph* g;
+  bool on;
+  ProfGuard(mincut_graph* gg, bool enable) : g(gg), on(enable) {
+    if (on) {
+      if (!g->prof) g->prof = prof_create();
+      tl_prof = g->prof;
+    }
+  }
+  ~ProfGuard() {
+    if (on) {
+      cudaStreamSynchronize(g->stream);
+      prof_flush(g->prof);
+      tl_prof = nullptr;
+    }
+  }
+};
 
 void* dev_alloc(mincut_graph* g, size_t bytes) {
   bytes = std::max<size_t>(bytes, 16);
@@ -239,14 +267,16 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   cudaStream_t s = g->stream;
   const int n = g->n;
   const long long M = g->M;
-  CK(uf_relabel(g->parent, g->L, g->flags, g->rank, g->part, n, g->st, s, &g->launches));
+  { ProfScope ps(P_UF, n, s);
+    CK(uf_relabel(g->parent, g->L, g->flags, g->rank, g->part, n, g->st, s, &g->launches)); }
   int rc = sync_state(g);
   if (rc) return rc;
   const int n2 = g->hst->n_next;
   const int vbits = bits_for(n2);
   CK(cudaMemsetAsync(&g->st->emit_count, 0, sizeof(long long), s));
-  CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
-                    g->keys[0], (WT*)g->vals[0], g->st, 0, s, &g->launches));
+  { ProfScope ps(P_EMIT, M, s);
+    CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
+                      g->keys[0], (WT*)g->vals[0], g->st, 0, s, &g->launches)); }
   rc = sync_state(g);
   if (rc) return rc;
   const long long N = g->hst->emit_count;
@@ -254,10 +284,14 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
                           2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
   const int nxt = g->cur == 0 ? 1 : 0;
-  CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
-                   vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], g->st,
-                   g->m2_dev, s, &g->launches));
-  if (compose) CK(compose_map(g->map0, g->L, g->n0, s, &g->launches));
+  { ProfScope ps(P_BUILD, N, s);
+    CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
+                     vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], g->st,
+                     g->m2_dev, s, &g->launches)); }
+  if (compose) {
+    ProfScope ps(P_UF, g->n0, s);
+    CK(compose_map(g->map0, g->L, g->n0, s, &g->launches));
+  }
   int m2 = 0;
   CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   rc = sync_state(g);
@@ -308,11 +342,15 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   WT* deg = (WT*)g->deg;
   reset_round_kernel<<<1, 1, 0, s>>>(g->st);
   ++g->launches;
-  if (n >= 2) CK(degrees_min<WT>(rp, w, n, deg, g->blk, g->st, s, &g->launches));
+  if (n >= 2) {
+    ProfScope ps(P_DEGREE, M, s);
+    CK(degrees_min<WT>(rp, w, n, deg, g->blk, g->st, s, &g->launches));
+  }
   int rc = sync_state(g);
   if (rc) return rc;
   long long lam = (long long)g->hst->lambda;
   if (lam < lambda_before) {
+    ProfScope ps(P_WITNESS, g->n0, s);
     CK(side_from_vertex(g->side0, g->map0, g->n0, g->hst->deg_arg, s, &g->launches));
     o->src = 1;
     lambda_before = lam;
@@ -322,26 +360,33 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     o->stopped = true;
     return MINCUT_OK;
   }
-  CK(tile_rows(rp, n, M, g->tile_row, s, &g->launches));
+  { ProfScope ps(P_TILES, n, s);
+    CK(tile_rows(rp, n, M, g->tile_row, s, &g->launches)); }
   const int* lab_final = nullptr;
   if (c.lp_now && c.lp_iters > 0 && n >= c.lp_min_n) {
     rc = ensure_lp(g);
     if (rc) return rc;
     iota_kernel<<<std::min((n + 255) / 256, g->sms * 8), 256, 0, s>>>(g->lab[0], n);
     ++g->launches;
-    for (int it = 0; it < c.lp_iters; ++it)
+    for (int it = 0; it < c.lp_iters; ++it) {
+      ProfScope ps(P_LP_SWEEP, M, s);
       CK(lp_sweep<WT>(n, rp, col, w, g->lab[it & 1], g->lab[(it + 1) & 1], it, g->long_rows,
                       g->long_count, g->pool_lab, g->pool_sc, g->pool_slots, g->pool_cursor,
                       g->st, s, &g->launches));
+    }
     lab_final = g->lab[c.lp_iters & 1];
+    ProfScope ps(P_LP_BOUND, M, s);
     CK(lp_bound<WT>(n, M, rp, col, w, lab_final, g->tile_row, g->lp_cut, g->lp_size, g->blk,
                     g->st, s, &g->launches));
   }
-  CK(uf_init(g->parent, n, s, &g->launches));
+  { ProfScope ps(P_UF, n, s);
+    CK(uf_init(g->parent, n, s, &g->launches)); }
   uint8_t* flags_dev = c.pr_flags_host ? reinterpret_cast<uint8_t*>(g->vals[1]) : nullptr;
-  if (c.pr_mask)
+  if (c.pr_mask) {
+    ProfScope ps(P_PR, M, s);
     CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, c.pr_mask, c.pr_budget, g->parent,
                     flags_dev, g->st, s, &g->launches));
+  }
   if (c.capforest == 1 && n > 2) {
     CK(cudaMemsetAsync(g->owner, 0, (size_t)n * sizeof(int), s));
     PassConfig pc;
@@ -349,6 +394,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     pc.warps_per_block = 4;
     pc.passes = std::min(c.passes, g->max_passes);
     pc.seed = c.seed;
+    ProfScope ps(P_CF_PASSES, M, s);
     CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log,
                             g->pass_best, g->pass_len, g->pass_counter, pc, g->st, s,
                             &g->launches));
@@ -365,9 +411,12 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     const long long cap = c.cf_marks_host ? std::min(c.cf_marks_cap, M / 2 + 1) : 0;
     int* marks_dev = c.cf_marks_host ? reinterpret_cast<int*>(g->keys[1]) : nullptr;
     const int start = (c.capforest == 2) ? c.cf_start : 0;
-    CK(capforest_sequential<WT>(n, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_vis,
-                                g->seq_tree, g->seq_order, marks_dev, cap, g->st, s,
-                                &g->launches));
+    {
+      ProfScope ps(P_CF_SEQ, M, s);
+      CK(capforest_sequential<WT>(n, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_vis,
+                                  g->seq_tree, g->seq_order, marks_dev, cap, g->st, s,
+                                  &g->launches));
+    }
     rc = sync_state(g);
     if (rc) return rc;
     o->seq_pass = true;
@@ -389,11 +438,13 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   if (lam < lambda_before) {
     const DevState& h = *g->hst;
     if (lab_final && h.lp_val == (unsigned long long)lam) {
+      ProfScope ps(P_WITNESS, g->n0, s);
       CK(side_from_label(g->side0, g->map0, g->n0, lab_final, h.lp_label, s, &g->launches));
       o->src = 2;
     } else if (h.cf_val == (unsigned long long)lam) {
       const int* list = h.cf_pass >= 0 ? g->visit_log + (long long)h.cf_pass * c.table
                                        : g->seq_order;
+      ProfScope ps(P_WITNESS, g->n0, s);
       CK(side_from_list(g->side0, g->map0, g->n0, g->cur_side, n, list, h.cf_len, s,
                         &g->launches));
       o->src = 3;
@@ -771,8 +822,12 @@ int mincut_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_value
   if (op.pass_table != 0 && (op.pass_table < 256 || op.pass_table > 2048 ||
                              (op.pass_table & (op.pass_table - 1))))
     return fail(MINCUT_ERR_INVALID, "pass_table must be a power of two in [256, 2048]");
-  const int rc = g->wt64 ? solve_impl<int64_t>(g, op, cut_value, side_bitmap, stats)
-                         : solve_impl<int32_t>(g, op, cut_value, side_bitmap, stats);
+  int rc;
+  {
+    ProfGuard pg(g, op.profile != 0);
+    rc = g->wt64 ? solve_impl<int64_t>(g, op, cut_value, side_bitmap, stats)
+                 : solve_impl<int32_t>(g, op, cut_value, side_bitmap, stats);
+  }
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
@@ -830,6 +885,8 @@ int mincut_graph_reset(mincut_graph* g) {
 void mincut_graph_destroy(mincut_graph* g) {
   if (!g) return;
   cudaStreamSynchronize(g->stream);
+  prof_destroy(g->prof);
+  g->prof = nullptr;
   free_all(g);
   cudaStreamSynchronize(g->stream);
   delete g;
@@ -849,5 +906,30 @@ const char* mincut_status_string(int status) {
 }
 
 const char* mincut_last_error(void) { return g_last_error.c_str(); }
+
+int mincut_profile_read(mincut_graph* g, mincut_profile_entry* out, int32_t cap, int32_t* count,
+                        int32_t reset) {
+  if (!g || !count) return fail(MINCUT_ERR_INVALID, "NULL argument");
+  *count = 0;
+  if (!g->prof) return MINCUT_OK;
+  int k = 0;
+  for (int c = 0; c < P_NCAT; ++c) {
+    double ms;
+    long long l, u;
+    prof_read(g->prof, c, &ms, &l, &u);
+    if (l == 0) continue;
+    if (out && k < cap) {
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, prof_name(c), sizeof(out[k].name) - 1);
+      out[k].launches = l;
+      out[k].units = u;
+      out[k].ms = ms;
+    }
+    ++k;
+  }
+  *count = k;
+  if (reset) prof_reset(g->prof);
+  return MINCUT_OK;
+}
 
 }  // extern "C"

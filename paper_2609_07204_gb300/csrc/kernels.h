@@ -11,6 +11,26 @@ namespace mc {
 
 using u64 = unsigned long long;
 
+// ------------------------------------------------------------ profiling
+// Optional per-kernel timing: when a Profiler is installed on the calling
+// thread, every launcher brackets its kernels with CUDA events on the launch
+// stream (category, units processed).  Resolved after the stream synchronises.
+enum ProfCat {
+  P_DEGREE, P_LP_SWEEP, P_LP_BOUND, P_PR, P_CF_PASSES, P_CF_SEQ, P_UF, P_EMIT,
+  P_SORT_HIST, P_SORT_PASS, P_BUILD, P_TILES, P_WITNESS, P_OTHER, P_NCAT
+};
+const char* prof_name(int cat);
+struct Profiler;
+extern thread_local Profiler* tl_prof;
+struct ProfScope {
+  ProfScope(int cat, long long units, cudaStream_t s);
+  ~ProfScope();
+  int cat;
+  long long units;
+  cudaStream_t s;
+  int idx;
+};
+
 // ------------------------------------------------------------- sort.cu
 // Onesweep LSD radix sort of N (key, value) pairs on the low `bits` bits of
 // the keys, 8 bits per pass.  Ping-pongs between (k0, v0) and (k1, v1);

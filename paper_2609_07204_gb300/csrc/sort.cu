@@ -317,14 +317,18 @@ cudaError_t radix_sort_pairs(u64* k0, WT* v0, u64* k1, WT* v1, int N, int bits, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int hgrid = (int)std::min<long long>((maxN + 4095) / 4096, (long long)sms * 4);
-  rs_hist_kernel<<<std::max(hgrid, 1), 512, 0, s>>>(k0, N, passes, sc.hist);
-  rs_scan_hist_kernel<<<passes, 256, 0, s>>>(sc.hist, sc.goff);
+  {
+    ProfScope ps(P_SORT_HIST, N, s);
+    rs_hist_kernel<<<std::max(hgrid, 1), 512, 0, s>>>(k0, N, passes, sc.hist);
+    rs_scan_hist_kernel<<<passes, 256, 0, s>>>(sc.hist, sc.goff);
+  }
   *launches += 2;
   const int tiles = (int)((maxN + kRsTile - 1) / kRsTile);
   u64 *ki = k0, *ko = k1;
   WT *vi = v0, *vo = v1;
   for (int p = 0; p < passes; ++p) {
     cudaMemsetAsync(sc.lookback, 0, (size_t)tiles * 256 * sizeof(u64), s);
+    ProfScope ps(P_SORT_PASS, N, s);
     rs_pass_kernel<WT><<<tiles, kRsThreads, smem, s>>>(
         ki, vi, ko, vo, N, 8 * p, sc.goff + p * 256, sc.lookback,
         reinterpret_cast<unsigned long long*>(&st->tile_counter[p]), &st->error, spin_limit);

@@ -30,7 +30,7 @@ def test_exports_every_declared_symbol(lib):
 
 def test_struct_sizes_match_header(lib):
     # the ctypes mirrors must match the C layout field by field
-    assert ctypes.sizeof(mc.MincutOptions) == 64
+    assert ctypes.sizeof(mc.MincutOptions) == 72
     assert ctypes.sizeof(mc.MincutStats) == 64
     o = mc.default_options()
     assert (o.lp_iters, o.lp_min_n, o.lp_every_round, o.pr_mask, o.pr_budget) == (2, 10000, 1, 0xF, 64)
