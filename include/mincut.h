@@ -72,7 +72,7 @@ typedef struct mincut_options {
     int32_t lp_min_n;        /* run LP only on graphs with n >= lp_min_n (default 10000) */
     int32_t lp_every_round;  /* 1: LP bound in every round (default); 0: first round only */
     uint32_t pr_mask;        /* PR1..PR4 as bits 0..3 (default 0xF) */
-    int64_t pr_budget;       /* PR3/PR4 only if min(|N(u)|,|N(v)|) <= budget (default 64; <0 = all) */
+    int64_t pr_budget;       /* PR3/PR4 only if min(|N(u)|,|N(v)|) <= budget (default 32; <0 = all) */
     int32_t passes;          /* concurrent CAPFOREST passes per wave (0 = auto) */
     int32_t pass_table;      /* per-pass table slots, power of two in [256, 2048] (0 = auto) */
     int32_t waves;           /* CAPFOREST waves per round (0 = auto) */
@@ -119,6 +119,7 @@ typedef struct mincut_round_options {
     int32_t* cf_order_out;   /* [n] visit order of the sequential pass (capforest == 2) */
     int32_t* cf_marks_out;   /* [2*cf_marks_cap] marked pairs (x, y) of that pass */
     int64_t cf_marks_cap;
+    int32_t* lp_labels_out;  /* [n] labels after the LP sweeps (when LP ran) */
 } mincut_round_options;
 
 typedef struct mincut_round_result {

@@ -75,7 +75,8 @@ class MincutRoundOptions(ctypes.Structure):
                 ("groups", ctypes.c_void_p), ("npairs", ctypes.c_int64),
                 ("pair_u", ctypes.c_void_p), ("pair_v", ctypes.c_void_p),
                 ("pr_flags_out", ctypes.c_void_p), ("cf_order_out", ctypes.c_void_p),
-                ("cf_marks_out", ctypes.c_void_p), ("cf_marks_cap", ctypes.c_int64)]
+                ("cf_marks_out", ctypes.c_void_p), ("cf_marks_cap", ctypes.c_int64),
+                ("lp_labels_out", ctypes.c_void_p)]
 
 
 class MincutRoundResult(ctypes.Structure):

@@ -122,7 +122,8 @@ struct mincut_graph {
   u64* keys[2]{};
   void* vals[2]{};
   int* tile_row = nullptr;
-  void* deg = nullptr;
+  void* deg0 = nullptr;     // degrees of the canonical input
+  void* degb[2]{};          // degrees of the ping-pong CSRs
   unsigned long long* blk = nullptr;
   int *parent = nullptr, *L = nullptr, *flags = nullptr, *rank = nullptr, *part = nullptr,
       *uid = nullptr, *owner = nullptr, *gmin = nullptr, *map0 = nullptr;
@@ -157,6 +158,7 @@ struct mincut_graph {
   const int64_t* crp() const { return cur < 0 ? rp0 : rp[cur]; }
   const int* ccol() const { return cur < 0 ? col0 : col[cur]; }
   const void* cw() const { return cur < 0 ? w0 : w[cur]; }
+  void* cdeg() const { return cur < 0 ? deg0 : degb[cur]; }
 };
 
 namespace mc {
@@ -253,7 +255,7 @@ int ensure_lp(mincut_graph* g) {
   g->pool_slots = 2 * std::max<long long>(g->M0, 1);
   if (!galloc(g, &g->lab[0], g->n0) || !galloc(g, &g->lab[1], g->n0) ||
       !galloc(g, &g->lp_cut, g->n0) || !galloc(g, &g->lp_size, g->n0) ||
-      !galloc(g, &g->long_rows, g->n0) || !galloc(g, &g->long_count, 1) ||
+      !galloc(g, &g->long_rows, 2ll * g->n0) || !galloc(g, &g->long_count, 2) ||
       !galloc(g, &g->pool_lab, g->pool_slots) || !galloc(g, &g->pool_sc, g->pool_slots) ||
       !galloc(g, &g->pool_cursor, 1))
     return fail(MINCUT_ERR_OOM, "label propagation buffers");
@@ -286,8 +288,8 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   const int nxt = g->cur == 0 ? 1 : 0;
   { ProfScope ps(P_BUILD, N, s);
     CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
-                     vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], g->st,
-                     g->m2_dev, s, &g->launches)); }
+                     vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt],
+                     (WT*)g->degb[nxt], g->st, g->m2_dev, s, &g->launches)); }
   if (compose) {
     ProfScope ps(P_UF, g->n0, s);
     CK(compose_map(g->map0, g->L, g->n0, s, &g->launches));
@@ -317,6 +319,7 @@ struct RoundCfg {
   int* cf_order_host;
   int* cf_marks_host;
   long long cf_marks_cap;
+  int* lp_labels_host;
 };
 
 struct RoundOut {
@@ -339,12 +342,12 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   const int64_t* rp = g->crp();
   const int* col = g->ccol();
   const WT* w = (const WT*)g->cw();
-  WT* deg = (WT*)g->deg;
+  const WT* deg = (const WT*)g->cdeg();
   reset_round_kernel<<<1, 1, 0, s>>>(g->st);
   ++g->launches;
   if (n >= 2) {
-    ProfScope ps(P_DEGREE, M, s);
-    CK(degrees_min<WT>(rp, w, n, deg, g->blk, g->st, s, &g->launches));
+    ProfScope ps(P_DEGREE, n, s);
+    CK(degrees_min<WT>(deg, n, g->blk, g->st, s, &g->launches));
   }
   int rc = sync_state(g);
   if (rc) return rc;
@@ -378,6 +381,9 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     ProfScope ps(P_LP_BOUND, M, s);
     CK(lp_bound<WT>(n, M, rp, col, w, lab_final, g->tile_row, g->lp_cut, g->lp_size, g->blk,
                     g->st, s, &g->launches));
+    if (c.lp_labels_host)
+      CK(cudaMemcpyAsync(c.lp_labels_host, lab_final, (size_t)n * sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
   }
   { ProfScope ps(P_UF, n, s);
     CK(uf_init(g->parent, n, s, &g->launches)); }
@@ -588,6 +594,7 @@ int contract_round_impl(mincut_graph* g, const mincut_round_options* ro,
   c.cf_order_host = ro->cf_order_out;
   c.cf_marks_host = ro->cf_marks_out;
   c.cf_marks_cap = ro->cf_marks_cap;
+  c.lp_labels_host = ro->lp_labels_out;
   CK(cudaMemsetAsync(g->side0, 0, (size_t)g->n0, s));
   iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
   RoundOut o;
@@ -630,8 +637,8 @@ int canonicalize_input(mincut_graph* g, int n, long long Mraw, bool validate) {
   CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
                           2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
   CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
-                   vbits, n, g->uid, g->part, g->rp[0], g->col[0], (WT*)g->w[0], g->st,
-                   g->m2_dev, s, &g->launches));
+                   vbits, n, g->uid, g->part, g->rp[0], g->col[0], (WT*)g->w[0], (WT*)g->deg0,
+                   g->st, g->m2_dev, s, &g->launches));
   int m2 = 0;
   CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   rc = sync_state(g);
@@ -736,7 +743,8 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   const long long scan_parts = (std::max<long long>(Mb, n) + 4095) / 4096 + 2;
   g->max_table = 1024;
   g->max_passes = std::max(256, g->sms * 12 * 4);
-  ok = ok && galloc(g, &g->tile_row, ntiles) && (g->deg = dev_alloc(g, (size_t)n * wsz)) &&
+  ok = ok && galloc(g, &g->tile_row, ntiles) && (g->deg0 = dev_alloc(g, (size_t)n * wsz)) &&
+       (g->degb[0] = dev_alloc(g, (size_t)n * wsz)) && (g->degb[1] = dev_alloc(g, (size_t)n * wsz)) &&
        galloc(g, &g->blk, 2 * 1024) && galloc(g, &g->parent, n) && galloc(g, &g->L, n) &&
        galloc(g, &g->flags, n) && galloc(g, &g->rank, n) && galloc(g, &g->part, scan_parts) &&
        galloc(g, &g->uid, Mb) && galloc(g, &g->owner, n) && galloc(g, &g->gmin, n) &&
@@ -790,7 +798,7 @@ void mincut_default_options(mincut_options* o) {
   o->lp_min_n = 10000;
   o->lp_every_round = 1;
   o->pr_mask = 0xF;
-  o->pr_budget = 64;
+  o->pr_budget = 32;
   o->seed = 0x5eed;
 }
 
@@ -801,7 +809,7 @@ void mincut_default_round_options(mincut_round_options* ro) {
   ro->lp_iters = 2;
   ro->lp_min_n = 10000;
   ro->pr_mask = 0xF;
-  ro->pr_budget = 64;
+  ro->pr_budget = 32;
   ro->capforest = 1;
   ro->seed = 0x5eed;
 }

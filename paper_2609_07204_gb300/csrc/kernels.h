@@ -58,21 +58,24 @@ constexpr int kEntryTile = 2048;  // entries per block of the entry-parallel ker
 cudaError_t tile_rows(const int64_t* rp, int n, long long M, int* tile_row, cudaStream_t s,
                       int* launches);
 
+// Minimum degree and its vertex (smallest id) -> st->deg_val/deg_arg; lowers
+// st->lambda.  The degrees come with the CSR (build_csr).
 template <typename WT>
-cudaError_t degrees_min(const int64_t* rp, const WT* w, int n, WT* deg, unsigned long long* blk,
-                        DevState* st, cudaStream_t s, int* launches);
+cudaError_t degrees_min(const WT* deg, int n, unsigned long long* blk, DevState* st,
+                        cudaStream_t s, int* launches);
 
 template <typename WT>
 cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                        const int* L, int vbits, const int* tile_row, u64* keys, WT* vals,
                        DevState* st, int validate, cudaStream_t s, int* launches);
 
-// After sorting: unique keys -> canonical CSR (rp2[n2+1], col2, w2); the
-// number of unique entries goes to *m2_dev.  uid/part: N and N/4096+1 ints.
+// After sorting: unique keys -> canonical CSR (rp2[n2+1], col2, w2) and the
+// weighted degrees deg2[n2]; the number of unique entries goes to *m2_dev.
+// uid/part: N and N/4096+1 ints.
 template <typename WT>
 cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
-                      int* part, int64_t* rp2, int* col2, WT* w2, DevState* st, int* m2_dev,
-                      cudaStream_t s, int* launches);
+                      int* part, int64_t* rp2, int* col2, WT* w2, WT* deg2, DevState* st,
+                      int* m2_dev, cudaStream_t s, int* launches);
 
 template <typename WT>
 cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* col, const WT* w,
@@ -85,7 +88,9 @@ cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, cons
                      int* launches);
 
 // One label-propagation sweep (vertices with ((v ^ sweep) & 1) == 0 update).
-// Rows longer than 128 entries use tables of 2d slots from the pool.
+// Rows up to 128 entries use a warp table, up to 1024 a block table, longer
+// rows tables of 2d slots from the pool.  long_rows holds 2n ints and
+// long_count 2 ints of scratch.
 template <typename WT>
 cudaError_t lp_sweep(int n, const int64_t* rp, const int* col, const WT* w, const int* lab_in,
                      int* lab_out, int sweep, int* long_rows, int* long_count, int* pool_lab,

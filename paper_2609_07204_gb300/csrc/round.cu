@@ -113,21 +113,12 @@ __device__ __forceinline__ ValArg block_va_min(ValArg x) {
   return x;
 }
 
-// deg[v] = sum of w over row v (one warp per row); per-block (min, argmin).
+// Per-block (min, argmin) of the degrees deg[0..n) (computed with the CSR).
 template <typename WT>
-__global__ void degrees_kernel(const int64_t* __restrict__ rp, const WT* __restrict__ w, int n,
-                               WT* __restrict__ deg, unsigned long long* __restrict__ blk) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
+__global__ void degmin_kernel(const WT* __restrict__ deg, int n, unsigned long long* __restrict__ blk) {
   ValArg best{~0ull, 0x7fffffff};
-  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-    const long long b = rp[v], e = rp[v + 1];
-    long long s = 0;
-    for (long long i = b + lane; i < e; i += 32) s += (long long)w[i];
-    s = warp_sum(s);
-    if (lane == 0) deg[v] = (WT)s;
-    best = va_min(best, ValArg{(unsigned long long)s, v});
-  }
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    best = va_min(best, ValArg{(unsigned long long)(long long)deg[v], v});
   ValArg r = block_va_min(best);
   if (threadIdx.x == 0) {
     blk[2 * blockIdx.x] = r.v;
@@ -229,7 +220,7 @@ template <typename WT>
 __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict__ vals, int N,
                               const int* __restrict__ uid, int vbits, int n2,
                               const int* __restrict__ m2p, int64_t* __restrict__ rp2,
-                              int* __restrict__ col2, WT* __restrict__ w2) {
+                              int* __restrict__ col2, WT* __restrict__ w2, WT* __restrict__ deg2) {
   const u64 vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
   const long long nchunks = ((long long)N + 7) / 8;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
@@ -239,8 +230,17 @@ __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict
     long long acc = 0;
     bool run_started_here = false;
     int cur_uid = -1;
+    int du_row = -1;      // row whose degree is being accumulated
+    long long dacc = 0;
     for (long long i = i0; i < i1; ++i) {
       const u64 k = keys[i];
+      const int ku = (int)(k >> vbits);
+      if (ku != du_row) {
+        if (du_row >= 0) atomic_add_w(&deg2[du_row], (WT)dacc);
+        du_row = ku;
+        dacc = 0;
+      }
+      dacc += (long long)vals[i];
       const bool head = (i == 0) || (k != prev);
       if (head) {
         if (cur_uid >= 0) {
@@ -263,6 +263,7 @@ __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict
       acc += (long long)vals[i];
       prev = k;
     }
+    if (du_row >= 0) atomic_add_w(&deg2[du_row], (WT)dacc);
     if (cur_uid >= 0) {
       const bool run_ends_here = (i1 == N) || (keys[i1] != prev);
       if (run_started_here && run_ends_here) w2[cur_uid] = (WT)acc;
@@ -340,19 +341,28 @@ __global__ void __launch_bounds__(kETThreads)
     uint8_t f = 0;
     if ((mask & 1u) && c >= lam) f |= 1;
     if ((mask & 2u) && (du < 2 * c || dv < 2 * c)) f |= 2;
-    if (mask & 12u) {
+    if ((mask & 12u) && (flags_out || f == 0)) {
       const long long bu = rp[u], eu = rp[u + 1], bv = rp[v], ev = rp[v + 1];
       const long long lu = eu - bu, lv = ev - bv;
       if (budget < 0 || min(lu, lv) <= budget) {
         const bool a_is_u = lu <= lv;
         const long long ab = a_is_u ? bu : bv, ae = a_is_u ? eu : ev;
         const long long bb = a_is_u ? bv : bu, be = a_is_u ? ev : eu;
+        const long long da = a_is_u ? du : dv;
         long long sum = c;
         bool pr3 = false;
+        // Without a flags output only "some test passes" matters, so the scan
+        // stops once the answer is known: PR4 reached, PR3 found, or neither
+        // still possible (rem = weight of a's unscanned edges bounds the PR4
+        // sum still to come; PR3 needs a single edge heavier than da/2 - c).
+        long long rem = da - c;
+        const bool exact = flags_out != nullptr;
         long long lo = bb;
         for (long long ea = ab; ea < ae; ++ea) {
           const int x = col[ea];
           if (x == u || x == v) continue;
+          const long long cax = (long long)w[ea];
+          rem -= cax;
           // neighbours of the shorter row ascend, so the search window only
           // moves right
           long long hi = be;
@@ -361,11 +371,16 @@ __global__ void __launch_bounds__(kETThreads)
             if (col[mid] < x) lo = mid + 1; else hi = mid;
           }
           if (lo >= be) break;
-          if (col[lo] != x) continue;
-          const long long ca = (long long)w[ea], cb = (long long)w[lo];
-          const long long cux = a_is_u ? ca : cb, cvx = a_is_u ? cb : ca;
-          sum += cux < cvx ? cux : cvx;
-          if (du < 2 * (c + cux) && dv < 2 * (c + cvx)) pr3 = true;
+          if (col[lo] == x) {
+            const long long cbx = (long long)w[lo];
+            const long long cux = a_is_u ? cax : cbx, cvx = a_is_u ? cbx : cax;
+            sum += cux < cvx ? cux : cvx;
+            if (du < 2 * (c + cux) && dv < 2 * (c + cvx)) pr3 = true;
+          }
+          if (!exact) {
+            if (((mask & 8u) && sum >= lam) || ((mask & 4u) && pr3)) break;
+            if (sum + rem < lam && !((mask & 4u) && 2 * (c + rem) > da)) break;
+          }
         }
         if ((mask & 4u) && pr3) f |= 4;
         if ((mask & 8u) && sum >= lam) f |= 8;
@@ -386,6 +401,8 @@ __global__ void __launch_bounds__(kETThreads)
 constexpr int kLpShort = 128;       // rows up to this length use a warp table
 constexpr int kLpSlots = 256;       // slots of a warp table (power of two)
 constexpr int kLpWarps = 8;
+constexpr int kLpMedium = 1024;     // rows up to this length use a block table
+constexpr int kLpMidSlots = 2048;
 
 __device__ __forceinline__ unsigned lp_hash(int l) { return (unsigned)l * 0x9E3779B1u; }
 
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(kLpWarps * 32)
     lp_short_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
                     const WT* __restrict__ w, const int* __restrict__ lab_in,
                     int* __restrict__ lab_out, int sweep, int* __restrict__ long_rows,
-                    int* long_count) {
+                    int* long_count, int* __restrict__ mid_rows, int* mid_count) {
   __shared__ int s_key[kLpWarps][kLpSlots];
   __shared__ long long s_sc[kLpWarps][kLpSlots];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -436,7 +453,10 @@ __global__ void __launch_bounds__(kLpWarps * 32)
       continue;
     }
     if (d > kLpShort) {
-      if (lane == 0) long_rows[atomicAdd(long_count, 1)] = v;
+      if (lane == 0) {
+        if (d <= kLpMedium) mid_rows[atomicAdd(mid_count, 1)] = v;
+        else long_rows[atomicAdd(long_count, 1)] = v;
+      }
       continue;
     }
     for (int i = lane; i < kLpSlots; i += 32) { key[i] = -1; sc[i] = 0; }
@@ -467,6 +487,64 @@ __global__ void __launch_bounds__(kLpWarps * 32)
     own_s = warp_sum(own_s);
     if (lane == 0) lab_out[v] = (best.s > own_s) ? best.l : own;
     __syncwarp();
+  }
+}
+
+// Medium rows: one block per row with a shared-memory table of 2048 slots.
+template <typename WT>
+__global__ void __launch_bounds__(256)
+    lp_mid_kernel(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                  const WT* __restrict__ w, const int* __restrict__ lab_in,
+                  int* __restrict__ lab_out, const int* __restrict__ rows, const int* count) {
+  __shared__ int key[kLpMidSlots];
+  __shared__ long long sc[kLpMidSlots];
+  __shared__ long long s_bs[8];
+  __shared__ int s_bl[8];
+  __shared__ long long s_own[8];
+  const int cnt = *count;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = blockIdx.x; r < cnt; r += gridDim.x) {
+    const int v = rows[r];
+    const int own = lab_in[v];
+    const long long b = rp[v], e = rp[v + 1];
+    for (int i = threadIdx.x; i < kLpMidSlots; i += blockDim.x) { key[i] = -1; sc[i] = 0; }
+    __syncthreads();
+    for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+      const int l = lab_in[col[i]];
+      const long long c = (long long)w[i];
+      unsigned h = lp_hash(l) & (kLpMidSlots - 1);
+      for (int p = 0; p < kLpMidSlots; ++p) {
+        const int prev = atomicCAS(&key[h], -1, l);
+        if (prev == -1 || prev == l) {
+          atomicAdd((unsigned long long*)&sc[h], (unsigned long long)c);
+          break;
+        }
+        h = (h + 1) & (kLpMidSlots - 1);
+      }
+    }
+    __syncthreads();
+    LabScore best{-1, 0x7fffffff};
+    long long own_s = 0;
+    for (int i = threadIdx.x; i < kLpMidSlots; i += blockDim.x) {
+      const int l = key[i];
+      if (l < 0) continue;
+      best = ls_best(best, LabScore{sc[i], l});
+      if (l == own) own_s = sc[i];
+    }
+    best = warp_ls_best(best);
+    own_s = warp_sum(own_s);
+    if (lane == 0) { s_bs[warp] = best.s; s_bl[warp] = best.l; s_own[warp] = own_s; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      LabScore bb{-1, 0x7fffffff};
+      long long os = 0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+        bb = ls_best(bb, LabScore{s_bs[w2], s_bl[w2]});
+        os += s_own[w2];
+      }
+      lab_out[v] = (bb.s > os) ? bb.l : own;
+    }
+    __syncthreads();
   }
 }
 
@@ -551,32 +629,21 @@ __global__ void lp_long_kernel(const int64_t* __restrict__ rp, const int* __rest
   }
 }
 
-// Cluster cut values: cut[l] += w for every entry (u, v) with lab[u] = l != lab[v].
+// Cluster cut values: cut[l] += w for every entry (u, v) with lab[u] = l != lab[v]
+// (one warp per row, one atomic per row).
 template <typename WT>
-__global__ void __launch_bounds__(kETThreads)
-    lp_cut_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
-                  const WT* __restrict__ w, const int* __restrict__ lab,
-                  const int* __restrict__ tile_row, int ntiles, long long* __restrict__ cut) {
-  __shared__ TileRowsSmem tr;
-  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+__global__ void lp_cut_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                              const WT* __restrict__ w, const int* __restrict__ lab,
+                              long long* __restrict__ cut) {
   const int lane = threadIdx.x & 31;
-  const long long e0 = (long long)blockIdx.x * kET;
-  for (int i = 0; i < kETItems; ++i) {
-    const long long e = e0 + i * kETThreads + threadIdx.x;
-    int key = -1;
-    long long val = 0;
-    if (e < M) {
-      const int u = tile_row_of(tr, rp, e);
-      const int lu = lab[u];
-      if (lu != lab[col[e]]) { key = lu; val = (long long)w[e]; }
-    }
-    const unsigned peers = __match_any_sync(FULL, key);
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nwarps) {
+    const int lu = lab[u];
     long long s = 0;
-    for (int b2 = 0; b2 < 32; ++b2) {
-      long long x = __shfl_sync(FULL, val, b2);
-      if ((peers >> b2) & 1u) s += x;
-    }
-    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd((unsigned long long*)&cut[key], (unsigned long long)s);
+    for (long long e = rp[u] + lane; e < rp[u + 1]; e += 32)
+      if (lab[col[e]] != lu) s += (long long)w[e];
+    s = warp_sum(s);
+    if (lane == 0 && s) atomicAdd((unsigned long long*)&cut[lu], (unsigned long long)s);
   }
 }
 
@@ -722,10 +789,10 @@ cudaError_t tile_rows(const int64_t* rp, int n, long long M, int* tile_row, cuda
 }
 
 template <typename WT>
-cudaError_t degrees_min(const int64_t* rp, const WT* w, int n, WT* deg, unsigned long long* blk,
-                        DevState* st, cudaStream_t s, int* launches) {
-  const int nb = std::min(grid_for((long long)n * 32, 256), 1024);
-  degrees_kernel<WT><<<nb, 256, 0, s>>>(rp, w, n, deg, blk);
+cudaError_t degrees_min(const WT* deg, int n, unsigned long long* blk, DevState* st,
+                        cudaStream_t s, int* launches) {
+  const int nb = std::min(grid_for(n, 256), 1024);
+  degmin_kernel<WT><<<nb, 256, 0, s>>>(deg, n, blk);
   degmin_final_kernel<<<1, 1024, 0, s>>>(blk, nb, st);
   *launches += 2;
   return cudaGetLastError();
@@ -745,8 +812,9 @@ cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, co
 
 template <typename WT>
 cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
-                      int* part, int64_t* rp2, int* col2, WT* w2, DevState* st, int* m2_dev,
-                      cudaStream_t s, int* launches) {
+                      int* part, int64_t* rp2, int* col2, WT* w2, WT* deg2, DevState* st,
+                      int* m2_dev, cudaStream_t s, int* launches) {
+  cudaMemsetAsync(deg2, 0, (size_t)std::max(n2, 1) * sizeof(WT), s);
   if (N <= 0) {
     rp_fill_kernel<<<grid_for(n2 + 1, 256), 256, 0, s>>>(rp2, n2);
     cudaMemsetAsync(m2_dev, 0, sizeof(int), s);
@@ -759,7 +827,7 @@ cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2,
   if (err != cudaSuccess) return err;
   cudaMemsetAsync(w2, 0, (size_t)N * sizeof(WT), s);
   segsum_kernel<WT><<<grid_for((N + 7) / 8, 256), 256, 0, s>>>(keys, vals, N, uid, vbits, n2,
-                                                               m2_dev, rp2, col2, w2);
+                                                               m2_dev, rp2, col2, w2, deg2);
   ++*launches;
   return cudaGetLastError();
 }
@@ -792,14 +860,19 @@ cudaError_t lp_sweep(int n, const int64_t* rp, const int* col, const WT* w, cons
                      int* lab_out, int sweep, int* long_rows, int* long_count, int* pool_lab,
                      long long* pool_sc, long long pool_slots, unsigned long long* pool_cursor,
                      DevState* st, cudaStream_t s, int* launches) {
-  cudaMemsetAsync(long_count, 0, sizeof(int), s);
+  // long_count[0] counts long rows, long_count[1] medium rows; medium rows
+  // are listed from the end of long_rows (n entries) downwards.
+  int* mid_rows = long_rows + n;
+  cudaMemsetAsync(long_count, 0, 2 * sizeof(int), s);
   cudaMemsetAsync(pool_cursor, 0, sizeof(unsigned long long), s);
   lp_short_kernel<WT><<<grid_for((long long)n * 32, kLpWarps * 32), kLpWarps * 32, 0, s>>>(
-      n, rp, col, w, lab_in, lab_out, sweep, long_rows, long_count);
+      n, rp, col, w, lab_in, lab_out, sweep, long_rows, long_count, mid_rows, long_count + 1);
+  lp_mid_kernel<WT><<<num_sms() * 4, 256, 0, s>>>(rp, col, w, lab_in, lab_out, mid_rows,
+                                                  long_count + 1);
   lp_long_kernel<WT><<<num_sms() * 2, 512, 0, s>>>(rp, col, w, lab_in, lab_out, long_rows,
                                                    long_count, pool_lab, pool_sc, pool_slots,
                                                    pool_cursor, st);
-  *launches += 2;
+  *launches += 3;
   return cudaGetLastError();
 }
 
@@ -810,8 +883,8 @@ cudaError_t lp_bound(int n, long long M, const int64_t* rp, const int* col, cons
   cudaMemsetAsync(cut, 0, (size_t)n * sizeof(long long), s);
   cudaMemsetAsync(size, 0, (size_t)n * sizeof(int), s);
   if (M > 0) {
-    const int ntiles = (int)((M + kET - 1) / kET);
-    lp_cut_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, lab, tile_row, ntiles, cut);
+    lp_cut_kernel<WT><<<std::min(grid_for((long long)n * 32, 256), num_sms() * 64), 256, 0, s>>>(
+        n, rp, col, w, lab, cut);
     ++*launches;
   }
   lp_size_kernel<<<grid_for(n, 256), 256, 0, s>>>(lab, n, size);
@@ -897,13 +970,13 @@ cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream
 
 // ----------------------------------------------------- explicit instances
 #define MC_INST(WT)                                                                              \
-  template cudaError_t degrees_min<WT>(const int64_t*, const WT*, int, WT*, unsigned long long*, \
-                                       DevState*, cudaStream_t, int*);                           \
+  template cudaError_t degrees_min<WT>(const WT*, int, unsigned long long*, DevState*,           \
+                                       cudaStream_t, int*);                                      \
   template cudaError_t emit_pairs<WT>(int, long long, const int64_t*, const int*, const WT*,     \
                                       const int*, int, const int*, u64*, WT*, DevState*, int,    \
                                       cudaStream_t, int*);                                       \
   template cudaError_t build_csr<WT>(const u64*, const WT*, int, int, int, int*, int*, int64_t*, \
-                                     int*, WT*, DevState*, int*, cudaStream_t, int*);            \
+                                     int*, WT*, WT*, DevState*, int*, cudaStream_t, int*);       \
   template cudaError_t check_symmetric<WT>(int, long long, const int64_t*, const int*,           \
                                            const WT*, const int*, DevState*, cudaStream_t,       \
                                            int*);                                                \

@@ -256,6 +256,47 @@ def test_deterministic_round_bit_exact_with_pr_and_lp():
         assert_csr_equal(mc.mincut_graph_export_csr(g), (rp2, col2, w2))
 
 
+# --------------------------------------------------------- label propagation
+def _lp_case(c, n, iters):
+    g = make(n, c[0], c[1], c[2])
+    lab = np.full(n, -1, np.int32)
+    ro = mc.default_round_options()
+    ro.lp_iters = iters
+    ro.lp_min_n = 2
+    ro.pr_mask = 0
+    ro.capforest = 0
+    ro.lp_labels_out = lab.ctypes.data
+    res = mc.mincut_contract_round(g, ro)
+    assert not res["stopped"]
+    exp = oracle.lp(n, *c, iters)
+    assert np.array_equal(lab, exp)
+    deg = oracle.degrees(n, *c)
+    val, _ = oracle.lp_bound(n, *c, exp)
+    assert res["lambda_out"] == min(int(deg.min()), val)
+
+
+def test_lp_labels_bit_exact_short_rows():
+    rng = np.random.default_rng(81)
+    for trial in range(6):
+        n = int(rng.integers(50, 3000))
+        s = synth.er_connected(n, int(n * rng.uniform(2, 6)), 1, int(rng.integers(1, 20)), trial)
+        _lp_case((s.row_ptr, s.col, s.w.astype(np.int64)), n, int(rng.integers(1, 5)))
+
+
+def test_lp_labels_bit_exact_medium_and_long_rows():
+    # R-MAT cores have rows of every length class (warp, block, pooled tables)
+    s = synth.workload_rmat_core(scale=15, k=8, seed=9)
+    d = np.diff(s.row_ptr)
+    assert d.max() > 1024 and ((d > 128) & (d <= 1024)).any()
+    for iters in (1, 2, 3):
+        _lp_case((s.row_ptr, s.col, s.w.astype(np.int64)), s.n, iters)
+
+
+def test_lp_two_communities_bound():
+    s = synth.planted(1 << 10, 21 << 10, 30, 3, 1, 7)
+    _lp_case((s.row_ptr, s.col, s.w.astype(np.int64)), s.n, 8)
+
+
 # ---------------------------------------------------------- concurrent passes
 def test_concurrent_round_sound_brute_force():
     rng = np.random.default_rng(51)
