@@ -192,6 +192,32 @@ typedef struct mincut_profile_entry {
 int mincut_profile_read(mincut_graph* g, mincut_profile_entry* out, int32_t cap, int32_t* count,
                         int32_t reset);
 
+/* Contraction without device allocation.  The paper has no counterpart: this
+ * entry point serves callers that cannot allocate device memory -- a plug-in
+ * inside a host application that owns the whole device pool, or a
+ * latency-critical loop that cannot afford cudaMalloc's latency and implicit
+ * synchronisation.  It contracts a device CSR (row_ptr[n+1], col[M], w[M],
+ * M = m_directed = row_ptr[n]; symmetric, weights >= 0, total weight < 2^31)
+ * by caller-given labels (labels[v] in [0, n2) names v's contracted vertex)
+ * and writes the canonical contracted CSR: row_ptr_out[n2+1], col_out and
+ * w_out with capacity M (all device pointers); *m_out (host) gets its number
+ * of entries.  Rows are numbered by label, sorted by neighbour, parallel
+ * edges summed, self-loops and zero weights dropped -- the same result as
+ * mincut_contract_round with groups = labels when the labels are numbered
+ * by increasing smallest member.
+ * Limits: n and M at most 262,144 (MINCUT_ERR_OVERFLOW beyond).  All
+ * intermediate data lives in one fixed ~8.2 MB device array inside the
+ * library, held by every GPU that loads it until the process exits; the
+ * library allocates nothing on this path.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Calls share the array, so calls that
+ * overlap on the GPU race: serialise them.  Stream-ordered on cuda_stream;
+ * returns after the work finished. */
+int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                const int32_t* w, int64_t m_directed, const int32_t* labels,
+                                int64_t n2, int64_t* row_ptr_out, int32_t* col_out,
+                                int32_t* w_out, int64_t* m_out, void* cuda_stream);
+
 /* Static description of a status code. */
 const char* mincut_status_string(int status);
 

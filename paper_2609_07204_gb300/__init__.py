@@ -145,6 +145,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mincut_profile_read.argtypes = [vp, ctypes.POINTER(MincutProfileEntry), i32,
                                         ctypes.POINTER(i32), i32]
     lib.mincut_profile_read.restype = ctypes.c_int
+    lib.mincut_contract_csr_noalloc.argtypes = [i64, vp, vp, vp, i64, vp, i64, vp, vp, vp,
+                                                ctypes.POINTER(i64), vp]
+    lib.mincut_contract_csr_noalloc.restype = ctypes.c_int
     if path is None:
         _lib = lib
     return lib
@@ -342,6 +345,26 @@ def mincut_profile_read(g: Graph, reset: bool = False) -> dict:
     _check(lib.mincut_profile_read(g.handle, buf, 32, ctypes.byref(cnt), 1 if reset else 0))
     return {buf[i].name.decode(): {"launches": int(buf[i].launches), "units": int(buf[i].units),
                                    "ms": float(buf[i].ms)} for i in range(cnt.value)}
+
+
+def mincut_contract_csr_noalloc(n: int, row_ptr, col, w, labels, n2: int, row_ptr_out, col_out,
+                                w_out, *, stream: Any = None) -> int:
+    """Contract a device CSR (torch CUDA tensors) by labels without any device
+    allocation inside the library; the caller supplies the output tensors
+    (row_ptr_out int64[n2+1], col_out/w_out int32 with capacity M).  Returns
+    the number of entries written.  See include/mincut.h for the limits."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(row_ptr.device).cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    m = ctypes.c_int64(0)
+    M = int(col.numel())
+    _check(load_library().mincut_contract_csr_noalloc(
+        n, row_ptr.data_ptr(), col.data_ptr(), w.data_ptr(), M, labels.data_ptr(), n2,
+        row_ptr_out.data_ptr(), col_out.data_ptr(), w_out.data_ptr(), ctypes.byref(m),
+        ctypes.c_void_p(stream or 0)))
+    return int(m.value)
 
 
 def mincut_status_string(status: int) -> str:

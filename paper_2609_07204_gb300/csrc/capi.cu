@@ -162,6 +162,7 @@ struct mincut_graph {
 };
 
 namespace mc {
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 Profiler* prof_create();
 void prof_destroy(Profiler* p);
 void prof_flush(Profiler* p);

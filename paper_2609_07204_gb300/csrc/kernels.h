@@ -11,6 +11,9 @@ namespace mc {
 
 using u64 = unsigned long long;
 
+// Message returned by mincut_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // ------------------------------------------------------------ profiling
 // Optional per-kernel timing: when a Profiler is installed on the calling
 // thread, every launcher brackets its kernels with CUDA events on the launch
