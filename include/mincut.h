@@ -206,7 +206,7 @@ int mincut_profile_read(mincut_graph* g, mincut_profile_entry* out, int32_t cap,
  * mincut_contract_round with groups = labels when the labels are numbered
  * by increasing smallest member.
  * Limits: n and M at most 262,144 (MINCUT_ERR_OVERFLOW beyond).  All
- * intermediate data lives in one fixed ~8.2 MB device array inside the
+ * intermediate data lives in one fixed ~7.2 MB device array inside the
  * library, held by every GPU that loads it until the process exits; the
  * library allocates nothing on this path.  The first call on a device looks
  * up that array's device address (cudaGetSymbolAddress); make that first

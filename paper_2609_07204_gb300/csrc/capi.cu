@@ -131,6 +131,9 @@ struct mincut_graph {
   u64* bitmap_dev = nullptr;
   // label propagation (allocated on first use)
   int* lab[2]{};
+  int* lp_chunk0 = nullptr;
+  long long* lp_tbase = nullptr;
+  unsigned long long* lp_best = nullptr;
   long long* lp_cut = nullptr;
   int *lp_size = nullptr, *long_rows = nullptr, *long_count = nullptr, *pool_lab = nullptr;
   long long* pool_sc = nullptr;
@@ -256,7 +259,9 @@ int ensure_lp(mincut_graph* g) {
   g->pool_slots = 2 * std::max<long long>(g->M0, 1);
   if (!galloc(g, &g->lab[0], g->n0) || !galloc(g, &g->lab[1], g->n0) ||
       !galloc(g, &g->lp_cut, g->n0) || !galloc(g, &g->lp_size, g->n0) ||
-      !galloc(g, &g->long_rows, 2ll * g->n0) || !galloc(g, &g->long_count, 2) ||
+      !galloc(g, &g->long_rows, 2ll * g->n0) || !galloc(g, &g->long_count, 4) ||
+      !galloc(g, &g->lp_chunk0, g->n0) || !galloc(g, &g->lp_tbase, g->n0) ||
+      !galloc(g, &g->lp_best, g->n0) ||
       !galloc(g, &g->pool_lab, g->pool_slots) || !galloc(g, &g->pool_sc, g->pool_slots) ||
       !galloc(g, &g->pool_cursor, 1))
     return fail(MINCUT_ERR_OOM, "label propagation buffers");
@@ -289,8 +294,8 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   const int nxt = g->cur == 0 ? 1 : 0;
   { ProfScope ps(P_BUILD, N, s);
     CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
-                     vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt],
-                     (WT*)g->degb[nxt], g->st, g->m2_dev, s, &g->launches)); }
+                     vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], g->st,
+                     g->m2_dev, s, &g->launches)); }
   if (compose) {
     ProfScope ps(P_UF, g->n0, s);
     CK(compose_map(g->map0, g->L, g->n0, s, &g->launches));
@@ -299,6 +304,9 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   rc = sync_state(g);
   if (rc) return rc;
+  { ProfScope ps(P_DEGREE, m2, s);
+    CK(row_degrees<WT>(n2, m2, g->rp[nxt], (const WT*)g->w[nxt], g->tile_row, (WT*)g->degb[nxt], s,
+                       &g->launches)); }
   g->cur = nxt;
   g->n = n2;
   g->M = m2;
@@ -370,13 +378,22 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   if (c.lp_now && c.lp_iters > 0 && n >= c.lp_min_n) {
     rc = ensure_lp(g);
     if (rc) return rc;
-    iota_kernel<<<std::min((n + 255) / 256, g->sms * 8), 256, 0, s>>>(g->lab[0], n);
-    ++g->launches;
     for (int it = 0; it < c.lp_iters; ++it) {
       ProfScope ps(P_LP_SWEEP, M, s);
-      CK(lp_sweep<WT>(n, rp, col, w, g->lab[it & 1], g->lab[(it + 1) & 1], it, g->long_rows,
-                      g->long_count, g->pool_lab, g->pool_sc, g->pool_slots, g->pool_cursor,
-                      g->st, s, &g->launches));
+      if (it == 0 && sizeof(WT) == 4) {  // identity labels: heaviest-neighbour sweep
+        CK(lp_first_sweep<WT>(n, M, rp, col, w, g->tile_row, 0,
+                              reinterpret_cast<unsigned long long*>(g->lp_cut), g->lab[1], s,
+                              &g->launches));
+        continue;
+      }
+      if (it == 0) {
+        iota_kernel<<<std::min((n + 255) / 256, g->sms * 8), 256, 0, s>>>(g->lab[0], n);
+        ++g->launches;
+      }
+      LpScratch sc{g->long_rows, g->long_count, g->lp_chunk0, g->lp_tbase, g->lp_best,
+                   g->pool_lab, g->pool_sc, g->pool_slots, g->pool_cursor};
+      CK(lp_sweep<WT>(n, rp, col, w, g->lab[it & 1], g->lab[(it + 1) & 1], it, sc, g->st, s,
+                      &g->launches));
     }
     lab_final = g->lab[c.lp_iters & 1];
     ProfScope ps(P_LP_BOUND, M, s);
@@ -638,13 +655,15 @@ int canonicalize_input(mincut_graph* g, int n, long long Mraw, bool validate) {
   CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
                           2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
   CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
-                   vbits, n, g->uid, g->part, g->rp[0], g->col[0], (WT*)g->w[0], (WT*)g->deg0,
-                   g->st, g->m2_dev, s, &g->launches));
+                   vbits, n, g->uid, g->part, g->rp[0], g->col[0], (WT*)g->w[0], g->st,
+                   g->m2_dev, s, &g->launches));
   int m2 = 0;
   CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   rc = sync_state(g);
   if (rc) return rc;
   g->M0 = m2;
+  CK(row_degrees<WT>(n, m2, g->rp[0], (const WT*)g->w[0], g->tile_row, (WT*)g->deg0, s,
+                     &g->launches));
   if (validate && m2 > 0) {
     CK(tile_rows(g->rp[0], n, m2, g->tile_row, s, &g->launches));
     CK(check_symmetric<WT>(n, m2, g->rp[0], g->col[0], (const WT*)g->w[0], g->tile_row, g->st, s,

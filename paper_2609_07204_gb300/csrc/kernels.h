@@ -39,6 +39,8 @@ struct ProfScope {
 // the keys, 8 bits per pass.  Ping-pongs between (k0, v0) and (k1, v1);
 // returns in *in_alt whether the result ended in (k1, v1).  hist and goff
 // hold 8*256 unsigned, lookback sort_lookback_words(N) u64.
+constexpr int kSortTile = 3072;  // keys per onesweep tile (256 threads x 12)
+
 struct SortScratch {
   unsigned* hist;
   unsigned* goff;
@@ -72,13 +74,12 @@ cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, co
                        const int* L, int vbits, const int* tile_row, u64* keys, WT* vals,
                        DevState* st, int validate, cudaStream_t s, int* launches);
 
-// After sorting: unique keys -> canonical CSR (rp2[n2+1], col2, w2) and the
-// weighted degrees deg2[n2]; the number of unique entries goes to *m2_dev.
-// uid/part: N and N/4096+1 ints.
+// After sorting: unique keys -> canonical CSR (rp2[n2+1], col2, w2); the
+// number of unique entries goes to *m2_dev.  uid/part: N and N/4096+1 ints.
 template <typename WT>
 cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
-                      int* part, int64_t* rp2, int* col2, WT* w2, WT* deg2, DevState* st,
-                      int* m2_dev, cudaStream_t s, int* launches);
+                      int* part, int64_t* rp2, int* col2, WT* w2, DevState* st, int* m2_dev,
+                      cudaStream_t s, int* launches);
 
 template <typename WT>
 cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* col, const WT* w,
@@ -91,14 +92,36 @@ cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, cons
                      int* launches);
 
 // One label-propagation sweep (vertices with ((v ^ sweep) & 1) == 0 update).
-// Rows up to 128 entries use a warp table, up to 1024 a block table, longer
-// rows tables of 2d slots from the pool.  long_rows holds 2n ints and
-// long_count 2 ints of scratch.
+// Rows up to 128 entries use a warp table, up to 4096 a block table, longer
+// rows tables of 2d slots from the pool, split into 4096-entry chunks over
+// many blocks.
+struct LpScratch {
+  int* long_rows;               // 2n ints: long-row list, then medium-row list
+  int* counts;                  // 4 ints
+  int* chunk0;                  // n ints
+  long long* tbase;             // n
+  unsigned long long* best;     // n
+  int* pool_lab;                // pool_slots (>= 2M)
+  long long* pool_sc;           // pool_slots
+  long long pool_slots;
+  unsigned long long* pool_cursor;
+};
 template <typename WT>
 cudaError_t lp_sweep(int n, const int64_t* rp, const int* col, const WT* w, const int* lab_in,
-                     int* lab_out, int sweep, int* long_rows, int* long_count, int* pool_lab,
-                     long long* pool_sc, long long pool_slots, unsigned long long* pool_cursor,
-                     DevState* st, cudaStream_t s, int* launches);
+                     int* lab_out, int sweep, const LpScratch& sc, DevState* st, cudaStream_t s,
+                     int* launches);
+
+// First LP sweep from identity labels (vertices of parity `sweep` adopt their
+// heaviest neighbour, ties to the smaller id).  best: n u64 of scratch.
+template <typename WT>
+cudaError_t lp_first_sweep(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                           const int* tile_row, int sweep, unsigned long long* best, int* lab_out,
+                           cudaStream_t s, int* launches);
+
+// deg[u] = sum of the weights of row u (recomputes tile_row for this CSR).
+template <typename WT>
+cudaError_t row_degrees(int n, long long M, const int64_t* rp, const WT* w, int* tile_row,
+                        WT* deg, cudaStream_t s, int* launches);
 
 // Minimum cut value over the proper clusters of `lab` -> st->lp_val/lp_label.
 template <typename WT>

@@ -35,18 +35,17 @@ constexpr size_t kOffKeys1 = kOffKeys0 + a256(kNaMaxEntries * 8);
 constexpr size_t kOffVals0 = kOffKeys1 + a256(kNaMaxEntries * 8);
 constexpr size_t kOffVals1 = kOffVals0 + a256(kNaMaxEntries * 4);
 constexpr size_t kOffUid = kOffVals1 + a256(kNaMaxEntries * 4);
-constexpr size_t kOffDeg = kOffUid + a256(kNaMaxEntries * 4);
 constexpr size_t kTiles = kNaMaxEntries / kEntryTile + 2;
-constexpr size_t kOffTiles = kOffDeg + a256(kNaMaxVertices * 4);
+constexpr size_t kOffTiles = kOffUid + a256(kNaMaxEntries * 4);
 constexpr size_t kParts = (kNaMaxEntries > kNaMaxVertices ? kNaMaxEntries : kNaMaxVertices) / 4096 + 2;
 constexpr size_t kOffPart = kOffTiles + a256(kTiles * 4);
-constexpr size_t kLookWords = (kNaMaxEntries / 4096 + 2) * 256;
+constexpr size_t kLookWords = (kNaMaxEntries / kSortTile + 2) * 256;
 constexpr size_t kOffLook = kOffPart + a256(kParts * 4);
 constexpr size_t kOffHist = kOffLook + a256(kLookWords * 8);
 constexpr size_t kOffGoff = kOffHist + a256(8 * 256 * 4);
 constexpr size_t kOffState = kOffGoff + a256(8 * 256 * 4);
 constexpr size_t kOffM2 = kOffState + a256(sizeof(DevState));
-constexpr size_t kScratchBytes = kOffM2 + 256;  // about 8.2 MB
+constexpr size_t kScratchBytes = kOffM2 + 256;  // about 7.2 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -109,7 +108,6 @@ int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t
   int32_t* vals0 = reinterpret_cast<int32_t*>(base + kOffVals0);
   int32_t* vals1 = reinterpret_cast<int32_t*>(base + kOffVals1);
   int* uid = reinterpret_cast<int*>(base + kOffUid);
-  int32_t* deg = reinterpret_cast<int32_t*>(base + kOffDeg);
   int* tiles = reinterpret_cast<int*>(base + kOffTiles);
   int* part = reinterpret_cast<int*>(base + kOffPart);
   SortScratch sc;
@@ -142,8 +140,7 @@ int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t
   if (radix_sort_pairs<int32_t>(keys0, vals0, keys1, vals1, (int)N, 2 * vbits, sc, st,
                                 1ll << 22, s, &alt, &launches) != cudaSuccess ||
       build_csr<int32_t>(alt ? keys1 : keys0, alt ? vals1 : vals0, (int)N, vbits, n2i, uid, part,
-                         row_ptr_out, col_out, w_out, deg, st, m2_dev, s,
-                         &launches) != cudaSuccess)
+                         row_ptr_out, col_out, w_out, st, m2_dev, s, &launches) != cudaSuccess)
     return na_fail(MINCUT_ERR_CUDA, "launch failed (sort/build)");
   int m2 = 0;
   if (cudaMemcpyAsync(&m2, m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -68,6 +68,43 @@ __device__ __forceinline__ int tile_row_of(const TileRowsSmem& s, const int64_t*
   return s.use ? s.r0 + row_in(s.rp, 0, s.r1 - s.r0 + 1, e) : row_in(rp, s.r0, s.r1 + 1, e);
 }
 
+// Warp-level segmented sum over 32 consecutive entries whose segment keys
+// (row ids) are non-decreasing across lanes; the last lane of each segment
+// adds the segment's total to out[target].  Lanes with valid == false must
+// come after all valid lanes (tile tails).
+template <typename T, typename O>
+__device__ __forceinline__ void warp_segment_add(int seg, int target, T val, bool valid, O* out) {
+  const int lane = threadIdx.x & 31;
+  T x = valid ? val : T(0);
+  const int r = valid ? seg : -1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(FULL, x, o);
+    const int ry = __shfl_up_sync(FULL, r, o);
+    if (lane >= o && ry == r) x += y;
+  }
+  const int rn = __shfl_down_sync(FULL, r, 1);
+  const bool last = lane == 31 || rn != r;
+  if (valid && last && x != T(0)) atomic_add_w(&out[target], (O)x);
+}
+
+// Warp-level segmented maximum of packed 64-bit values (same layout rules).
+__device__ __forceinline__ void warp_segment_max(int seg, unsigned long long val, bool valid,
+                                                 unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long x = valid ? val : 0ull;
+  const int r = valid ? seg : -1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, x, o);
+    const int ry = __shfl_up_sync(FULL, r, o);
+    if (lane >= o && ry == r && y > x) x = y;
+  }
+  const int rn = __shfl_down_sync(FULL, r, 1);
+  const bool last = lane == 31 || rn != r;
+  if (valid && last && x) atomicMax(&out[seg], x);
+}
+
 __global__ void tile_rows_kernel(const int64_t* __restrict__ rp, int n, int* __restrict__ tile_row) {
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
     long long b = rp[u], e = rp[u + 1];
@@ -220,7 +257,7 @@ template <typename WT>
 __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict__ vals, int N,
                               const int* __restrict__ uid, int vbits, int n2,
                               const int* __restrict__ m2p, int64_t* __restrict__ rp2,
-                              int* __restrict__ col2, WT* __restrict__ w2, WT* __restrict__ deg2) {
+                              int* __restrict__ col2, WT* __restrict__ w2) {
   const u64 vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
   const long long nchunks = ((long long)N + 7) / 8;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
@@ -230,17 +267,8 @@ __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict
     long long acc = 0;
     bool run_started_here = false;
     int cur_uid = -1;
-    int du_row = -1;      // row whose degree is being accumulated
-    long long dacc = 0;
     for (long long i = i0; i < i1; ++i) {
       const u64 k = keys[i];
-      const int ku = (int)(k >> vbits);
-      if (ku != du_row) {
-        if (du_row >= 0) atomic_add_w(&deg2[du_row], (WT)dacc);
-        du_row = ku;
-        dacc = 0;
-      }
-      dacc += (long long)vals[i];
       const bool head = (i == 0) || (k != prev);
       if (head) {
         if (cur_uid >= 0) {
@@ -263,7 +291,6 @@ __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict
       acc += (long long)vals[i];
       prev = k;
     }
-    if (du_row >= 0) atomic_add_w(&deg2[du_row], (WT)dacc);
     if (cur_uid >= 0) {
       const bool run_ends_here = (i1 == N) || (keys[i1] != prev);
       if (run_started_here && run_ends_here) w2[cur_uid] = (WT)acc;
@@ -274,6 +301,27 @@ __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict
       const int m2 = *m2p;
       for (int r = cu + 1; r <= n2; ++r) rp2[r] = m2;
     }
+  }
+}
+
+// deg[u] = sum of w over row u (entry tiles, warp segmented sums).
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    degree_kernel(int n, long long M, const int64_t* __restrict__ rp, const WT* __restrict__ w,
+                  const int* __restrict__ tile_row, int ntiles, WT* __restrict__ deg) {
+  __shared__ TileRowsSmem tr;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  const long long e0 = (long long)blockIdx.x * kET;
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    const bool valid = e < M;
+    int u = 0;
+    long long val = 0;
+    if (valid) {
+      u = tile_row_of(tr, rp, e);
+      val = (long long)w[e];
+    }
+    warp_segment_add<long long, WT>(u, u, val, valid, deg);
   }
 }
 
@@ -344,7 +392,12 @@ __global__ void __launch_bounds__(kETThreads)
     if ((mask & 12u) && (flags_out || f == 0)) {
       const long long bu = rp[u], eu = rp[u + 1], bv = rp[v], ev = rp[v + 1];
       const long long lu = eu - bu, lv = ev - bv;
-      if (budget < 0 || min(lu, lv) <= budget) {
+      // Without a flags output an edge whose endpoints are already joined in
+      // the union-find (by marks hooked so far) cannot change the contraction:
+      // skip its intersection.
+      const bool joined = !flags_out && (budget < 0 || min(lu, lv) <= budget) &&
+                          uf_find(parent, u) == uf_find(parent, v);
+      if (!joined && (budget < 0 || min(lu, lv) <= budget)) {
         const bool a_is_u = lu <= lv;
         const long long ab = a_is_u ? bu : bv, ae = a_is_u ? eu : ev;
         const long long bb = a_is_u ? bv : bu, be = a_is_u ? ev : eu;
@@ -401,8 +454,8 @@ __global__ void __launch_bounds__(kETThreads)
 constexpr int kLpShort = 128;       // rows up to this length use a warp table
 constexpr int kLpSlots = 256;       // slots of a warp table (power of two)
 constexpr int kLpWarps = 8;
-constexpr int kLpMedium = 1024;     // rows up to this length use a block table
-constexpr int kLpMidSlots = 2048;
+constexpr int kLpMedium = 4096;     // rows up to this length use a block table
+constexpr int kLpMidSlots = 8192;
 
 __device__ __forceinline__ unsigned lp_hash(int l) { return (unsigned)l * 0x9E3779B1u; }
 
@@ -490,14 +543,15 @@ __global__ void __launch_bounds__(kLpWarps * 32)
   }
 }
 
-// Medium rows: one block per row with a shared-memory table of 2048 slots.
+// Medium rows: one block per row with a shared-memory table of 8192 slots.
 template <typename WT>
 __global__ void __launch_bounds__(256)
     lp_mid_kernel(const int64_t* __restrict__ rp, const int* __restrict__ col,
                   const WT* __restrict__ w, const int* __restrict__ lab_in,
                   int* __restrict__ lab_out, const int* __restrict__ rows, const int* count) {
-  __shared__ int key[kLpMidSlots];
-  __shared__ long long sc[kLpMidSlots];
+  extern __shared__ __align__(16) unsigned char lp_smem[];
+  long long* sc = reinterpret_cast<long long*>(lp_smem);
+  int* key = reinterpret_cast<int*>(sc + kLpMidSlots);
   __shared__ long long s_bs[8];
   __shared__ int s_bl[8];
   __shared__ long long s_own[8];
@@ -507,25 +561,27 @@ __global__ void __launch_bounds__(256)
     const int v = rows[r];
     const int own = lab_in[v];
     const long long b = rp[v], e = rp[v + 1];
-    for (int i = threadIdx.x; i < kLpMidSlots; i += blockDim.x) { key[i] = -1; sc[i] = 0; }
+    int slots = 256;  // smallest power of two >= 2d
+    while (slots < 2 * (e - b) && slots < kLpMidSlots) slots <<= 1;
+    for (int i = threadIdx.x; i < slots; i += blockDim.x) { key[i] = -1; sc[i] = 0; }
     __syncthreads();
     for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
       const int l = lab_in[col[i]];
       const long long c = (long long)w[i];
-      unsigned h = lp_hash(l) & (kLpMidSlots - 1);
-      for (int p = 0; p < kLpMidSlots; ++p) {
+      unsigned h = lp_hash(l) & (slots - 1);
+      for (int p = 0; p < slots; ++p) {
         const int prev = atomicCAS(&key[h], -1, l);
         if (prev == -1 || prev == l) {
           atomicAdd((unsigned long long*)&sc[h], (unsigned long long)c);
           break;
         }
-        h = (h + 1) & (kLpMidSlots - 1);
+        h = (h + 1) & (slots - 1);
       }
     }
     __syncthreads();
     LabScore best{-1, 0x7fffffff};
     long long own_s = 0;
-    for (int i = threadIdx.x; i < kLpMidSlots; i += blockDim.x) {
+    for (int i = threadIdx.x; i < slots; i += blockDim.x) {
       const int l = key[i];
       if (l < 0) continue;
       best = ls_best(best, LabScore{sc[i], l});
@@ -545,6 +601,41 @@ __global__ void __launch_bounds__(256)
       lab_out[v] = (bb.s > os) ? bb.l : own;
     }
     __syncthreads();
+  }
+}
+
+// First sweep from identity labels: all labels differ, so the weight of a
+// neighbour label at v is the single edge weight; v (with ((v ^ sweep) & 1)
+// == 0) adopts the neighbour of largest edge weight, ties to the smaller id
+// (its own label has weight 0: there are no self-loops).  Entry tiles with a
+// segmented maximum of (w << 32 | ~col) per row; requires w < 2^32.
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    lp_first_kernel(int n, long long M, const int64_t* __restrict__ rp,
+                    const int* __restrict__ col, const WT* __restrict__ w,
+                    const int* __restrict__ tile_row, int ntiles, int sweep,
+                    unsigned long long* __restrict__ best) {
+  __shared__ TileRowsSmem tr;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  const long long e0 = (long long)blockIdx.x * kET;
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    bool valid = e < M;
+    int u = 0;
+    unsigned long long key = 0;
+    if (valid) {
+      u = tile_row_of(tr, rp, e);
+      key = ((unsigned long long)(unsigned)w[e] << 32) | (0xffffffffu - (unsigned)col[e]);
+    }
+    warp_segment_max(u, key, valid && (((u ^ sweep) & 1) == 0), best);
+  }
+}
+
+__global__ void lp_first_finish_kernel(int n, const unsigned long long* __restrict__ best,
+                                       int* __restrict__ lab_out) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const unsigned long long b = best[v];
+    lab_out[v] = b ? (int)(0xffffffffu - (unsigned)(b & 0xffffffffull)) : v;
   }
 }
 
@@ -629,21 +720,202 @@ __global__ void lp_long_kernel(const int64_t* __restrict__ rp, const int* __rest
   }
 }
 
-// Cluster cut values: cut[l] += w for every entry (u, v) with lab[u] = l != lab[v]
-// (one warp per row, one atomic per row).
+// ---- long rows split across blocks (rows longer than kLpMedium entries) ----
+// Each long row r owns a table of 2 d_r slots in the pool and ceil(d_r / kLpChunk)
+// chunks of work; chunk0[r] / tbase[r] are exclusive prefix sums over the
+// long rows.  Blocks walk the chunks; a block finds its row by binary search.
+constexpr int kLpChunk = 4096;
+
+__global__ void lp_long_prep_kernel(const int64_t* __restrict__ rp, const int* __restrict__ rows,
+                                    const int* count, int* __restrict__ chunk0,
+                                    long long* __restrict__ tbase, int* tot_chunks) {
+  __shared__ int s_w[32];
+  __shared__ long long s_wl[32];
+  __shared__ int s_c;
+  __shared__ long long s_t;
+  const int K = *count;
+  if (threadIdx.x == 0) { s_c = 0; s_t = 0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < K; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    int c = 0;
+    long long t = 0;
+    if (i < K) {
+      const long long d = rp[rows[i] + 1] - rp[rows[i]];
+      c = (int)((d + kLpChunk - 1) / kLpChunk);
+      t = 2 * d;
+    }
+    int xc = c;
+    long long xt = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yc = __shfl_up_sync(FULL, xc, o);
+      const long long yt = __shfl_up_sync(FULL, xt, o);
+      if (lane >= o) { xc += yc; xt += yt; }
+    }
+    if (lane == 31) { s_w[warp] = xc; s_wl[warp] = xt; }
+    __syncthreads();
+    int ac = 0;
+    long long at = 0, tc = 0, tt = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+      if (w2 < warp) { ac += s_w[w2]; at += s_wl[w2]; }
+      tc += s_w[w2];
+      tt += s_wl[w2];
+    }
+    const int cb = s_c;
+    const long long tb = s_t;
+    if (i < K) {
+      chunk0[i] = cb + ac + xc - c;
+      tbase[i] = tb + at + xt - t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { s_c = cb + (int)tc; s_t = tb + tt; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *tot_chunks = s_c;
+}
+
+__device__ __forceinline__ int chunk_row(const int* chunk0, int K, int b) {
+  int lo = 0, hi = K;  // largest r with chunk0[r] <= b
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (chunk0[mid] <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void lp_long_clear_kernel(const int64_t* __restrict__ rp, const int* __restrict__ rows,
+                                     const int* count, const int* __restrict__ chunk0,
+                                     const long long* __restrict__ tbase, const int* tot_chunks,
+                                     int* pool_lab, long long* pool_sc) {
+  const int K = *count, T = *tot_chunks;
+  for (int b = blockIdx.x; b < T; b += gridDim.x) {
+    const int r = chunk_row(chunk0, K, b);
+    const long long slots = 2 * (rp[rows[r] + 1] - rp[rows[r]]);
+    const long long s0 = (long long)(b - chunk0[r]) * 2 * kLpChunk;
+    const long long s1 = min(s0 + 2 * kLpChunk, slots);
+    for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+      pool_lab[tbase[r] + i] = -1;
+      pool_sc[tbase[r] + i] = 0;
+    }
+  }
+}
+
 template <typename WT>
-__global__ void lp_cut_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
-                              const WT* __restrict__ w, const int* __restrict__ lab,
-                              long long* __restrict__ cut) {
-  const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nwarps) {
-    const int lu = lab[u];
-    long long s = 0;
-    for (long long e = rp[u] + lane; e < rp[u + 1]; e += 32)
-      if (lab[col[e]] != lu) s += (long long)w[e];
-    s = warp_sum(s);
-    if (lane == 0 && s) atomicAdd((unsigned long long*)&cut[lu], (unsigned long long)s);
+__global__ void lp_long_insert_kernel(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                                      const WT* __restrict__ w, const int* __restrict__ lab_in,
+                                      const int* __restrict__ rows, const int* count,
+                                      const int* __restrict__ chunk0,
+                                      const long long* __restrict__ tbase, const int* tot_chunks,
+                                      int* pool_lab, long long* pool_sc) {
+  const int K = *count, T = *tot_chunks;
+  for (int b = blockIdx.x; b < T; b += gridDim.x) {
+    const int r = chunk_row(chunk0, K, b);
+    const int v = rows[r];
+    const long long rb = rp[v], d = rp[v + 1] - rb;
+    const long long slots = 2 * d;
+    int* key = pool_lab + tbase[r];
+    long long* sc = pool_sc + tbase[r];
+    const long long e0 = rb + (long long)(b - chunk0[r]) * kLpChunk;
+    const long long e1 = min(e0 + kLpChunk, rb + d);
+    for (long long i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+      const int l = lab_in[col[i]];
+      const long long c = (long long)w[i];
+      long long h = (long long)(lp_hash(l) % (unsigned long long)slots);
+      for (long long p = 0; p < slots; ++p) {
+        const int prev = atomicCAS(&key[h], -1, l);
+        if (prev == -1 || prev == l) {
+          atomicAdd((unsigned long long*)&sc[h], (unsigned long long)c);
+          break;
+        }
+        h = (h + 1 == slots) ? 0 : h + 1;
+      }
+    }
+  }
+}
+
+// Best (score, smaller label) of each long row's table as score << 32 | ~label.
+__global__ void lp_long_scan_kernel(const int64_t* __restrict__ rp, const int* __restrict__ rows,
+                                    const int* count, const int* __restrict__ chunk0,
+                                    const long long* __restrict__ tbase, const int* tot_chunks,
+                                    const int* pool_lab, const long long* pool_sc,
+                                    unsigned long long* __restrict__ best) {
+  __shared__ unsigned long long s_b[32];
+  const int K = *count, T = *tot_chunks;
+  for (int b = blockIdx.x; b < T; b += gridDim.x) {
+    const int r = chunk_row(chunk0, K, b);
+    const long long slots = 2 * (rp[rows[r] + 1] - rp[rows[r]]);
+    const long long s0 = (long long)(b - chunk0[r]) * 2 * kLpChunk;
+    const long long s1 = min(s0 + 2 * kLpChunk, slots);
+    const volatile int* key = pool_lab + tbase[r];
+    const volatile long long* sc = pool_sc + tbase[r];
+    unsigned long long m = 0;
+    for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+      const int l = key[i];
+      if (l < 0) continue;
+      const unsigned long long pk =
+          ((unsigned long long)sc[i] << 32) | (0xffffffffu - (unsigned)l);
+      m = pk > m ? pk : m;
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) s_b[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2) m = s_b[w2] > m ? s_b[w2] : m;
+      if (m) atomicMax(&best[r], m);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void lp_long_finish_kernel(const int64_t* __restrict__ rp, const int* __restrict__ rows,
+                                      const int* count, const long long* __restrict__ tbase,
+                                      const int* pool_lab, const long long* pool_sc,
+                                      const unsigned long long* __restrict__ best,
+                                      const int* __restrict__ lab_in, int* __restrict__ lab_out) {
+  const int K = *count;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < K; r += gridDim.x * blockDim.x) {
+    const int v = rows[r];
+    const int own = lab_in[v];
+    const long long slots = 2 * (rp[v + 1] - rp[v]);
+    const volatile int* key = pool_lab + tbase[r];
+    const volatile long long* sc = pool_sc + tbase[r];
+    long long own_s = 0;
+    long long h = (long long)(lp_hash(own) % (unsigned long long)slots);
+    for (long long p = 0; p < slots; ++p) {
+      const int l = key[h];
+      if (l == own) { own_s = sc[h]; break; }
+      if (l < 0) break;
+      h = (h + 1 == slots) ? 0 : h + 1;
+    }
+    const unsigned long long b = best[r];
+    const long long bs = (long long)(b >> 32);
+    const int bl = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
+    lab_out[v] = (b && bs > own_s) ? bl : own;
+  }
+}
+
+// Cluster cut values: cut[l] += w for every entry (u, v) with lab[u] = l != lab[v]
+// (entry tiles; one atomic per row segment of a warp).
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    lp_cut_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                  const WT* __restrict__ w, const int* __restrict__ lab,
+                  const int* __restrict__ tile_row, int ntiles, long long* __restrict__ cut) {
+  __shared__ TileRowsSmem tr;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  const long long e0 = (long long)blockIdx.x * kET;
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    const bool valid = e < M;
+    int u = 0, lu = 0;
+    long long val = 0;
+    if (valid) {
+      u = tile_row_of(tr, rp, e);
+      lu = lab[u];
+      if (lab[col[e]] != lu) val = (long long)w[e];
+    }
+    warp_segment_add<long long, long long>(u, lu, val, valid, cut);
   }
 }
 
@@ -812,9 +1084,8 @@ cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, co
 
 template <typename WT>
 cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
-                      int* part, int64_t* rp2, int* col2, WT* w2, WT* deg2, DevState* st,
+                      int* part, int64_t* rp2, int* col2, WT* w2, DevState* st,
                       int* m2_dev, cudaStream_t s, int* launches) {
-  cudaMemsetAsync(deg2, 0, (size_t)std::max(n2, 1) * sizeof(WT), s);
   if (N <= 0) {
     rp_fill_kernel<<<grid_for(n2 + 1, 256), 256, 0, s>>>(rp2, n2);
     cudaMemsetAsync(m2_dev, 0, sizeof(int), s);
@@ -827,8 +1098,20 @@ cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2,
   if (err != cudaSuccess) return err;
   cudaMemsetAsync(w2, 0, (size_t)N * sizeof(WT), s);
   segsum_kernel<WT><<<grid_for((N + 7) / 8, 256), 256, 0, s>>>(keys, vals, N, uid, vbits, n2,
-                                                               m2_dev, rp2, col2, w2, deg2);
+                                                               m2_dev, rp2, col2, w2);
   ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t row_degrees(int n, long long M, const int64_t* rp, const WT* w, int* tile_row,
+                        WT* deg, cudaStream_t s, int* launches) {
+  cudaMemsetAsync(deg, 0, (size_t)std::max(n, 1) * sizeof(WT), s);
+  if (M <= 0) return cudaGetLastError();
+  tile_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(rp, n, tile_row);
+  const int ntiles = (int)((M + kET - 1) / kET);
+  degree_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, w, tile_row, ntiles, deg);
+  *launches += 2;
   return cudaGetLastError();
 }
 
@@ -856,23 +1139,66 @@ cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, cons
 }
 
 template <typename WT>
+cudaError_t lp_first_sweep(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                           const int* tile_row, int sweep, unsigned long long* best, int* lab_out,
+                           cudaStream_t s, int* launches) {
+  cudaMemsetAsync(best, 0, (size_t)n * sizeof(unsigned long long), s);
+  if (M > 0) {
+    const int ntiles = (int)((M + kET - 1) / kET);
+    lp_first_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, tile_row, ntiles, sweep,
+                                                      best);
+    ++*launches;
+  }
+  lp_first_finish_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, best, lab_out);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
 cudaError_t lp_sweep(int n, const int64_t* rp, const int* col, const WT* w, const int* lab_in,
-                     int* lab_out, int sweep, int* long_rows, int* long_count, int* pool_lab,
-                     long long* pool_sc, long long pool_slots, unsigned long long* pool_cursor,
-                     DevState* st, cudaStream_t s, int* launches) {
-  // long_count[0] counts long rows, long_count[1] medium rows; medium rows
-  // are listed from the end of long_rows (n entries) downwards.
-  int* mid_rows = long_rows + n;
-  cudaMemsetAsync(long_count, 0, 2 * sizeof(int), s);
-  cudaMemsetAsync(pool_cursor, 0, sizeof(unsigned long long), s);
+                     int* lab_out, int sweep, const LpScratch& sc, DevState* st, cudaStream_t s,
+                     int* launches) {
+  // counts[0] long rows, counts[1] medium rows, counts[2] chunks of long rows;
+  // medium rows are listed after the n-entry long list
+  int* mid_rows = sc.long_rows + n;
+  cudaMemsetAsync(sc.counts, 0, 4 * sizeof(int), s);
+  cudaMemsetAsync(sc.pool_cursor, 0, sizeof(unsigned long long), s);
   lp_short_kernel<WT><<<grid_for((long long)n * 32, kLpWarps * 32), kLpWarps * 32, 0, s>>>(
-      n, rp, col, w, lab_in, lab_out, sweep, long_rows, long_count, mid_rows, long_count + 1);
-  lp_mid_kernel<WT><<<num_sms() * 4, 256, 0, s>>>(rp, col, w, lab_in, lab_out, mid_rows,
-                                                  long_count + 1);
-  lp_long_kernel<WT><<<num_sms() * 2, 512, 0, s>>>(rp, col, w, lab_in, lab_out, long_rows,
-                                                   long_count, pool_lab, pool_sc, pool_slots,
-                                                   pool_cursor, st);
-  *launches += 3;
+      n, rp, col, w, lab_in, lab_out, sweep, sc.long_rows, sc.counts, mid_rows, sc.counts + 1);
+  const size_t mid_smem = (size_t)kLpMidSlots * (sizeof(long long) + sizeof(int));
+  static bool mid_attr = false;
+  if (!mid_attr) {
+    cudaFuncSetAttribute(lp_mid_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)mid_smem);
+    cudaFuncSetAttribute(lp_mid_kernel<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)mid_smem);
+    mid_attr = true;
+  }
+  lp_mid_kernel<WT><<<num_sms() * 2, 256, mid_smem, s>>>(rp, col, w, lab_in, lab_out, mid_rows,
+                                                         sc.counts + 1);
+  *launches += 2;
+  if (sizeof(WT) == 8) {  // scores may exceed 32 bits: one block per long row
+    lp_long_kernel<WT><<<num_sms() * 2, 512, 0, s>>>(rp, col, w, lab_in, lab_out, sc.long_rows,
+                                                     sc.counts, sc.pool_lab, sc.pool_sc,
+                                                     sc.pool_slots, sc.pool_cursor, st);
+    ++*launches;
+    return cudaGetLastError();
+  }
+  cudaMemsetAsync(sc.best, 0, (size_t)std::max(n, 1) * sizeof(unsigned long long), s);
+  lp_long_prep_kernel<<<1, 1024, 0, s>>>(rp, sc.long_rows, sc.counts, sc.chunk0, sc.tbase,
+                                         sc.counts + 2);
+  const int g = num_sms() * 8;
+  lp_long_clear_kernel<<<g, 256, 0, s>>>(rp, sc.long_rows, sc.counts, sc.chunk0, sc.tbase,
+                                         sc.counts + 2, sc.pool_lab, sc.pool_sc);
+  lp_long_insert_kernel<WT><<<g, 256, 0, s>>>(rp, col, w, lab_in, sc.long_rows, sc.counts,
+                                              sc.chunk0, sc.tbase, sc.counts + 2, sc.pool_lab,
+                                              sc.pool_sc);
+  lp_long_scan_kernel<<<g, 256, 0, s>>>(rp, sc.long_rows, sc.counts, sc.chunk0, sc.tbase,
+                                        sc.counts + 2, sc.pool_lab, sc.pool_sc, sc.best);
+  lp_long_finish_kernel<<<num_sms(), 256, 0, s>>>(rp, sc.long_rows, sc.counts, sc.tbase,
+                                                  sc.pool_lab, sc.pool_sc, sc.best, lab_in,
+                                                  lab_out);
+  *launches += 5;
   return cudaGetLastError();
 }
 
@@ -883,8 +1209,8 @@ cudaError_t lp_bound(int n, long long M, const int64_t* rp, const int* col, cons
   cudaMemsetAsync(cut, 0, (size_t)n * sizeof(long long), s);
   cudaMemsetAsync(size, 0, (size_t)n * sizeof(int), s);
   if (M > 0) {
-    lp_cut_kernel<WT><<<std::min(grid_for((long long)n * 32, 256), num_sms() * 64), 256, 0, s>>>(
-        n, rp, col, w, lab, cut);
+    const int ntiles = (int)((M + kET - 1) / kET);
+    lp_cut_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, lab, tile_row, ntiles, cut);
     ++*launches;
   }
   lp_size_kernel<<<grid_for(n, 256), 256, 0, s>>>(lab, n, size);
@@ -976,7 +1302,9 @@ cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream
                                       const int*, int, const int*, u64*, WT*, DevState*, int,    \
                                       cudaStream_t, int*);                                       \
   template cudaError_t build_csr<WT>(const u64*, const WT*, int, int, int, int*, int*, int64_t*, \
-                                     int*, WT*, WT*, DevState*, int*, cudaStream_t, int*);       \
+                                     int*, WT*, DevState*, int*, cudaStream_t, int*);            \
+  template cudaError_t row_degrees<WT>(int, long long, const int64_t*, const WT*, int*, WT*,      \
+                                       cudaStream_t, int*);                                      \
   template cudaError_t check_symmetric<WT>(int, long long, const int64_t*, const int*,           \
                                            const WT*, const int*, DevState*, cudaStream_t,       \
                                            int*);                                                \
@@ -984,8 +1312,10 @@ cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream
                                     const WT*, const int*, uint32_t, long long, int*, uint8_t*,  \
                                     DevState*, cudaStream_t, int*);                              \
   template cudaError_t lp_sweep<WT>(int, const int64_t*, const int*, const WT*, const int*,      \
-                                    int*, int, int*, int*, int*, long long*, long long,          \
-                                    unsigned long long*, DevState*, cudaStream_t, int*);         \
+                                    int*, int, const LpScratch&, DevState*, cudaStream_t, int*); \
+  template cudaError_t lp_first_sweep<WT>(int, long long, const int64_t*, const int*, const WT*, \
+                                          const int*, int, unsigned long long*, int*,           \
+                                          cudaStream_t, int*);                                  \
   template cudaError_t lp_bound<WT>(int, long long, const int64_t*, const int*, const WT*,       \
                                     const int*, const int*, long long*, int*,                    \
                                     unsigned long long*, DevState*, cudaStream_t, int*);

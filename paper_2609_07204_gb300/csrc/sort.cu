@@ -6,7 +6,7 @@
 // parallel edges are then adjacent and summed).  The sort is a single-pass
 // ("onesweep") LSD radix sort, 8 bits per pass:
 //   1. one histogram kernel counts every digit of every pass in one read;
-//   2. each pass is one kernel: a tile of 4096 keys is ranked inside the block
+//   2. each pass is one kernel: a tile of 3072 keys is ranked inside the block
 //      (warp-striped layout + match.any keeps it stable), its digit counts
 //      are published to a decoupled look-back array, the tile reads its
 //      predecessors' counts, and the keys are scattered through shared memory
@@ -24,8 +24,9 @@ namespace mc {
 namespace {
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;  // 4096
+constexpr int kRsItems = kSortTile / kRsThreads;  // 12
+constexpr int kRsTile = kSortTile;
+static_assert(kRsItems * kRsThreads == kRsTile, "tile");
 constexpr u64 kFlagAgg = 1ull << 62;
 constexpr u64 kFlagInc = 2ull << 62;
 constexpr u64 kCountMask = (1ull << 62) - 1;
@@ -79,7 +80,7 @@ __device__ __forceinline__ unsigned block_exclusive_256(unsigned v, unsigned* wa
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(kRsThreads)
+__global__ void __launch_bounds__(kRsThreads, 3)
     rs_pass_kernel(const u64* __restrict__ kin, const WT* __restrict__ vin,
                    u64* __restrict__ kout, WT* __restrict__ vout, int N, int shift, const unsigned* __restrict__ goff, u64* lookback,
                    unsigned long long* tile_counter, unsigned* err, long long spin_limit) {
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kRsThreads)
   const long long tile_base = (long long)tile * kRsTile;
   if (tile_base >= N) return;  // surplus block (grid sized for the upper bound)
 
-  // ---- load (warp-striped: warp w owns keys [w*512, w*512+512) of the tile)
+  // ---- load (warp-striped: warp w owns keys [w*384, w*384+384) of the tile)
   u64 k[kRsItems];
   WT v[kRsItems];
   unsigned short rank[kRsItems];
@@ -302,6 +303,7 @@ cudaError_t radix_sort_pairs(u64* k0, WT* v0, u64* k1, WT* v1, int N, int bits, 
   *in_alt = false;
   if (N <= 1 || bits <= 0) return cudaSuccess;
   const long long maxN = N;
+  if (sort_lookback_words(maxN) > sc.lookback_words) return cudaErrorInvalidValue;
   const int passes = (bits + 7) / 8;
   if (passes > 8) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kRsTile * (sizeof(u64) + sizeof(WT)) + kRsWarps * 256 * sizeof(unsigned);
