@@ -29,6 +29,7 @@
 // alpha, so no key exceeds the new bound), so the tree is maintained with
 // atomicMax and recomputed only along the popped vertex's path.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -247,74 +248,81 @@ __global__ void cf_best_kernel(const unsigned long long* __restrict__ pass_best,
 }
 
 // ------------------------------------------------------ sequential pass
-// Tree levels: level 0 has the n leaves padded to a multiple of 32; each
-// higher level has one node per 32 nodes below, padded likewise, until a
-// level has at most 32 nodes (the top, reduced by one warp).
-struct TreeLayout {
-  int levels;
-  long long off[8];
-  long long size[8];
+// Queue of the sequential pass.  A queued vertex's key is min(r(y), lambda)
+// + 1 (0 = not queued); because no queued r(y) ever exceeds the current bound
+// (see the header comment), the key can be recomputed from r[] at any time,
+// so the leaves of the max-tree are r[] itself (r = -1 marks a visited
+// vertex, r = 0 an untouched one; the start vertex is popped first without a
+// search).  Level 1 holds the maximum key of each 32 consecutive vertices,
+// level 2 of each 32 level-1 nodes, and so on up to a level of at most 32
+// nodes.  Levels that fit go to shared memory, from the top down.
+struct SeqTree {
+  int levels;            // number of node levels (>= 1)
+  long long off[8];      // word offset of level l (l = 1..levels) in the level arena
+  long long size[8];     // nodes of level l, padded to a multiple of 32
 };
 
-__host__ __device__ inline TreeLayout tree_layout(int n) {
-  TreeLayout t{};
-  long long sz = ((long long)n + 31) / 32 * 32;
+__host__ __device__ inline SeqTree seq_tree(int n) {
+  SeqTree t{};
+  long long below = ((long long)n + 31) / 32 * 32;  // padded leaves
   long long off = 0;
-  int l = 0;
+  int l = 1;
   for (;;) {
+    const long long sz = (below / 32 + 31) / 32 * 32;
     t.off[l] = off;
     t.size[l] = sz;
     off += sz;
+    t.levels = l;
+    if (sz <= 32 || l == 7) break;
+    below = sz;
     ++l;
-    if (sz <= 32 || l == 8) break;
-    sz = (sz / 32 + 31) / 32 * 32;
   }
-  t.levels = l;
   return t;
 }
 
-template <typename WT>
+template <typename KT>
+__device__ __forceinline__ KT key_of(long long r, long long lam) {
+  return r > 0 ? (KT)((r < lam ? r : lam) + 1) : (KT)0;
+}
+
+template <typename WT, typename KT>
 __global__ void __launch_bounds__(512)
     cf_seq_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
                   const WT* __restrict__ w, const WT* __restrict__ deg, int start, int* parent,
-                  WT* g_r, uint8_t* g_vis, unsigned long long* g_tree, int* __restrict__ order,
-                  int* __restrict__ marks_out, long long marks_cap, int use_smem,
-                  DevState* st) {
+                  WT* g_r, KT* g_levels, int* __restrict__ order, int* __restrict__ marks_out,
+                  long long marks_cap, int smem_from, int r_in_smem, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_x;
   __shared__ long long s_lam;
   __shared__ int s_done;
   __shared__ unsigned long long s_nmarks;
-  const TreeLayout tl = tree_layout(n);
-  const long long tree_words = tl.off[tl.levels - 1] + tl.size[tl.levels - 1];
-  volatile unsigned long long* tree;
-  volatile WT* r;
-  volatile uint8_t* vis;
-  if (use_smem) {
-    tree = reinterpret_cast<unsigned long long*>(smem);
-    r = reinterpret_cast<WT*>(smem + tree_words * 8);
-    vis = reinterpret_cast<uint8_t*>(smem + tree_words * 8 + (long long)n * sizeof(WT));
-  } else {
-    tree = g_tree;
-    r = g_r;
-    vis = g_vis;
-  }
+  __shared__ long long s_rb, s_re;
+  const SeqTree tl = seq_tree(n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (long long i = tid; i < tree_words; i += blockDim.x) tree[i] = 0;
-  for (long long i = tid; i < n; i += blockDim.x) { r[i] = 0; vis[i] = 0; }
+  // level pointers: levels >= smem_from live in shared memory
+  KT* lev[8];
+  {
+    long long soff = 0;
+    for (int l = tl.levels; l >= 1; --l) {
+      if (l >= smem_from) {
+        lev[l] = reinterpret_cast<KT*>(smem) + soff;
+        soff += tl.size[l];
+      } else {
+        lev[l] = g_levels + tl.off[l];
+      }
+    }
+    const long long sbytes = ((soff * (long long)sizeof(KT)) + 15) / 16 * 16;
+    if (r_in_smem) g_r = reinterpret_cast<WT*>(smem + sbytes);
+  }
+  volatile WT* r = g_r;
+  for (int l = 1; l <= tl.levels; ++l)
+    for (long long i = tid; i < tl.size[l]; i += blockDim.x) lev[l][i] = 0;
+  for (long long i = tid; i < ((long long)n + 31) / 32 * 32; i += blockDim.x)
+    if (i < n) r[i] = 0;
   if (tid == 0) {
     s_lam = (long long)st->lambda;
     s_done = 0;
     s_nmarks = 0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned long long k1 = 1;  // key 0 of the start vertex
-    long long idx = start;
-    for (int l = 0; l < tl.levels; ++l) {
-      tree[tl.off[l] + idx] = k1;
-      idx >>= 5;
-    }
   }
   __syncthreads();
   long long alpha = 0, best_alpha = -1;
@@ -323,36 +331,72 @@ __global__ void __launch_bounds__(512)
   unsigned long long my_marks = 0;
   for (int it = 0; it < n; ++it) {
     if (warp == 0) {
-      // ---- descend to the leftmost maximum
-      const int top = tl.levels - 1;
-      const unsigned long long tv = lane < tl.size[top] ? tree[tl.off[top] + lane] : 0;
-      const unsigned long long m = warp_max(tv);
-      if (m == 0) {
-        if (lane == 0) s_done = 1;
+      int x = -1;
+      long long rx = 0, xb = 0, xe = 0, xd = 0;
+      const long long lam = s_lam;
+      if (it == 0) {
+        x = start;
+        xb = rp[start];
+        xe = rp[start + 1];
+        xd = (long long)deg[start];
       } else {
-        long long idx = __ffs(__ballot_sync(FULL, tv == m)) - 1;
-        for (int l = top - 1; l >= 0; --l) {
-          const unsigned long long cv = tree[tl.off[l] + idx * 32 + lane];
-          idx = idx * 32 + (__ffs(__ballot_sync(FULL, cv == m)) - 1);
-        }
-        const int x = (int)idx;
-        // ---- pop: clear the leaf and recompute its ancestors
-        if (lane == 0) tree[x] = 0;
-        __syncwarp();
-        long long child = x;
-        for (int l = 1; l < tl.levels; ++l) {
-          const long long node = child >> 5;
-          const unsigned long long cv = tree[tl.off[l - 1] + node * 32 + lane];
-          const unsigned long long nm = warp_max(cv);
-          if (lane == 0) tree[tl.off[l] + node] = nm;
+        const int top = tl.levels;
+        volatile KT* lt = lev[top];
+        const KT tv = lane < tl.size[top] ? lt[lane] : (KT)0;
+        const KT m = warp_max(tv);
+        if (m != 0) {
+          long long idx = __ffs(__ballot_sync(FULL, tv == m)) - 1;
+          for (int l = top - 1; l >= 1; --l) {
+            volatile KT* ll = lev[l];
+            const KT cv = ll[idx * 32 + lane];
+            idx = idx * 32 + (__ffs(__ballot_sync(FULL, cv == m)) - 1);
+          }
+          // leaves: keys recomputed from r of the 32 vertices under node idx
+          // (row bounds and degrees of the 32 candidates load alongside r,
+          // so the winner's row is known without another round trip)
+          const long long v = idx * 32 + lane;
+          long long rv = -1, vb = 0, ve = 0, vd = 0;
+          if (v < n) {
+            rv = (long long)r[v];
+            vb = rp[v];
+            ve = rp[v + 1];
+            vd = (long long)deg[v];
+          }
+          const KT kv = key_of<KT>(rv, lam);
+          const unsigned hit = __ballot_sync(FULL, kv == m);
+          const int wl = __ffs(hit) - 1;
+          x = (int)(idx * 32 + wl);
+          rx = __shfl_sync(FULL, rv, wl);
+          xb = __shfl_sync(FULL, vb, wl);
+          xe = __shfl_sync(FULL, ve, wl);
+          xd = __shfl_sync(FULL, vd, wl);
+          // pop x and recompute its ancestors
+          KT nk = lane == wl ? (KT)0 : kv;
+          KT node = warp_max(nk);
+          long long child = idx;
+          if (lane == 0) lev[1][child] = node;
           __syncwarp();
-          child = node;
+          for (int l = 2; l <= tl.levels; ++l) {
+            const long long p = child >> 5;
+            volatile KT* lb = lev[l - 1];
+            const KT cv = lb[p * 32 + lane];
+            node = warp_max(cv);
+            if (lane == 0) lev[l][p] = node;
+            __syncwarp();
+            child = p;
+          }
         }
-        if (lane == 0) {
-          vis[x] = 1;
+      }
+      if (lane == 0) {
+        if (x < 0) {
+          s_done = 1;
+        } else {
+          r[x] = (WT)-1;  // visited
           order[ns] = x;
           ++ns;
-          alpha += (long long)deg[x] - 2 * (long long)r[x];
+          s_rb = xb;
+          s_re = xe;
+          alpha += xd - 2 * rx;
           if (ns < n && alpha < s_lam) {
             s_lam = alpha;
             best_alpha = alpha;
@@ -366,12 +410,12 @@ __global__ void __launch_bounds__(512)
     if (s_done) break;
     const int x = s_x;
     const long long lam = s_lam;
-    const long long rb = rp[x], re = rp[x + 1];
+    const long long rb = s_rb, re = s_re;
     for (long long e = rb + tid; e < re; e += blockDim.x) {
       const int y = col[e];
-      if (vis[y]) continue;
-      const long long c = (long long)w[e];
       const long long r0 = (long long)r[y];
+      if (r0 < 0) continue;  // visited
+      const long long c = (long long)w[e];
       const long long r1 = r0 + c;
       r[y] = (WT)r1;
       if (r0 < lam && lam <= r1) {
@@ -385,12 +429,10 @@ __global__ void __launch_bounds__(512)
           }
         }
       }
-      const unsigned long long key = (unsigned long long)((r1 < lam ? r1 : lam) + 1);
-      long long idx = y;
-      for (int l = 0; l < tl.levels; ++l) {
-        volatile unsigned long long* node = tree + tl.off[l] + idx;
-        if (*node >= key) break;
-        atomicMax((unsigned long long*)node, key);
+      const KT key = key_of<KT>(r1, lam);
+      long long idx = y >> 5;
+      for (int l = 1; l <= tl.levels; ++l) {
+        atomicMax(&lev[l][idx], key);
         idx >>= 5;
       }
     }
@@ -446,12 +488,8 @@ size_t capforest_pass_smem(int table, int warps_per_block, size_t wt_size) {
 }
 
 long long seq_tree_words(int n) {
-  TreeLayout t = tree_layout(n);
-  return t.off[t.levels - 1] + t.size[t.levels - 1];
-}
-
-size_t seq_smem_bytes(int n, size_t wt_size) {
-  return (size_t)seq_tree_words(n) * 8 + (size_t)n * wt_size + (size_t)n + 16;
+  const SeqTree t = seq_tree(n);
+  return t.off[t.levels] + t.size[t.levels];
 }
 
 template <typename WT>
@@ -460,19 +498,36 @@ cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const
                                  uint8_t* visited, unsigned long long* tree, int* order,
                                  int* marks_out, long long marks_cap, DevState* st,
                                  cudaStream_t s, int* launches) {
-  const size_t need = seq_smem_bytes(n, sizeof(WT));
+  (void)visited;
+  using KT = typename std::conditional<sizeof(WT) == 4, unsigned, unsigned long long>::type;
   const size_t limit = 200 * 1024;
-  const int use_smem = need <= limit ? 1 : 0;
+  const SeqTree t = seq_tree(n);
+  // levels from the top down while they fit, then r[] if everything fits
+  size_t used = 0;
+  int smem_from = t.levels + 1;
+  for (int l = t.levels; l >= 1; --l) {
+    const size_t b = (size_t)t.size[l] * sizeof(KT);
+    if (used + b > limit) break;
+    used += b;
+    smem_from = l;
+  }
+  const size_t lev_bytes = (used + 15) / 16 * 16;
+  int r_in_smem = 0;
+  size_t smem = used;
+  if (smem_from == 1 && lev_bytes + (size_t)n * sizeof(WT) <= limit) {
+    r_in_smem = 1;
+    smem = lev_bytes + (size_t)n * sizeof(WT);
+  }
   static bool attr[2] = {false, false};
   const int ai = sizeof(WT) == 8 ? 1 : 0;
   if (!attr[ai]) {
-    cudaFuncSetAttribute(cf_seq_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(cf_seq_kernel<WT, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)limit);
     attr[ai] = true;
   }
-  cf_seq_kernel<WT><<<1, 512, use_smem ? need : 0, s>>>(n, rp, col, w, deg, start, parent, r,
-                                                       visited, tree, order, marks_out,
-                                                       marks_cap, use_smem, st);
+  cf_seq_kernel<WT, KT><<<1, 512, smem, s>>>(n, rp, col, w, deg, start, parent, r,
+                                             reinterpret_cast<KT*>(tree), order, marks_out,
+                                             marks_cap, smem_from, r_in_smem, st);
   ++*launches;
   return cudaGetLastError();
 }

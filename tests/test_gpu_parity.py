@@ -388,3 +388,31 @@ def test_solve_planted_small():
     s = synth.planted(1 << 12, 21 << 12, 30, 25, 1, 5)
     c = (s.row_ptr, s.col, s.w.astype(np.int64))
     _check_solve(s.n, c, mc.default_options(lp_min_n=1000), expect=25)
+
+
+# ------------------------------------------------------- full-size workloads
+def test_solve_er2000_full_size_bitmap():
+    s = synth.workload_er2000()
+    c = (s.row_ptr, s.col, s.w.astype(np.int64))
+    _check_solve(s.n, c, mc.default_options(), expect=oracle.noi(s.n, *c)[0])
+
+
+def test_solve_rmat20_core_full_size():
+    """The benchmark workload at full size, in the benchmark's configuration
+    (default options): the value equals the oracle's NOI and the returned
+    side's cut weight equals the value."""
+    s = synth.workload_rmat_core(20, 10, 2)
+    c = (s.row_ptr, s.col, s.w)
+    lam, _, _ = oracle.noi(s.n, *c)
+    _check_solve(s.n, c, mc.default_options(), expect=lam)
+
+
+@pytest.mark.slow
+def test_solve_planted21_full_size():
+    """Two 2^21-vertex blocks, 25 unit cross edges: lambda = 25 by
+    construction, and the block split is a minimum cut."""
+    s = synth.workload_planted(21, 42, 30, 25, 3)
+    c = (s.row_ptr, s.col, s.w)
+    assert s.m > 80_000_000
+    st = _check_solve(s.n, c, mc.default_options(), expect=25)
+    assert st["rounds"] >= 1
