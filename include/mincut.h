@@ -177,6 +177,27 @@ int mincut_graph_reset(mincut_graph* g);
 /* Release a graph and its device memory (NULL is ignored). */
 void mincut_graph_destroy(mincut_graph* g);
 
+/* Packed batch of independent graphs (many small solves at once).  Graph i
+ * owns the vertices [vertex_offsets[i], vertex_offsets[i+1]) of one CSR over
+ * all vertices (vertex_offsets: host int64[num_graphs+1], vertex_offsets[0] =
+ * 0, every graph at least 2 vertices); no edge may join two graphs
+ * (MINCUT_ERR_INVALID).  Other arguments as mincut_graph_from_csr; the total
+ * weight must stay below 2^31 (MINCUT_ERR_OVERFLOW).  The result is a graph
+ * object usable only with mincut_batch_solve / mincut_graph_destroy. */
+int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
+                          const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                          uint32_t flags, void* cuda_stream, const mincut_allocator* alloc,
+                          mincut_graph** out);
+
+/* Exact minimum cut of every graph of a batch (Algorithm 2 per graph; one
+ * set of round kernels serves all graphs, each graph with its own bound,
+ * stop test and witness; label propagation is not used).  cut_values: host
+ * int64[num_graphs].  side_bitmap (nullable, host or device, ceil(n/64)
+ * words): bit v = 1 iff vertex v is on the side of its graph's minimum cut
+ * that does not hold the graph's first vertex. */
+int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_values,
+                       uint64_t* side_bitmap, mincut_stats* stats);
+
 /* Per-kernel-category timing collected by solves run with opts->profile = 1
  * (CUDA events recorded on the graph's stream around each launch).  Fills up
  * to `cap` entries (out may be NULL to count), sets *count to the number of

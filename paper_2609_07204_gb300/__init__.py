@@ -145,6 +145,12 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mincut_profile_read.argtypes = [vp, ctypes.POINTER(MincutProfileEntry), i32,
                                         ctypes.POINTER(i32), i32]
     lib.mincut_profile_read.restype = ctypes.c_int
+    lib.mincut_batch_from_csr.argtypes = [i64, vp, vp, vp, vp, u32, vp,
+                                          ctypes.POINTER(MincutAllocator), ctypes.POINTER(vp)]
+    lib.mincut_batch_from_csr.restype = ctypes.c_int
+    lib.mincut_batch_solve.argtypes = [vp, ctypes.POINTER(MincutOptions), vp, vp,
+                                       ctypes.POINTER(MincutStats)]
+    lib.mincut_batch_solve.restype = ctypes.c_int
     lib.mincut_contract_csr_noalloc.argtypes = [i64, vp, vp, vp, i64, vp, i64, vp, vp, vp,
                                                 ctypes.POINTER(i64), vp]
     lib.mincut_contract_csr_noalloc.restype = ctypes.c_int
@@ -269,6 +275,64 @@ def mincut_graph_from_csr(n: int, row_ptr, col, w, *, stream: Any = None,
                                    ctypes.byref(out))
     _check(rc)
     return Graph(out.value, n, keep, alloc)
+
+
+def pack_graphs(graphs) -> tuple:
+    """Pack (n, row_ptr, col, w) graphs into one CSR with per-graph vertex
+    offsets: returns (vertex_offsets int64[G+1], row_ptr, col, w)."""
+    offs = [0]
+    rps, cols, ws = [], [], []
+    ebase = 0
+    for (n, rp, col, w) in graphs:
+        rp = np.asarray(rp, np.int64)
+        rps.append(rp[:-1] + ebase)
+        cols.append(np.asarray(col, np.int64) + offs[-1])
+        ws.append(np.asarray(w, np.int64))
+        ebase += int(rp[-1])
+        offs.append(offs[-1] + int(n))
+    row_ptr = np.concatenate(rps + [np.array([ebase], np.int64)])
+    col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    w = np.concatenate(ws).astype(np.int32) if ws else np.zeros(0, np.int32)
+    return np.asarray(offs, np.int64), row_ptr, col, w
+
+
+def mincut_batch_from_csr(vertex_offsets, row_ptr, col, w, *, stream: Any = None,
+                          skip_validate: bool = False) -> Graph:
+    """Build a packed batch of graphs (host numpy arrays; see pack_graphs)."""
+    lib = load_library()
+    vo = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, np.int32)
+        w = np.zeros(1, np.int32)
+    flags = MINCUT_HOST_PTRS | (MINCUT_SKIP_VALIDATE if skip_validate else 0)
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = ctypes.c_void_p(0)
+    rc = lib.mincut_batch_from_csr(len(vo) - 1, vo.ctypes.data, row_ptr.ctypes.data,
+                                   col.ctypes.data, w.ctypes.data, flags,
+                                   ctypes.c_void_p(stream or 0), None, ctypes.byref(out))
+    _check(rc)
+    gr = Graph(out.value, int(vo[-1]), [vo, row_ptr, col, w])
+    gr.G = len(vo) - 1
+    gr.vertex_offsets = vo
+    return gr
+
+
+def mincut_batch_solve(g: Graph, opts: Optional[MincutOptions] = None, *, bitmap: bool = True):
+    """Exact minimum cut of every graph of a batch: (values int64[G],
+    bitmap uint64[ceil(n/64)] or None, stats)."""
+    lib = load_library()
+    vals = np.zeros(g.G, np.int64)
+    st = MincutStats()
+    bm = np.zeros((g.n + 63) // 64, np.uint64) if bitmap else None
+    rc = lib.mincut_batch_solve(g.handle, ctypes.byref(opts) if opts is not None else None,
+                                vals.ctypes.data, bm.ctypes.data if bm is not None else None,
+                                ctypes.byref(st))
+    _check(rc)
+    return vals, bm, st.as_dict()
 
 
 def mincut_solve(g: Graph, opts: Optional[MincutOptions] = None, *, bitmap: bool = True,

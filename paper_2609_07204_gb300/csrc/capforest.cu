@@ -71,7 +71,8 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
                                  int* owner, int* parent, int* __restrict__ visit_log,
                                  unsigned long long* __restrict__ pass_best,
                                  int* __restrict__ pass_len, int total_passes, int table,
-                                 unsigned long long seed, int* pass_counter, DevState* st) {
+                                 unsigned long long seed, int* pass_counter, DevState* st,
+                                 BatchView bv, int batch) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -110,6 +111,18 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
     }
     unsigned long long best_alpha = ~0ull;
     int best_len = 0;
+    int g = 0;
+    long long n_here = n;  // vertices of the graph the pass runs in
+    if (batch && start >= 0) {
+      g = bv.gid[start];
+      if (bv.done_g[g]) {
+        start = -1;
+      } else {
+        lam = (long long)*(volatile unsigned long long*)&bv.lam_g[g];
+        n_here = bv.voff[g + 1] - bv.voff[g];
+      }
+    }
+    unsigned long long pass_marks = 0;
     if (start >= 0 && lam > 0) {
       if (lane == 0) {
         const int h = slot_hash(start) & (table - 1);
@@ -159,11 +172,11 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
         ++nscanned;
         if (lane == 0) visit_log[(long long)p * table + nscanned - 1] = x;
         alpha += (long long)deg[x] - 2 * rx;
-        if (nscanned < n && alpha < lam) {
+        if (nscanned < n_here && alpha < lam) {
           lam = alpha;
           best_alpha = (unsigned long long)alpha;
           best_len = nscanned;
-          if (lane == 0) atomicMin(&st->lambda, (unsigned long long)alpha);
+          if (lane == 0) atomicMin(batch ? &bv.lam_g[g] : &st->lambda, (unsigned long long)alpha);
         }
         // ---- scan x's edges
         for (long long b = rb; b < re; b += 32) {
@@ -194,6 +207,7 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
                 if (r0 < lam && lam <= r1) {
                   if (!uf_union(parent, x, y)) uf_fail = true;
                   ++marks_total;
+                  ++pass_marks;
                 }
                 const unsigned long long np = pack_key(r1 < lam ? r1 : lam, y);
                 if (np > pk[s]) pk[s] = np;
@@ -206,6 +220,14 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
         }
       }
       scanned_total += nscanned;
+    }
+    if (batch) {
+      pass_marks = warp_sum(pass_marks);
+      if (lane == 0) {
+        if (pass_marks) atomicAdd(&bv.marks_g[g], (int)pass_marks);
+        if (best_alpha != ~0ull)
+          atomicMin(&bv.cf_best[g], (best_alpha << 32) | (unsigned long long)(unsigned)p);
+      }
     }
     if (lane == 0) {
       pass_best[p] = best_alpha;
@@ -285,42 +307,30 @@ __device__ __forceinline__ KT key_of(long long r, long long lam) {
   return r > 0 ? (KT)((r < lam ? r : lam) + 1) : (KT)0;
 }
 
+// One sequential pass over the graph of n vertices whose CSR rows are
+// rp[0..n] (entry offsets into col/w), with neighbour ids col[e] - vbase.
+// Parent hooks use ids + vbase.  lev[1..levels] and r point to shared or
+// global memory as chosen by the caller.  Returns the results in the out
+// references (thread 0's values are authoritative).
 template <typename WT, typename KT>
-__global__ void __launch_bounds__(512)
-    cf_seq_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
-                  const WT* __restrict__ w, const WT* __restrict__ deg, int start, int* parent,
-                  WT* g_r, KT* g_levels, int* __restrict__ order, int* __restrict__ marks_out,
-                  long long marks_cap, int smem_from, int r_in_smem, DevState* st) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ void seq_pass_body(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                              int vbase, const WT* __restrict__ w, const WT* __restrict__ deg,
+                              int start, int* parent, KT** lev, const SeqTree& tl, volatile WT* r,
+                              int* __restrict__ order, int* __restrict__ marks_out,
+                              long long marks_cap, long long lam0, long long* best_alpha_out,
+                              int* best_len_out, int* ns_out, unsigned long long* marks_out_cnt,
+                              bool* uf_fail_out) {
   __shared__ int s_x;
   __shared__ long long s_lam;
   __shared__ int s_done;
   __shared__ unsigned long long s_nmarks;
   __shared__ long long s_rb, s_re;
-  const SeqTree tl = seq_tree(n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // level pointers: levels >= smem_from live in shared memory
-  KT* lev[8];
-  {
-    long long soff = 0;
-    for (int l = tl.levels; l >= 1; --l) {
-      if (l >= smem_from) {
-        lev[l] = reinterpret_cast<KT*>(smem) + soff;
-        soff += tl.size[l];
-      } else {
-        lev[l] = g_levels + tl.off[l];
-      }
-    }
-    const long long sbytes = ((soff * (long long)sizeof(KT)) + 15) / 16 * 16;
-    if (r_in_smem) g_r = reinterpret_cast<WT*>(smem + sbytes);
-  }
-  volatile WT* r = g_r;
   for (int l = 1; l <= tl.levels; ++l)
     for (long long i = tid; i < tl.size[l]; i += blockDim.x) lev[l][i] = 0;
-  for (long long i = tid; i < ((long long)n + 31) / 32 * 32; i += blockDim.x)
-    if (i < n) r[i] = 0;
+  for (long long i = tid; i < n; i += blockDim.x) r[i] = 0;
   if (tid == 0) {
-    s_lam = (long long)st->lambda;
+    s_lam = lam0;
     s_done = 0;
     s_nmarks = 0;
   }
@@ -412,14 +422,14 @@ __global__ void __launch_bounds__(512)
     const long long lam = s_lam;
     const long long rb = s_rb, re = s_re;
     for (long long e = rb + tid; e < re; e += blockDim.x) {
-      const int y = col[e];
+      const int y = col[e] - vbase;
       const long long r0 = (long long)r[y];
       if (r0 < 0) continue;  // visited
       const long long c = (long long)w[e];
       const long long r1 = r0 + c;
       r[y] = (WT)r1;
       if (r0 < lam && lam <= r1) {
-        if (!uf_union(parent, x, y)) uf_fail = true;
+        if (!uf_union(parent, x + vbase, y + vbase)) uf_fail = true;
         ++my_marks;
         if (marks_out) {
           const unsigned long long k = atomicAdd(&s_nmarks, 1ull);
@@ -438,10 +448,54 @@ __global__ void __launch_bounds__(512)
     }
     __syncthreads();
   }
+  *best_alpha_out = best_alpha;
+  *best_len_out = best_len;
+  *ns_out = ns;
+  *marks_out_cnt = my_marks;
+  *uf_fail_out = uf_fail;
+}
+
+// Places levels >= smem_from (and r when r_in_smem) in shared memory.
+template <typename WT, typename KT>
+__device__ __forceinline__ void seq_layout(const SeqTree& tl, int smem_from, int r_in_smem,
+                                           unsigned char* smem, KT* g_levels, WT* g_r, KT** lev,
+                                           WT** r_out) {
+  long long soff = 0;
+  for (int l = tl.levels; l >= 1; --l) {
+    if (l >= smem_from) {
+      lev[l] = reinterpret_cast<KT*>(smem) + soff;
+      soff += tl.size[l];
+    } else {
+      lev[l] = g_levels + tl.off[l];
+    }
+  }
+  const long long sbytes = ((soff * (long long)sizeof(KT)) + 15) / 16 * 16;
+  *r_out = r_in_smem ? reinterpret_cast<WT*>(smem + sbytes) : g_r;
+}
+
+template <typename WT, typename KT>
+__global__ void __launch_bounds__(512)
+    cf_seq_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                  const WT* __restrict__ w, const WT* __restrict__ deg, int start, int* parent,
+                  WT* g_r, KT* g_levels, int* __restrict__ order, int* __restrict__ marks_out,
+                  long long marks_cap, int smem_from, int r_in_smem, DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SeqTree tl = seq_tree(n);
+  KT* lev[8];
+  WT* rr;
+  seq_layout<WT, KT>(tl, smem_from, r_in_smem, smem, g_levels, g_r, lev, &rr);
+  long long best_alpha;
+  int best_len, ns;
+  unsigned long long my_marks;
+  bool uf_fail;
+  seq_pass_body<WT, KT>(n, rp, col, 0, w, deg, start, parent, lev, tl, rr, order, marks_out,
+                        marks_cap, (long long)st->lambda, &best_alpha, &best_len, &ns, &my_marks,
+                        &uf_fail);
+  const int lane = threadIdx.x & 31;
   if (uf_fail) set_error(st, ERR_INTERNAL);
   my_marks = warp_sum(my_marks);
   if (lane == 0 && my_marks) atomicAdd(&st->marks_cf, my_marks);
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     st->cf_nscanned = ns;
     if (best_alpha >= 0) {  // below the bound this pass started from
       st->cf_val = (unsigned long long)best_alpha;
@@ -451,7 +505,45 @@ __global__ void __launch_bounds__(512)
     }
   }
   __syncthreads();
-  if (tid == 0) st->cf_nmarks = (long long)(*(volatile unsigned long long*)&st->marks_cf);
+  if (threadIdx.x == 0) st->cf_nmarks = (long long)(*(volatile unsigned long long*)&st->marks_cf);
+}
+
+// Batch: block g runs the pass of graph g if it is not done and marked nothing.
+template <typename WT, typename KT>
+__global__ void __launch_bounds__(512)
+    cf_seq_batch_kernel(int G, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                        const WT* __restrict__ w, const WT* __restrict__ deg, int* parent,
+                        WT* g_r, KT* g_levels, const long long* __restrict__ level_off,
+                        int* __restrict__ order, int all_smem, int always, BatchView bv,
+                        DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int g = blockIdx.x;
+  if (g >= G || bv.done_g[g] || (!always && *(volatile int*)&bv.marks_g[g] > 0)) return;
+  const int vbase = bv.voff[g];
+  const int n = bv.voff[g + 1] - vbase;
+  if (n < 2) return;
+  const SeqTree tl = seq_tree(n);
+  KT* lev[8];
+  WT* rr;
+  seq_layout<WT, KT>(tl, all_smem ? 1 : tl.levels + 1, all_smem, smem, g_levels + level_off[g],
+                     g_r + vbase, lev, &rr);
+  long long best_alpha;
+  int best_len, ns;
+  unsigned long long my_marks;
+  bool uf_fail;
+  const long long lam0 = (long long)*(volatile unsigned long long*)&bv.lam_g[g];
+  seq_pass_body<WT, KT>(n, rp + vbase, col, vbase, w, deg + vbase, 0, parent, lev, tl, rr,
+                        order + vbase, nullptr, 0, lam0, &best_alpha, &best_len, &ns, &my_marks,
+                        &uf_fail);
+  const int lane = threadIdx.x & 31;
+  if (uf_fail) set_error(st, ERR_INTERNAL);
+  my_marks = warp_sum(my_marks);
+  if (lane == 0 && my_marks) atomicAdd(&bv.marks_g[g], (int)my_marks);
+  if (threadIdx.x == 0 && best_alpha >= 0) {
+    atomicMin(&bv.lam_g[g], (unsigned long long)best_alpha);
+    atomicMin(&bv.cf_best[g], ((unsigned long long)best_alpha << 32) | 0xffffffffull);
+    bv.cf_len[g] = best_len;
+  }
 }
 
 }  // namespace
@@ -460,7 +552,8 @@ template <typename WT>
 cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT* w,
                              const WT* deg, int* owner, int* parent, int* visit_log,
                              unsigned long long* pass_best, int* pass_len, int* pass_counter,
-                             PassConfig pc, DevState* st, cudaStream_t s, int* launches) {
+                             PassConfig pc, DevState* st, cudaStream_t s, int* launches,
+                             const BatchView* bv) {
   const int nsum = pc.table >> 5;
   const size_t per_warp = (size_t)pc.table * (sizeof(int) + sizeof(WT) + 8) + (size_t)nsum * 8;
   const size_t smem = per_warp * pc.warps_per_block;
@@ -474,11 +567,16 @@ cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT*
   cudaMemsetAsync(pass_counter, 0, sizeof(int), s);
   const int blocks = std::max(1, std::min(pc.passes / pc.warps_per_block + 1,
                                           num_sms_cf() * 8));
+  BatchView v{};
+  if (bv) v = *bv;
   cf_passes_kernel<WT><<<blocks, pc.warps_per_block * 32, smem, s>>>(
       n, rp, col, w, deg, owner, parent, visit_log, pass_best, pass_len, pc.passes, pc.table,
-      pc.seed, pass_counter, st);
-  cf_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, pc.passes, st);
-  *launches += 2;
+      pc.seed, pass_counter, st, v, bv ? 1 : 0);
+  ++*launches;
+  if (!bv) {
+    cf_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, pc.passes, st);
+    ++*launches;
+  }
   return cudaGetLastError();
 }
 
@@ -532,15 +630,47 @@ cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const
   return cudaGetLastError();
 }
 
+template <typename WT>
+cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col, const WT* w,
+                                       const WT* deg, int* parent, WT* r,
+                                       unsigned long long* levels, const long long* level_off,
+                                       int* order, int max_graph_n, int always,
+                                       const BatchView& bv, DevState* st, cudaStream_t s,
+                                       int* launches) {
+  using KT = typename std::conditional<sizeof(WT) == 4, unsigned, unsigned long long>::type;
+  const size_t limit = 200 * 1024;
+  const SeqTree t = seq_tree(max_graph_n);
+  size_t lev_words = 0;
+  for (int l = 1; l <= t.levels; ++l) lev_words += (size_t)t.size[l];
+  const size_t need = (lev_words * sizeof(KT) + 15) / 16 * 16 + (size_t)max_graph_n * sizeof(WT);
+  const int all_smem = need <= limit ? 1 : 0;
+  static bool attr[2] = {false, false};
+  const int ai = sizeof(WT) == 8 ? 1 : 0;
+  if (!attr[ai]) {
+    cudaFuncSetAttribute(cf_seq_batch_kernel<WT, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)limit);
+    attr[ai] = true;
+  }
+  if (G <= 0) return cudaSuccess;
+  cf_seq_batch_kernel<WT, KT><<<G, 512, all_smem ? need : 0, s>>>(
+      G, rp, col, w, deg, parent, r, reinterpret_cast<KT*>(levels), level_off, order, all_smem,
+      always, bv, st);
+  ++*launches;
+  return cudaGetLastError();
+}
+
 #define MC_CF_INST(WT)                                                                        \
   template cudaError_t capforest_passes<WT>(int, const int64_t*, const int*, const WT*,       \
                                             const WT*, int*, int*, int*, unsigned long long*, \
                                             int*, int*, PassConfig, DevState*, cudaStream_t,  \
-                                            int*);                                            \
+                                            int*, const BatchView*);                          \
   template cudaError_t capforest_sequential<WT>(int, const int64_t*, const int*, const WT*,   \
                                                 const WT*, int, int*, WT*, uint8_t*,          \
                                                 unsigned long long*, int*, int*, long long,   \
-                                                DevState*, cudaStream_t, int*);
+                                                DevState*, cudaStream_t, int*);               \
+  template cudaError_t capforest_sequential_batch<WT>(                                        \
+      int, const int64_t*, const int*, const WT*, const WT*, int*, WT*, unsigned long long*,   \
+      const long long*, int*, int, int, const BatchView&, DevState*, cudaStream_t, int*);
 MC_CF_INST(int32_t)
 MC_CF_INST(int64_t)
 

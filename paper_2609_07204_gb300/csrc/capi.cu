@@ -156,6 +156,12 @@ struct mincut_graph {
   int* m2_dev = nullptr;
   int launches = 0;
   Profiler* prof = nullptr;
+  // packed batch (batch.G > 0)
+  BatchState batch;
+  std::vector<long long> voff0_h;
+  int max_graph_n = 0;
+  unsigned long long* batch_levels = nullptr;
+  long long* batch_vals = nullptr;
   long long spin_limit = 1ll << 22;
 
   const int64_t* crp() const { return cur < 0 ? rp0 : rp[cur]; }
@@ -807,6 +813,110 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   return MINCUT_OK;
 }
 
+template <typename WT>
+int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_values,
+                     uint64_t* side_bitmap, mincut_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = g->stream;
+  BatchState& b = g->batch;
+  const int G = b.G;
+  g->launches = 0;
+  g->cur = -1;
+  g->n = g->n0;
+  g->M = g->M0;
+  if (op.spin_limit > 0) g->spin_limit = op.spin_limit;
+  CK(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
+  CK(cudaMemcpyAsync(b.voff, b.voff0, (size_t)(G + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(b.gid, b.gid0, (size_t)g->n0 * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CK(batch_start(G, b.lam_g, b.done_g, s, &g->launches));
+  iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
+  ++g->launches;
+  CK(cudaMemsetAsync(g->side0, 0, (size_t)g->n0, s));
+  mincut_stats stl{};
+  stl.n_input = g->n0;
+  stl.m_input = g->M0 / 2;
+  const int table = op.pass_table > 0 ? std::min(op.pass_table, g->max_table) : g->max_table;
+  const int max_rounds = op.max_rounds > 0 ? op.max_rounds : g->max_graph_n + 8;
+  for (int round = 0; round < max_rounds; ++round) {
+    const int n = g->n;
+    const long long M = g->M;
+    const int64_t* rp = g->crp();
+    const int* col = g->ccol();
+    const WT* w = (const WT*)g->cw();
+    const WT* deg = (const WT*)g->cdeg();
+    reset_round_kernel<<<1, 1, 0, s>>>(g->st);
+    ++g->launches;
+    CK(batch_round_reset(G, b, s, &g->launches));
+    { ProfScope ps(P_DEGREE, n, s);
+      CK(batch_degree_bound<WT>(n, G, deg, b, &g->st->batch_done, s, &g->launches)); }
+    { ProfScope ps(P_TILES, n, s);
+      CK(tile_rows(rp, n, M, g->tile_row, s, &g->launches)); }
+    { ProfScope ps(P_UF, n, s);
+      CK(uf_init(g->parent, n, s, &g->launches)); }
+    const BatchView v = b.view();
+    if (op.pr_mask) {
+      ProfScope ps(P_PR, M, s);
+      CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, op.pr_mask, op.pr_budget, g->parent,
+                      nullptr, g->st, s, &g->launches, &v));
+    }
+    if (!op.deterministic) {
+      ProfScope ps(P_CF_PASSES, M, s);
+      CK(cudaMemsetAsync(g->owner, 0, (size_t)n * sizeof(int), s));
+      PassConfig pc;
+      pc.table = table;
+      pc.warps_per_block = 4;
+      pc.passes = op.passes > 0 ? std::min(op.passes, g->max_passes)
+                                : std::max(32, std::min(g->max_passes, n / 4));
+      pc.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
+      CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log, g->pass_best,
+                              g->pass_len, g->pass_counter, pc, g->st, s, &g->launches, &v));
+    }
+    { ProfScope ps(P_CF_SEQ, M, s);
+      CK(capforest_sequential_batch<WT>(G, rp, col, w, deg, g->parent, (WT*)g->seq_r,
+                                        g->batch_levels, b.level_off, g->seq_order,
+                                        g->max_graph_n, op.deterministic ? 1 : 0, v, g->st, s,
+                                        &g->launches)); }
+    { ProfScope ps(P_WITNESS, g->n0, s);
+      CK(batch_witness(G, g->n0, b, g->visit_log, table, g->pass_len, g->seq_order, g->cur_side,
+                       g->map0, g->side0, g->st, s, &g->launches)); }
+    CK(batch_collapse(n, b, g->parent, s, &g->launches));
+    stl.rounds++;
+    stl.entries_processed += M;
+    int n2 = 0;
+    long long m2 = 0;
+    int rc = contract_current<WT>(g, &n2, &m2, true);
+    if (rc) return rc;
+    CK(batch_new_offsets(G, b, g->rank, g->st, s, &g->launches));
+    std::swap(b.voff, b.voff_next);
+    CK(batch_gid(b.voff, G, n2, b.gid, s, &g->launches));
+    if (g->hst->batch_done >= G) break;
+  }
+  int rc = sync_state(g);
+  if (rc) return rc;
+  if (g->hst->batch_done < G) return fail(MINCUT_ERR_INTERNAL, "batch did not finish in %d rounds", max_rounds);
+  CK(batch_values(b.lam_g, G, g->batch_vals, s, &g->launches));
+  CK(cudaMemcpyAsync(cut_values, g->batch_vals, (size_t)G * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  if (side_bitmap) {
+    cudaPointerAttributes attr{};
+    bool dev = cudaPointerGetAttributes(&attr, side_bitmap) == cudaSuccess &&
+               (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    u64* target = dev ? reinterpret_cast<u64*>(side_bitmap) : g->bitmap_dev;
+    CK(batch_bitmap(g->side0, g->n0, b, target, s, &g->launches));
+    if (!dev)
+      CK(cudaMemcpyAsync(side_bitmap, g->bitmap_dev, (size_t)((g->n0 + 63) / 64) * 8,
+                         cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  stl.kernel_launches = g->launches;
+  stl.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = stl;
+  g->cur = -1;
+  g->n = g->n0;
+  g->M = g->M0;
+  return MINCUT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -934,6 +1044,87 @@ const char* mincut_status_string(int status) {
 }
 
 const char* mincut_last_error(void) { return g_last_error.c_str(); }
+
+int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
+                          const int64_t* row_ptr, const int32_t* col, const int32_t* w,
+                          uint32_t flags, void* cuda_stream, const mincut_allocator* alloc,
+                          mincut_graph** out) {
+  g_last_error.clear();
+  if (!out || !vertex_offsets) return fail(MINCUT_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (num_graphs < 1 || num_graphs > 0x7ffffff) return fail(MINCUT_ERR_INVALID, "num_graphs");
+  if (vertex_offsets[0] != 0) return fail(MINCUT_ERR_INVALID, "vertex_offsets[0] must be 0");
+  int maxn = 0;
+  for (int64_t i = 0; i < num_graphs; ++i) {
+    const int64_t ng = vertex_offsets[i + 1] - vertex_offsets[i];
+    if (ng < 2) return fail(MINCUT_ERR_INVALID, "graph %lld has fewer than 2 vertices", (long long)i);
+    if (ng > maxn) maxn = (int)std::min<int64_t>(ng, 0x7fffffff);
+  }
+  const int64_t n = vertex_offsets[num_graphs];
+  mincut_graph* g = nullptr;
+  int rc = create_impl(n, row_ptr, col, w, flags, cuda_stream, alloc, &g);
+  if (rc) return rc;
+  auto bail = [&](int r) { mincut_graph_destroy(g); return r; };
+  if (g->wt64) return bail(fail(MINCUT_ERR_OVERFLOW, "a batch needs a total weight below 2^31"));
+  cudaStream_t s = g->stream;
+  const int G = (int)num_graphs;
+  BatchState& b = g->batch;
+  b.G = G;
+  g->max_graph_n = maxn;
+  g->voff0_h.assign(vertex_offsets, vertex_offsets + G + 1);
+  std::vector<int> v32(G + 1);
+  std::vector<long long> loff(G);
+  long long words = 0;
+  for (int i = 0; i < G; ++i) {
+    v32[i] = (int)vertex_offsets[i];
+    loff[i] = words;
+    words += seq_tree_words((int)(vertex_offsets[i + 1] - vertex_offsets[i]));
+  }
+  v32[G] = (int)n;
+  if (!galloc(g, &b.voff0, G + 1) || !galloc(g, &b.gid0, n) || !galloc(g, &b.voff, G + 1) ||
+      !galloc(g, &b.voff_next, G + 1) || !galloc(g, &b.gid, n) || !galloc(g, &b.lam_g, G) ||
+      !galloc(g, &b.lam_before, G) || !galloc(g, &b.deg_best, G) || !galloc(g, &b.cf_best, G) ||
+      !galloc(g, &b.cf_len, G) || !galloc(g, &b.marks_g, G) || !galloc(g, &b.done_g, G) ||
+      !galloc(g, &b.wit_kind, G) || !galloc(g, &b.wit_x, G) || !galloc(g, &b.level_off, G) ||
+      !galloc(g, &g->batch_levels, words) || !galloc(g, &g->batch_vals, G))
+    return bail(fail(MINCUT_ERR_OOM, "batch arrays"));
+  if (cudaMemcpyAsync(b.voff0, v32.data(), (size_t)(G + 1) * sizeof(int), cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(b.level_off, loff.data(), (size_t)G * sizeof(long long), cudaMemcpyHostToDevice, s))
+    return bail(fail(MINCUT_ERR_CUDA, "batch offsets"));
+  if (batch_gid(b.voff0, G, (int)n, b.gid0, s, &g->launches) ||
+      batch_check_edges((int)n, g->rp0, g->col0, b.gid0, g->st, s, &g->launches))
+    return bail(fail(MINCUT_ERR_CUDA, "batch setup"));
+  rc = sync_state(g);
+  if (rc) {
+    if (rc == MINCUT_ERR_INVALID) fail(rc, "an edge joins two different graphs of the batch");
+    return bail(rc);
+  }
+  CK(cudaStreamSynchronize(s));
+  *out = g;
+  return MINCUT_OK;
+}
+
+int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_values,
+                       uint64_t* side_bitmap, mincut_stats* stats) {
+  g_last_error.clear();
+  if (!g || !cut_values) return fail(MINCUT_ERR_INVALID, "NULL graph or cut_values");
+  if (g->batch.G <= 0) return fail(MINCUT_ERR_INVALID, "not a batch (use mincut_batch_from_csr)");
+  mincut_options op;
+  if (opts) op = *opts; else mincut_default_options(&op);
+  if (op.pass_table != 0 && (op.pass_table < 256 || op.pass_table > 2048 ||
+                             (op.pass_table & (op.pass_table - 1))))
+    return fail(MINCUT_ERR_INVALID, "pass_table must be a power of two in [256, 2048]");
+  int rc;
+  {
+    ProfGuard pg(g, op.profile != 0);
+    rc = batch_solve_impl<int32_t>(g, op, cut_values, side_bitmap, stats);
+  }
+  g->cur = -1;
+  g->n = g->n0;
+  g->M = g->M0;
+  return rc;
+}
+
 
 int mincut_profile_read(mincut_graph* g, mincut_profile_entry* out, int32_t cap, int32_t* count,
                         int32_t reset) {

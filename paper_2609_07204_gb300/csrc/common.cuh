@@ -47,7 +47,7 @@ struct DevState {
   long long claimed;           // vertices claimed by concurrent passes this wave
   long long tile_counter[8];   // per-pass tile counters of the radix sort
   int lambda_src;              // 1 degree, 2 LP, 3 CAPFOREST (set by the witness step)
-  int pad;
+  int batch_done;              // graphs of a batch that finished
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -11,6 +11,57 @@ namespace mc {
 
 using u64 = unsigned long long;
 
+// Per-graph view of a packed batch (many graphs in one CSR; graph g owns the
+// current vertices [voff[g], voff[g+1])).  Kernels that take a BatchView use
+// the graph's own bound lam_g[g] instead of DevState::lambda.
+struct BatchView {
+  const int* gid;                // [n] graph of each current vertex
+  const int* voff;               // [G+1] current vertex offsets
+  unsigned long long* lam_g;     // [G] per-graph upper bound
+  unsigned long long* cf_best;   // [G] best CAPFOREST alpha << 32 | pass id (0xffffffff: sequential)
+  int* cf_len;                   // [G] prefix length of the sequential pass's best alpha
+  int* marks_g;                  // [G] marks of this round
+  const int* done_g;             // [G] 1: graph finished
+};
+
+// Device arrays of a packed batch.
+struct BatchState {
+  int G = 0;
+  int* voff0 = nullptr;   // [G+1] input vertex offsets
+  int* gid0 = nullptr;    // [n0] graph of each input vertex
+  int* voff = nullptr;    // [G+1] current offsets
+  int* voff_next = nullptr;
+  int* gid = nullptr;     // [n0] graph of each current vertex
+  unsigned long long *lam_g = nullptr, *lam_before = nullptr, *deg_best = nullptr,
+                     *cf_best = nullptr;
+  int *cf_len = nullptr, *marks_g = nullptr, *done_g = nullptr, *wit_kind = nullptr,
+      *wit_x = nullptr;
+  long long* level_off = nullptr;  // [G] sequential-pass tree offsets
+  BatchView view() const { return BatchView{gid, voff, lam_g, cf_best, cf_len, marks_g, done_g}; }
+};
+
+cudaError_t batch_gid(const int* voff, int G, int n, int* gid, cudaStream_t s, int* launches);
+cudaError_t batch_start(int G, unsigned long long* lam_g, int* done_g, cudaStream_t s,
+                        int* launches);
+cudaError_t batch_round_reset(int G, const BatchState& b, cudaStream_t s, int* launches);
+template <typename WT>
+cudaError_t batch_degree_bound(int n, int G, const WT* deg, const BatchState& b, int* newly_done,
+                               cudaStream_t s, int* launches);
+cudaError_t batch_witness(int G, int n0, const BatchState& b, const int* visit_log, int table,
+                          const int* pass_len, const int* seq_order, uint8_t* cur,
+                          const int* map0, uint8_t* side0, DevState* st, cudaStream_t s,
+                          int* launches);
+cudaError_t batch_collapse(int n, const BatchState& b, int* parent, cudaStream_t s,
+                           int* launches);
+cudaError_t batch_new_offsets(int G, const BatchState& b, const int* rank, const DevState* st,
+                              cudaStream_t s, int* launches);
+cudaError_t batch_bitmap(const uint8_t* side0, int n0, const BatchState& b, u64* bitmap,
+                         cudaStream_t s, int* launches);
+cudaError_t batch_check_edges(int n, const int64_t* rp, const int* col, const int* gid,
+                              DevState* st, cudaStream_t s, int* launches);
+cudaError_t batch_values(const unsigned long long* lam_g, int G, long long* out, cudaStream_t s,
+                         int* launches);
+
 // Message returned by mincut_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
@@ -89,7 +140,7 @@ template <typename WT>
 cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                      const WT* deg, const int* tile_row, uint32_t mask, long long budget,
                      int* parent, uint8_t* flags_out, DevState* st, cudaStream_t s,
-                     int* launches);
+                     int* launches, const BatchView* bv = nullptr);
 
 // One label-propagation sweep (vertices with ((v ^ sweep) & 1) == 0 update).
 // Rows up to 128 entries use a warp table, up to 4096 a block table, longer
@@ -165,7 +216,8 @@ template <typename WT>
 cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT* w,
                              const WT* deg, int* owner, int* parent, int* visit_log,
                              unsigned long long* pass_best, int* pass_len, int* pass_counter,
-                             PassConfig pc, DevState* st, cudaStream_t s, int* launches);
+                             PassConfig pc, DevState* st, cudaStream_t s, int* launches,
+                             const BatchView* bv = nullptr);
 size_t capforest_pass_smem(int table, int warps_per_block, size_t wt_size);
 
 // One sequential CAPFOREST pass over the whole graph from `start` (one block).
@@ -180,5 +232,18 @@ cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const
                                  int* marks_out, long long marks_cap, DevState* st,
                                  cudaStream_t s, int* launches);
 long long seq_tree_words(int n);
+
+// Batch form: one block per graph g of the view; a graph runs its sequential
+// pass (from its first vertex) only if it is not done and marked nothing this
+// round (always != 0: regardless of marks).  r[] is indexed by current
+// vertex; levels at level_off[g] (words of the key type); order at the
+// graph's vertex offset, as local ids.
+template <typename WT>
+cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col, const WT* w,
+                                       const WT* deg, int* parent, WT* r,
+                                       unsigned long long* levels, const long long* level_off,
+                                       int* order, int max_graph_n, int always,
+                                       const BatchView& bv, DevState* st, cudaStream_t s,
+                                       int* launches);
 
 }  // namespace mc

@@ -371,10 +371,11 @@ __global__ void __launch_bounds__(kETThreads)
     pr_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
               const WT* __restrict__ w, const WT* __restrict__ deg,
               const int* __restrict__ tile_row, int ntiles, uint32_t mask, long long budget,
-              int* parent, uint8_t* __restrict__ flags_out, DevState* st) {
+              int* parent, uint8_t* __restrict__ flags_out, DevState* st, BatchView bv,
+              int batch) {
   __shared__ TileRowsSmem tr;
   tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
-  const long long lam = (long long)*(volatile unsigned long long*)&st->lambda;
+  const long long lam_global = (long long)*(volatile unsigned long long*)&st->lambda;
   const long long e0 = (long long)blockIdx.x * kET;
   unsigned long long nmarks = 0;
   bool uf_fail = false;
@@ -384,6 +385,12 @@ __global__ void __launch_bounds__(kETThreads)
     const int u = tile_row_of(tr, rp, e);
     const int v = col[e];
     if (u > v && !flags_out) continue;
+    int gu = 0;
+    if (batch) {
+      gu = bv.gid[u];
+      if (bv.done_g[gu]) continue;
+    }
+    const long long lam = batch ? (long long)*(volatile unsigned long long*)&bv.lam_g[gu] : lam_global;
     const long long c = (long long)w[e];
     const long long du = (long long)deg[u], dv = (long long)deg[v];
     uint8_t f = 0;
@@ -443,6 +450,7 @@ __global__ void __launch_bounds__(kETThreads)
     if (f && u < v) {
       if (!uf_union(parent, u, v)) uf_fail = true;
       ++nmarks;
+      if (batch) atomicAdd(&bv.marks_g[gu], 1);
     }
   }
   if (uf_fail) set_error(st, ERR_INTERNAL);
@@ -1129,11 +1137,13 @@ template <typename WT>
 cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                      const WT* deg, const int* tile_row, uint32_t mask, long long budget,
                      int* parent, uint8_t* flags_out, DevState* st, cudaStream_t s,
-                     int* launches) {
+                     int* launches, const BatchView* bv) {
   if (M <= 0 || mask == 0) return cudaSuccess;
   const int ntiles = (int)((M + kET - 1) / kET);
+  BatchView v{};
+  if (bv) v = *bv;
   pr_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, deg, tile_row, ntiles, mask,
-                                               budget, parent, flags_out, st);
+                                               budget, parent, flags_out, st, v, bv ? 1 : 0);
   ++*launches;
   return cudaGetLastError();
 }
@@ -1310,7 +1320,7 @@ cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream
                                            int*);                                                \
   template cudaError_t pr_marks<WT>(int, long long, const int64_t*, const int*, const WT*,       \
                                     const WT*, const int*, uint32_t, long long, int*, uint8_t*,  \
-                                    DevState*, cudaStream_t, int*);                              \
+                                    DevState*, cudaStream_t, int*, const BatchView*);            \
   template cudaError_t lp_sweep<WT>(int, const int64_t*, const int*, const WT*, const int*,      \
                                     int*, int, const LpScratch&, DevState*, cudaStream_t, int*); \
   template cudaError_t lp_first_sweep<WT>(int, long long, const int64_t*, const int*, const WT*, \

@@ -1,0 +1,84 @@
+"""Packed batch solve (many independent graphs in one CSR) against the oracle:
+every graph's value equals the oracle's, and every graph's side (from the
+shared bitmap) has that cut weight with both sides non-empty."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2609_07204_gb300 as mc  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mc.load_library()
+
+
+def _check_batch(graphs, expect, opts=None):
+    vo, rp, col, w = mc.pack_graphs(graphs)
+    B = mc.mincut_batch_from_csr(vo, rp, col, w)
+    vals, bm, st = mc.mincut_batch_solve(B, opts)
+    side_all = mc.bitmap_to_side(bm, int(vo[-1]))
+    for i, (n, grp, gcol, gw) in enumerate(graphs):
+        assert vals[i] == expect[i], (i, n, vals[i], expect[i])
+        side = side_all[vo[i]:vo[i + 1]]
+        assert side[0] == 0 and 0 < side.sum() < n, i
+        assert oracle.cut_weight(n, grp, gcol, gw, side) == vals[i], i
+    B.destroy()
+    return st
+
+
+def test_batch_random_small_graphs():
+    rng = np.random.default_rng(91)
+    graphs, expect = [], []
+    for i in range(300):
+        n = int(rng.integers(2, 50))
+        g = G.random_graph(n, float(rng.uniform(0.05, 0.9)), rng, 1, int(rng.integers(1, 60)))
+        c = oracle.canonicalize(n, *g)
+        graphs.append((n, c[0], c[1], c[2]))
+        expect.append(oracle.stoer_wagner(n, *c)[0])
+    _check_batch(graphs, expect)
+    _check_batch(graphs, expect, mc.default_options(deterministic=1))
+
+
+def test_batch_closed_forms_and_disconnected():
+    cases = [(G.cycle(30), 30, 2), (G.complete(9), 9, 8), (G.hypercube(5), 32, 5),
+             (G.grid(6, 7), 42, 2), (G.two_cliques(7, 1, 6, 2), 14, 2),
+             (G.from_edges(5, [(0, 1), (2, 3)], [4, 4]), 5, 0),
+             (G.from_edges(2, [(0, 1)], [7]), 2, 7)]
+    graphs = []
+    for c, n, lam in cases:
+        cc = oracle.canonicalize(n, *c)
+        graphs.append((n, cc[0], cc[1], cc[2]))
+    _check_batch(graphs, [lam for _, _, lam in cases])
+
+
+def test_batch_workload_subset_vs_noi():
+    graphs, expect = [], []
+    for i in range(256):
+        s = synth.batch_graph(4, i)
+        graphs.append((s.n, s.row_ptr, s.col, s.w.astype(np.int64)))
+        expect.append(oracle.noi(s.n, s.row_ptr, s.col, s.w)[0])
+    st = _check_batch(graphs, expect)
+    assert st["rounds"] >= 1
+
+
+def test_batch_rejects_cross_graph_edge_and_tiny_graph():
+    c1 = oracle.canonicalize(3, *G.cycle(3))
+    c2 = oracle.canonicalize(3, *G.cycle(3))
+    vo, rp, col, w = mc.pack_graphs([(3, *c1), (3, *c2)])
+    col = col.copy()
+    col[0] = 4  # 0 -> 4 crosses into the second graph (and breaks symmetry)
+    with pytest.raises(mc.MincutError) as e:
+        mc.mincut_batch_from_csr(vo, rp, col, w, skip_validate=True)
+    assert e.value.status == mc.MINCUT_ERR_INVALID
+    vo2 = np.array([0, 1, 6], np.int64)
+    with pytest.raises(mc.MincutError):
+        mc.mincut_batch_from_csr(vo2, rp, col, w)
