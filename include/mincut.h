@@ -239,6 +239,54 @@ int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t
                                 int64_t n2, int64_t* row_ptr_out, int32_t* col_out,
                                 int32_t* w_out, int64_t* m_out, void* cuda_stream);
 
+/* Estimated peak device bytes of one graph with n vertices and m_directed
+ * CSR entries (creation, a solve with label propagation, total weight below
+ * 2^31); used by the server's admission control. */
+int64_t mincut_graph_footprint(int64_t n, int64_t m_directed);
+
+/* ---- Serving: continuous batching of solve requests ------------------------
+ * A server owns `workers` device workers, each with its own CUDA stream, so
+ * admitted requests run concurrently.  A request is admitted when a worker
+ * is free and the summed footprint estimates (mincut_graph_footprint) of the
+ * admitted requests stay under hbm_cap_bytes (a request alone is always
+ * admitted).  A worker that takes a request with n <= pack_max_n also takes
+ * the small requests queued right behind it (up to pack_max_requests and
+ * pack_max_vertices) and solves them as one packed batch; larger requests
+ * are solved alone.  Values are exact, so a request's value does not depend
+ * on what it was solved with. */
+typedef struct mincut_server mincut_server;
+typedef struct mincut_server_options {
+    int32_t workers;            /* default 4 */
+    int32_t pack_max_requests;  /* default 256 (1 disables packing) */
+    int64_t hbm_cap_bytes;      /* default 60 GiB */
+    int64_t pack_max_n;         /* default 4096 */
+    int64_t pack_max_vertices;  /* default 2^20 */
+    int32_t want_bitmap;        /* keep each request's side bitmap (default 1) */
+    int32_t device;             /* CUDA device of the workers (default 0) */
+    mincut_options solve;       /* options of every solve */
+} mincut_server_options;
+typedef struct mincut_server_stats {
+    int64_t submitted, completed;
+    int64_t packed_batches, packed_requests, single_solves;
+    int64_t peak_inflight_bytes, inflight_bytes, queued;
+    int32_t peak_inflight, reserved;
+} mincut_server_stats;
+void mincut_server_default_options(mincut_server_options* o);
+int mincut_server_create(const mincut_server_options* opts, mincut_server** out);
+/* Queue a request; the host CSR (as for mincut_graph_from_csr with
+ * MINCUT_HOST_PTRS) is copied before the call returns.  *request_id names
+ * the request in mincut_server_wait. */
+int mincut_server_submit(mincut_server* s, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                         const int32_t* w, uint64_t* request_id);
+/* Block until the request is solved; returns its status and fills the value,
+ * the latency from submission to completion (ms) and, if requested and kept,
+ * its side bitmap (host, ceil(n/64) words).  The request is then released. */
+int mincut_server_wait(mincut_server* s, uint64_t request_id, int64_t* cut_value,
+                       double* latency_ms, uint64_t* side_bitmap);
+int mincut_server_stats_read(mincut_server* s, mincut_server_stats* out);
+/* Finish every queued request, stop the workers and free the server. */
+void mincut_server_destroy(mincut_server* s);
+
 /* Static description of a status code. */
 const char* mincut_status_string(int status);
 

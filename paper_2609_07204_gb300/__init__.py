@@ -104,6 +104,24 @@ class MincutProfileEntry(ctypes.Structure):
                 ("units", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
+class MincutServerOptions(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("pack_max_requests", ctypes.c_int32),
+                ("hbm_cap_bytes", ctypes.c_int64), ("pack_max_n", ctypes.c_int64),
+                ("pack_max_vertices", ctypes.c_int64), ("want_bitmap", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("solve", MincutOptions)]
+
+
+class MincutServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("packed_batches", ctypes.c_int64), ("packed_requests", ctypes.c_int64),
+                ("single_solves", ctypes.c_int64), ("peak_inflight_bytes", ctypes.c_int64),
+                ("inflight_bytes", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("peak_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -151,6 +169,20 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mincut_batch_solve.argtypes = [vp, ctypes.POINTER(MincutOptions), vp, vp,
                                        ctypes.POINTER(MincutStats)]
     lib.mincut_batch_solve.restype = ctypes.c_int
+    lib.mincut_graph_footprint.argtypes = [i64, i64]
+    lib.mincut_graph_footprint.restype = i64
+    lib.mincut_server_default_options.argtypes = [ctypes.POINTER(MincutServerOptions)]
+    lib.mincut_server_create.argtypes = [ctypes.POINTER(MincutServerOptions), ctypes.POINTER(vp)]
+    lib.mincut_server_create.restype = ctypes.c_int
+    lib.mincut_server_submit.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mincut_server_submit.restype = ctypes.c_int
+    lib.mincut_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i64),
+                                       ctypes.POINTER(ctypes.c_double), vp]
+    lib.mincut_server_wait.restype = ctypes.c_int
+    lib.mincut_server_stats_read.argtypes = [vp, ctypes.POINTER(MincutServerStats)]
+    lib.mincut_server_stats_read.restype = ctypes.c_int
+    lib.mincut_server_destroy.argtypes = [vp]
+    lib.mincut_server_destroy.restype = None
     lib.mincut_contract_csr_noalloc.argtypes = [i64, vp, vp, vp, i64, vp, i64, vp, vp, vp,
                                                 ctypes.POINTER(i64), vp]
     lib.mincut_contract_csr_noalloc.restype = ctypes.c_int
@@ -429,6 +461,70 @@ def mincut_contract_csr_noalloc(n: int, row_ptr, col, w, labels, n2: int, row_pt
         row_ptr_out.data_ptr(), col_out.data_ptr(), w_out.data_ptr(), ctypes.byref(m),
         ctypes.c_void_p(stream or 0)))
     return int(m.value)
+
+
+def mincut_graph_footprint(n: int, m_directed: int) -> int:
+    return int(load_library().mincut_graph_footprint(n, m_directed))
+
+
+def server_default_options(**kw) -> MincutServerOptions:
+    o = MincutServerOptions()
+    load_library().mincut_server_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Continuous-batching solve server (mincut_server_* in the C ABI)."""
+
+    def __init__(self, opts: Optional[MincutServerOptions] = None, **kw):
+        lib = load_library()
+        if opts is None:
+            opts = server_default_options(**kw)
+        h = ctypes.c_void_p(0)
+        _check(lib.mincut_server_create(ctypes.byref(opts), ctypes.byref(h)))
+        self.handle = h
+        self.sizes: dict[int, int] = {}
+
+    def submit(self, n: int, row_ptr, col, w) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        c = np.ascontiguousarray(col, dtype=np.int32)
+        ww = np.ascontiguousarray(w, dtype=np.int32)
+        rid = ctypes.c_uint64(0)
+        _check(load_library().mincut_server_submit(self.handle, n, rp.ctypes.data,
+                                                   c.ctypes.data if c.size else None,
+                                                   ww.ctypes.data if ww.size else None,
+                                                   ctypes.byref(rid)))
+        self.sizes[int(rid.value)] = n
+        return int(rid.value)
+
+    def wait(self, rid: int, bitmap: bool = True):
+        """(value, latency_ms, bitmap or None) of a submitted request."""
+        n = self.sizes.pop(rid)
+        val = ctypes.c_int64(0)
+        lat = ctypes.c_double(0)
+        bm = np.zeros((n + 63) // 64, np.uint64) if bitmap else None
+        _check(load_library().mincut_server_wait(self.handle, rid, ctypes.byref(val),
+                                                 ctypes.byref(lat),
+                                                 bm.ctypes.data if bm is not None else None))
+        return int(val.value), float(lat.value), bm
+
+    def stats(self) -> dict:
+        st = MincutServerStats()
+        _check(load_library().mincut_server_stats_read(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self.handle and self.handle.value:
+            load_library().mincut_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mincut_status_string(status: int) -> str:

@@ -181,6 +181,12 @@ void prof_reset(Profiler* p);
 
 namespace {
 
+// Concurrent CAPFOREST passes per round: one per 4 vertices, at least 256, at
+// most 48 per SM (their visit logs are max_passes x 1024 ints).
+int graph_max_passes(long long n, int sms) {
+  return (int)std::max<long long>(256, std::min<long long>(n / 4, (long long)sms * 48));
+}
+
 // Installs the graph's profiler on this thread for the duration of a call.
 struct ProfGuard {
   mincut_graph* g;
@@ -768,7 +774,7 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   const long long ntiles = (Mb + kEntryTile - 1) / kEntryTile + 2;
   const long long scan_parts = (std::max<long long>(Mb, n) + 4095) / 4096 + 2;
   g->max_table = 1024;
-  g->max_passes = std::max(256, g->sms * 12 * 4);
+  g->max_passes = graph_max_passes(n, g->sms);
   ok = ok && galloc(g, &g->tile_row, ntiles) && (g->deg0 = dev_alloc(g, (size_t)n * wsz)) &&
        (g->degb[0] = dev_alloc(g, (size_t)n * wsz)) && (g->degb[1] = dev_alloc(g, (size_t)n * wsz)) &&
        galloc(g, &g->blk, 2 * 1024) && galloc(g, &g->parent, n) && galloc(g, &g->L, n) &&
@@ -1044,6 +1050,18 @@ const char* mincut_status_string(int status) {
 }
 
 const char* mincut_last_error(void) { return g_last_error.c_str(); }
+
+int64_t mincut_graph_footprint(int64_t n, int64_t m_directed) {
+  if (n < 0 || m_directed < 0) return -1;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+  cudaGetLastError();
+  const long long P = graph_max_passes(n, sms);
+  // 8-byte weights and sums double the weight terms; this bound assumes
+  // 4-byte ones (total weight < 2^31) plus the label-propagation buffers
+  return (int64_t)(140 * n + 90 * m_directed + 4096 * P + (1 << 20));
+}
 
 int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
                           const int64_t* row_ptr, const int32_t* col, const int32_t* w,

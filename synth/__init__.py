@@ -62,6 +62,7 @@ def _load():
         lib.synth_planted.argtypes = [i64, i64, i64, i64, i32, u64, G,
                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8))]
         lib.synth_cycle_plus.argtypes = [i64, dbl, i32, i32, u64, G]
+        lib.synth_truncate_lcc.argtypes = [G, i64, ctypes.c_int, G]
         lib.synth_batch_params.argtypes = [u64, i64, i64, i64, dbl, dbl, ctypes.POINTER(i64),
                                            ctypes.POINTER(dbl), ctypes.POINTER(u64)]
         lib.synth_splitmix64.argtypes = [u64, ctypes.POINTER(u64)]
@@ -197,6 +198,47 @@ def batch_graph(seed: int, i: int, nlo: int = 20, nhi: int = 2000) -> Graph:
     n, d, s = batch_params(seed, i, nlo, nhi)
     g = cycle_plus(n, d, 1, 100, s)
     g.meta.update({"batch_index": i})
+    return g
+
+
+def truncate_lcc(g: Graph, nkeep: int, lcc: bool = True) -> Graph:
+    """Induced subgraph on the vertices with id < nkeep, then the largest
+    connected component."""
+    lib = _load()
+    cg = _CGraph()
+    cg.n = g.n
+    cg.m = g.m
+    cg.row_ptr = g.row_ptr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    cg.col = g.col.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    cg.w = g.w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    out = _CGraph()
+    lib.synth_truncate_lcc(ctypes.byref(cg), nkeep, 1 if lcc else 0, ctypes.byref(out))
+    return _take(out, dict(g.meta))
+
+
+def serving_request(seed: int, i: int, nlo: int = 100, nhi: int = 1 << 20, wlo: int = 1,
+                    whi: int = 100) -> Graph:
+    """Request i of a serving stream: n log-uniform in [nlo, nhi]; with
+    probability 1/2 R-MAT (a=.57, b=.19, c=.19) of scale ceil(log2 n), edge
+    factor 16, truncated to n vertices, else G(n, 8n) (average degree 16);
+    weights uniform in [wlo, whi]; the largest connected component is kept."""
+    v, s = splitmix64(seed ^ (0xA0761D6478BD642F * (i + 1) & ((1 << 64) - 1)))
+    u, s = splitmix64(s)
+    kind, s = splitmix64(s)
+    sub, s = splitmix64(s)
+    x = (u >> 11) / float(1 << 53)
+    n = int(math.floor(math.exp(math.log(nlo) + x * (math.log(nhi) - math.log(nlo)))))
+    n = max(nlo, min(nhi, n))
+    if kind & 1:
+        scale = max(1, int(math.ceil(math.log2(n))))
+        g = rmat(scale, 16, 0.57, 0.19, 0.19, wlo, whi, sub)
+        g = truncate_lcc(g, n, True)
+        kind_s = "rmat"
+    else:
+        m = min(8 * n, n * (n - 1) // 2)
+        g = truncate_lcc(er(n, m, wlo, whi, sub), n, True)
+        kind_s = "er"
+    g.meta.update({"kind": kind_s, "request": i, "n_drawn": n})
     return g
 
 

@@ -343,6 +343,17 @@ int synth_core_lcc(const synth_graph* in, int64_t k, int lcc, synth_graph* out,
     return 0;
 }
 
+/* Vertices with id < nkeep, then (lcc != 0) the largest connected
+ * component, relabelled densely in increasing old id. */
+int synth_truncate_lcc(const synth_graph* in, int64_t nkeep, int lcc, synth_graph* out) {
+    uint8_t* keep = (uint8_t*)xmalloc((size_t)(in->n ? in->n : 1));
+    for (int64_t v = 0; v < in->n; ++v) keep[v] = v < nkeep ? 1 : 0;
+    if (lcc) lcc_keep(in, keep);
+    induced_subgraph(in, keep, out, NULL);
+    free(keep);
+    return 0;
+}
+
 /* ------------------------------------------------------- planted cut */
 /* Two independent G(nb, mb) blocks with unit weights, each reduced to its
  * kcore-core, joined by `cross` random edges of weight `cross_w` between
