@@ -15,6 +15,10 @@ until lambda is proven) on the graph already resident in HBM.
            value and the side bitmap
   roofline of the dominant kernel from the library's live CUDA-event profile
   cpu_baseline = the CPU oracle (sequential NOI) on the same workload
+  batched = 4096 small graphs in one packed batch solve vs one at a time
+  serving = open-loop Poisson request stream through the continuous-batching
+            server at 0.5x and 2x the sequential throughput: solves/s,
+            p50/p99 latency
 
 --impl reference times the CPU oracle as the reference arm.  Multi-GPU runs
 (torchrun) are independent replicas: the solve does not shard.
@@ -145,6 +149,114 @@ def cpu_oracle_time(g, budget_s: float = 30.0):
     dt = time.perf_counter() - t0
     return {"value": g.m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"one sequential NOI solve of the full workload ({dt:.2f} s, lambda={lam})"}, lam
+
+
+def measure_batched(mc, n_graphs: int = 4096, alone: int = 256, reps: int = 3):
+    """Batched workload: n_graphs graphs (n log-uniform in [20, 2000], average
+    degree uniform in [3, 12], weights in [1, 100], seed 4) solved by one
+    packed batch solve, against solving them one at a time on the device."""
+    import synth
+    import torch
+    graphs = []
+    for i in range(n_graphs):
+        s = synth.batch_graph(4, i)
+        graphs.append((s.n, s.row_ptr, s.col, s.w))
+    vo, rp, col, w = mc.pack_graphs(graphs)
+    B = mc.mincut_batch_from_csr(vo, rp, col, w)
+    mc.mincut_batch_solve(B, bitmap=False)
+    ts = []
+    launches = 0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vals, _, st = mc.mincut_batch_solve(B)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+        launches += st["kernel_launches"]
+    B.destroy()
+    t_batch = statistics.median(ts)
+    Gs = [mc.mincut_graph_from_csr(*g) for g in graphs[:alone]]
+    for Gi in Gs[:8]:
+        mc.mincut_solve(Gi, bitmap=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    one = [mc.mincut_solve(Gi)[0] for Gi in Gs]
+    torch.cuda.synchronize()
+    t_one = (time.perf_counter() - t0) / alone
+    for Gi in Gs:
+        Gi.destroy()
+    assert one == [int(v) for v in vals[:alone]]
+    rate = n_graphs / t_batch
+    return {"workload": f"{n_graphs} graphs, n log-uniform [20,2000], avg deg U[3,12], w U[1,100], seed 4",
+            "solves_per_s": rate, "ms_per_batch": t_batch * 1e3, "rounds": st["rounds"],
+            "one_at_a_time_solves_per_s": 1.0 / t_one,
+            "speedup_vs_one_at_a_time": rate * t_one, "gpu_launches_per_batch": launches // reps,
+            "one_at_a_time_sample": alone}
+
+
+def measure_serving(mc, n_req: int = 300, nhi: int = 1 << 14, seed: int = 5):
+    """Open-loop Poisson stream of n_req requests (n log-uniform in [100, nhi],
+    R-MAT or G(n, 8n) 50/50, weights in [1, 100], largest component) served by
+    the continuous-batching server at 0.5x and 2x the sequential-submission
+    throughput; sequential submission = create + solve + read back, one at a
+    time.  Latency = submission to completion."""
+    import threading
+
+    import synth
+    reqs = [synth.serving_request(seed, i, 100, nhi) for i in range(n_req)]
+    lat_seq = []
+    t0 = time.perf_counter()
+    vals_seq = []
+    for g in reqs:
+        t1 = time.perf_counter()
+        Gi = mc.mincut_graph_from_csr(g.n, g.row_ptr, g.col, g.w)
+        v, _, _ = mc.mincut_solve(Gi)
+        Gi.destroy()
+        lat_seq.append((time.perf_counter() - t1) * 1e3)
+        vals_seq.append(v)
+    t_seq = time.perf_counter() - t0
+    seq_rate = n_req / t_seq
+    out = {"workload": f"{n_req} requests, n log-uniform [100,{nhi}], R-MAT/ER 50/50, w U[1,100], seed {seed}",
+           "sequential": {"solves_per_s": seq_rate,
+                          "p50_ms": float(np.percentile(lat_seq, 50)),
+                          "p99_ms": float(np.percentile(lat_seq, 99))}}
+    rng = np.random.default_rng(seed)
+    for load in (0.5, 2.0):
+        rate = load * seq_rate
+        gaps = rng.exponential(1.0 / rate, size=n_req)
+        S = mc.Server(workers=4)
+        ids = [None] * n_req
+        start = time.perf_counter()
+
+        def submitter():
+            t_next = start
+            for i, g in enumerate(reqs):
+                t_next += gaps[i]
+                d = t_next - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids[i] = S.submit(g.n, g.row_ptr, g.col, g.w)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lats, vals = [], []
+        for i in range(n_req):
+            while ids[i] is None:
+                time.sleep(0.0002)
+            v, lat, _ = S.wait(ids[i], bitmap=False)
+            lats.append(lat)
+            vals.append(v)
+        th.join()
+        wall = time.perf_counter() - start
+        st = S.stats()
+        S.close()
+        assert vals == vals_seq
+        out[f"load_{load}x"] = {"offered_per_s": rate, "solves_per_s": n_req / wall,
+                                "p50_ms": float(np.percentile(lats, 50)),
+                                "p99_ms": float(np.percentile(lats, 99)),
+                                "packed_batches": st["packed_batches"],
+                                "peak_inflight": st["peak_inflight"]}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -283,6 +395,9 @@ def run_gpu(args, rank, world):
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "clocks": clk,
     }
+    if not args.no_extra:
+        line["batched"] = measure_batched(mc)
+        line["serving"] = measure_serving(mc)
     if not args.no_cpu_baseline:
         cb, lam = cpu_oracle_time(g)
         assert lam == val, (lam, val)
@@ -298,6 +413,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and serving measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
