@@ -651,6 +651,25 @@ int contract_round_impl(mincut_graph* g, const mincut_round_options* ro,
   return MINCUT_OK;
 }
 
+// Degrees of the canonical input rp0/col0/w0 (M0 entries) and, with
+// `validate`, the symmetry check.
+template <typename WT>
+int finish_input(mincut_graph* g, int n, bool validate) {
+  cudaStream_t s = g->stream;
+  const long long m = g->M0;
+  if (m > 0) CK(tile_rows(g->rp0, n, m, g->tile_row, s, &g->launches));
+  CK(row_degrees<WT>(n, m, g->rp0, (const WT*)g->w0, g->tile_row, (WT*)g->deg0, s,
+                     &g->launches));
+  if (validate && m > 0) {
+    CK(check_symmetric<WT>(n, m, g->rp0, g->col0, (const WT*)g->w0, g->tile_row, g->st, s,
+                           &g->launches));
+    int rc = sync_state(g);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(s));
+  return MINCUT_OK;
+}
+
 // Canonicalise the raw input already copied to rp[1]/col[1]/w[1] into
 // rp0/col0/w0 (identity labels: sort, sum duplicates, drop self-loops).
 template <typename WT>
@@ -674,15 +693,6 @@ int canonicalize_input(mincut_graph* g, int n, long long Mraw, bool validate) {
   rc = sync_state(g);
   if (rc) return rc;
   g->M0 = m2;
-  CK(row_degrees<WT>(n, m2, g->rp[0], (const WT*)g->w[0], g->tile_row, (WT*)g->deg0, s,
-                     &g->launches));
-  if (validate && m2 > 0) {
-    CK(tile_rows(g->rp[0], n, m2, g->tile_row, s, &g->launches));
-    CK(check_symmetric<WT>(n, m2, g->rp[0], g->col[0], (const WT*)g->w[0], g->tile_row, g->st, s,
-                           &g->launches));
-    rc = sync_state(g);
-    if (rc) return rc;
-  }
   if (!galloc(g, &g->rp0, n + 1) || !galloc(g, &g->col0, m2) ||
       !(g->w0 = dev_alloc(g, (size_t)std::max(m2, 1) * sizeof(WT))))
     return fail(MINCUT_ERR_OOM, "canonical input");
@@ -691,8 +701,7 @@ int canonicalize_input(mincut_graph* g, int n, long long Mraw, bool validate) {
     CK(cudaMemcpyAsync(g->col0, g->col[0], (size_t)m2 * sizeof(int), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(g->w0, g->w[0], (size_t)m2 * sizeof(WT), cudaMemcpyDeviceToDevice, s));
   }
-  CK(cudaStreamSynchronize(s));
-  return MINCUT_OK;
+  return finish_input<WT>(g, n, validate);
 }
 
 int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
@@ -760,6 +769,22 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   if (hws[2]) return bail(fail(MINCUT_ERR_INVALID, "row_ptr is not non-decreasing"));
   if (hws[1]) return bail(fail(MINCUT_ERR_INVALID, "negative weight"));
   g->wt64 = hws[0] > 0x7fffffffull;
+  // An input already in canonical form (the form every contraction writes)
+  // is adopted as is: no relabel/sort/sum pass.
+  const long long ntiles = (std::max<long long>(Mraw, 1) + kEntryTile - 1) / kEntryTile + 2;
+  if (!galloc(g, &g->tile_row, ntiles)) return bail(fail(MINCUT_ERR_OOM, "tile rows"));
+  bool canonical = false;
+  if (Mraw > 0) {
+    unsigned* bad = reinterpret_cast<unsigned*>(wst + 3);
+    if (tile_rows(rp_raw, n, Mraw, g->tile_row, s, &g->launches) != cudaSuccess ||
+        canon_check<int32_t>(n, Mraw, rp_raw, col_raw, w_raw, g->tile_row, bad, s,
+                             &g->launches) != cudaSuccess ||
+        cudaMemcpyAsync(&hws[3], wst + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return bail(fail(MINCUT_ERR_CUDA, "canonical check: %s", cudaGetErrorString(cudaGetLastError())));
+    canonical = hws[3] == 0;
+  }
   const size_t wsz = g->wt64 ? 8 : 4;
   g->n0 = n;
   g->Mraw = Mraw;
@@ -771,11 +796,10 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
          (g->w[i] = dev_alloc(g, (size_t)Mb * wsz)) && galloc(g, &g->keys[i], Mb) &&
          (g->vals[i] = dev_alloc(g, (size_t)Mb * wsz));
   }
-  const long long ntiles = (Mb + kEntryTile - 1) / kEntryTile + 2;
   const long long scan_parts = (std::max<long long>(Mb, n) + 4095) / 4096 + 2;
   g->max_table = 1024;
   g->max_passes = graph_max_passes(n, g->sms);
-  ok = ok && galloc(g, &g->tile_row, ntiles) && (g->deg0 = dev_alloc(g, (size_t)n * wsz)) &&
+  ok = ok && (g->deg0 = dev_alloc(g, (size_t)n * wsz)) &&
        (g->degb[0] = dev_alloc(g, (size_t)n * wsz)) && (g->degb[1] = dev_alloc(g, (size_t)n * wsz)) &&
        galloc(g, &g->blk, 2 * 1024) && galloc(g, &g->parent, n) && galloc(g, &g->L, n) &&
        galloc(g, &g->flags, n) && galloc(g, &g->rank, n) && galloc(g, &g->part, scan_parts) &&
@@ -791,6 +815,28 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
        galloc(g, &g->sort.lookback, sort_lookback_words(Mb));
   if (!ok) return bail(fail(MINCUT_ERR_OOM, "device buffers for n=%d M=%lld", n, Mraw));
   g->sort.lookback_words = sort_lookback_words(Mb);
+  const bool validate = (flags & MINCUT_SKIP_VALIDATE) == 0;
+  if (canonical) {
+    g->rp0 = rp_raw;
+    g->col0 = col_raw;
+    if (g->wt64) {
+      if (!(g->w0 = dev_alloc(g, (size_t)Mraw * 8))) return bail(fail(MINCUT_ERR_OOM, "weights"));
+      widen32_kernel<<<std::max(1, std::min(g->sms * 8, (int)((Mraw + 255) / 256))), 256, 0, s>>>(
+          w_raw, (int64_t*)g->w0, Mraw);
+      dev_free(g, w_raw);
+    } else {
+      g->w0 = w_raw;
+    }
+    dev_free(g, wst);
+    g->M0 = Mraw;
+    int rc = g->wt64 ? finish_input<int64_t>(g, n, validate) : finish_input<int32_t>(g, n, validate);
+    if (rc) return bail(rc);
+    g->cur = -1;
+    g->n = n;
+    g->M = g->M0;
+    *out = g;
+    return MINCUT_OK;
+  }
   // raw input into rp[1]/col[1]/w[1]
   if (cudaMemcpyAsync(g->rp[1], rp_raw, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
       (Mraw > 0 && cudaMemcpyAsync(g->col[1], col_raw, (size_t)Mraw * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess))
@@ -808,7 +854,6 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   dev_free(g, w_raw);
   dev_free(g, col_raw);
   dev_free(g, wst);
-  const bool validate = (flags & MINCUT_SKIP_VALIDATE) == 0;
   int rc = g->wt64 ? canonicalize_input<int64_t>(g, n, Mraw, validate)
                    : canonicalize_input<int32_t>(g, n, Mraw, validate);
   if (rc) return bail(rc);

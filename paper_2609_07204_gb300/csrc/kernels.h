@@ -114,6 +114,13 @@ constexpr int kEntryTile = 2048;  // entries per block of the entry-parallel ker
 cudaError_t tile_rows(const int64_t* rp, int n, long long M, int* tile_row, cudaStream_t s,
                       int* launches);
 
+// Sets *bad (atomicOr 1) unless every row is strictly increasing with
+// indices in [0, n), no self-loop and positive weights.  tile_row from
+// tile_rows(rp, ...); rp must be non-decreasing with rp[n] == M.
+template <typename WT>
+cudaError_t canon_check(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                        const int* tile_row, unsigned* bad, cudaStream_t s, int* launches);
+
 // Minimum degree and its vertex (smallest id) -> st->deg_val/deg_arg; lowers
 // st->lambda.  The degrees come with the CSR (build_csr).
 template <typename WT>

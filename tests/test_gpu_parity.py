@@ -92,6 +92,50 @@ def test_from_csr_large_multi_tile_multi_pass():
     assert_csr_equal(mc.mincut_graph_export_csr(g), canon(n, rp, dst.astype(np.int32), ww))
 
 
+@pytest.mark.parametrize("defect", ["none", "self", "zero", "swap", "swap_tile_edge"])
+@pytest.mark.parametrize("big", [False, True])
+def test_from_csr_canonical_input_and_single_defects(defect, big):
+    """A canonical input is taken as is; one defect (a self-loop, a zero
+    weight, two neighbours out of order -- also across an entry tile
+    boundary) sends it through the canonicalisation sort.  Both give the
+    oracle's canonical form and the exact minimum cut."""
+    rng = np.random.default_rng(31 + big)
+    n = 1200
+    lo, hi = ((1 << 22), (1 << 31) - 1) if big else (1, 50)
+    g0 = G.random_graph(n, 0.02, rng, lo, hi, connected=True)
+    rp, col, w = (np.array(x) for x in canon(n, *g0))
+    M = int(rp[-1])
+    assert M > 4 * 2048
+    col = col.astype(np.int32)
+    w = w.astype(np.int64)
+    if defect == "self":
+        u = int(np.searchsorted(rp, M // 3, "right")) - 1
+        b = int(rp[u])
+        col = np.insert(col, b, u).astype(np.int32)
+        w = np.insert(w, b, 7)
+        rp[u + 1:] += 1
+    elif defect == "zero":
+        u = int(np.searchsorted(rp, M // 3, "right")) - 1
+        b = int(rp[u])
+        v = int(col[b])
+        j = int(rp[v]) + int(np.searchsorted(col[rp[v]:rp[v + 1]], u))
+        w[b] = 0
+        w[j] = 0
+    elif defect.startswith("swap"):
+        i = 2047 if defect == "swap_tile_edge" else M // 2
+        u = int(np.searchsorted(rp, i, "right")) - 1
+        if i + 1 >= int(rp[u + 1]):  # keep both entries inside row u
+            i = int(rp[u + 1]) - 2
+        assert int(rp[u]) <= i
+        col[i], col[i + 1] = col[i + 1], col[i]
+        w[i], w[i + 1] = w[i + 1], w[i]
+    g = make(n, rp, col, w)
+    c = canon(n, rp, col, w)
+    assert_csr_equal(mc.mincut_graph_export_csr(g), c)
+    v, _, _ = mc.mincut_solve(g, bitmap=False)
+    assert v == oracle.stoer_wagner(n, *c)[0]
+
+
 def test_from_csr_device_pointers_and_torch_allocator():
     rng = np.random.default_rng(5)
     rp, col, w = noncanonical(400, rng, 5000)
@@ -184,6 +228,45 @@ def test_pr_flags_bit_exact(budget):
         assert np.array_equal(flags[:M], exp)
         src = np.repeat(np.arange(n), np.diff(c[0]))
         assert res["marks_pr"] == int(((exp != 0) & (src < c[1])).sum())
+
+
+@pytest.mark.parametrize("budget,big", [(-1, False), (3, False), (-1, True)])
+def test_pr_flags_bit_exact_hub_rows(budget, big):
+    """Rows longer than two entry tiles (whole tiles inside one row take the
+    shared-memory row index), with common neighbours among the leaves."""
+    rng = np.random.default_rng(77 + budget + 5 * big)
+    n = 9000
+    hubs = [0, 1, 2, 4500]
+    edges = set()
+    for h in hubs:
+        for x in rng.choice(n, size=int(rng.integers(4300, 8000)), replace=False):
+            if x != h:
+                edges.add((min(h, int(x)), max(h, int(x))))
+    edges.update((i, i + 1) for i in range(n - 1))
+    for _ in range(12000):
+        a, b = (int(t) for t in rng.integers(0, n, 2))
+        if a != b:
+            edges.add((min(a, b), max(a, b)))
+    edges = sorted(edges)
+    lo, hi = ((1 << 20), (1 << 31) - 1) if big else (1, 40)  # big: int64 totals
+    wts = [int(t) for t in rng.integers(lo, hi, len(edges))]
+    c = canon(n, *G.from_edges(n, edges, wts))
+    lam = int(oracle.degrees(n, *c).min())
+    g = make(n, c[0], c[1], c[2])
+    M = int(c[0][-1])
+    assert int(np.diff(c[0]).max()) > 2 * 2048
+    flags = np.zeros(M, np.uint8)
+    ro = mc.default_round_options()
+    ro.capforest = 0
+    ro.lp_iters = 0
+    ro.pr_budget = budget
+    ro.pr_flags_out = flags.ctypes.data
+    res = mc.mincut_contract_round(g, ro)
+    assert not res["stopped"]
+    exp = oracle.pr_marks(n, *c, lam, 0xF, budget)
+    assert np.array_equal(flags, exp)
+    src = np.repeat(np.arange(n), np.diff(c[0]))
+    assert res["marks_pr"] == int(((exp != 0) & (src < c[1])).sum())
 
 
 # ------------------------------------------------ deterministic CAPFOREST pass
