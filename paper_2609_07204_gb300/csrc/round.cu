@@ -390,6 +390,15 @@ __global__ void __launch_bounds__(kETThreads)
 // shorter row is walked and each neighbour binary-searched in the longer one.
 // A passing edge is hooked in the union-find.  With flags_out every directed
 // entry gets its flag byte (both directions evaluated).
+//
+// Two phases per tile.  Phase 1 (one thread per entry) applies PR1/PR2 and
+// the budget and queues the entries that need the PR3/PR4 intersection in
+// shared memory; phase 2 spreads the queued intersections over all threads
+// of the block, g lanes per entry with g the largest power of two that still
+// gives every entry its own lane group, so that a few long intersections in a
+// tile do not leave the other lanes idle.
+constexpr int kPrQueue = kET;
+
 template <typename WT>
 __global__ void __launch_bounds__(kETThreads)
     pr_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
@@ -398,17 +407,23 @@ __global__ void __launch_bounds__(kETThreads)
               int* parent, uint8_t* __restrict__ flags_out, DevState* st, BatchView bv,
               int batch) {
   __shared__ TileRowsSmem tr;
+  __shared__ int q_u[kPrQueue];
+  __shared__ unsigned q_ef[kPrQueue];  // entry offset in the tile | PR1/PR2 flags << 16
+  __shared__ int q_n;
+  if (threadIdx.x == 0) q_n = 0;
   tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  const bool exact = flags_out != nullptr;
   const long long lam_global = (long long)*(volatile unsigned long long*)&st->lambda;
   const long long e0 = (long long)blockIdx.x * kET;
   unsigned long long nmarks = 0;
   bool uf_fail = false;
+  // ---- phase 1: PR1/PR2, budget, queue
   for (int i = 0; i < kETItems; ++i) {
     const long long e = e0 + i * kETThreads + threadIdx.x;
     if (e >= M) break;
     const int u = tile_row_of(tr, rp, e);
     const int v = col[e];
-    if (u > v && !flags_out) continue;
+    if (u > v && !exact) continue;
     int gu = 0;
     if (batch) {
       gu = bv.gid[u];
@@ -420,61 +435,111 @@ __global__ void __launch_bounds__(kETThreads)
     uint8_t f = 0;
     if ((mask & 1u) && c >= lam) f |= 1;
     if ((mask & 2u) && (du < 2 * c || dv < 2 * c)) f |= 2;
-    if ((mask & 12u) && (flags_out || f == 0)) {
-      const long long bu = rp[u], eu = rp[u + 1], bv = rp[v], ev = rp[v + 1];
-      const long long lu = eu - bu, lv = ev - bv;
-      // Without a flags output an edge whose endpoints are already joined in
-      // the union-find (by marks hooked so far) cannot change the contraction:
-      // skip its intersection.
-      const bool joined = !flags_out && (budget < 0 || min(lu, lv) <= budget) &&
-                          uf_find(parent, u) == uf_find(parent, v);
-      if (!joined && (budget < 0 || min(lu, lv) <= budget)) {
-        const bool a_is_u = lu <= lv;
-        const long long ab = a_is_u ? bu : bv, ae = a_is_u ? eu : ev;
-        const long long bb = a_is_u ? bv : bu, be = a_is_u ? ev : eu;
-        const long long da = a_is_u ? du : dv;
-        long long sum = c;
-        bool pr3 = false;
-        // Without a flags output only "some test passes" matters, so the scan
-        // stops once the answer is known: PR4 reached, PR3 found, or neither
-        // still possible (rem = weight of a's unscanned edges bounds the PR4
-        // sum still to come; PR3 needs a single edge heavier than da/2 - c).
-        long long rem = da - c;
-        const bool exact = flags_out != nullptr;
-        long long lo = bb;
-        for (long long ea = ab; ea < ae; ++ea) {
-          const int x = col[ea];
-          if (x == u || x == v) continue;
-          const long long cax = (long long)w[ea];
-          rem -= cax;
-          // neighbours of the shorter row ascend, so the search window only
-          // moves right
-          long long hi = be;
-          while (lo < hi) {
-            long long mid = (lo + hi) >> 1;
-            if (col[mid] < x) lo = mid + 1; else hi = mid;
-          }
-          if (lo >= be) break;
-          if (col[lo] == x) {
-            const long long cbx = (long long)w[lo];
-            const long long cux = a_is_u ? cax : cbx, cvx = a_is_u ? cbx : cax;
-            sum += cux < cvx ? cux : cvx;
-            if (du < 2 * (c + cux) && dv < 2 * (c + cvx)) pr3 = true;
-          }
-          if (!exact) {
-            if (((mask & 8u) && sum >= lam) || ((mask & 4u) && pr3)) break;
-            if (sum + rem < lam && !((mask & 4u) && 2 * (c + rem) > da)) break;
-          }
-        }
-        if ((mask & 4u) && pr3) f |= 4;
-        if ((mask & 8u) && sum >= lam) f |= 8;
+    if ((mask & 12u) && (exact || f == 0)) {
+      const long long lu = rp[u + 1] - rp[u], lv = rp[v + 1] - rp[v];
+      if (budget < 0 || min(lu, lv) <= budget) {
+        const int slot = atomicAdd(&q_n, 1);
+        q_u[slot] = u;
+        q_ef[slot] = (unsigned)(e - e0) | ((unsigned)f << 16);
+        continue;
       }
     }
-    if (flags_out) flags_out[e] = f;
+    if (exact) flags_out[e] = f;
     if (f && u < v) {
       if (!uf_union(parent, u, v)) uf_fail = true;
       ++nmarks;
       if (batch) atomicAdd(&bv.marks_g[gu], 1);
+    }
+  }
+  __syncthreads();
+  // ---- phase 2: PR3/PR4 intersections, g lanes per queued entry
+  const int nq = q_n;
+  int g = 1;
+  while (g < 32 && nq * (2 * g) <= kETThreads) g *= 2;
+  const int lane = threadIdx.x & 31;
+  const int r = lane & (g - 1);
+  const unsigned gmask = g == 32 ? FULL : (((1u << g) - 1u) << (lane & ~(g - 1)));
+  for (int q = threadIdx.x / g; q < nq; q += kETThreads / g) {
+    const int u = q_u[q];
+    const long long e = e0 + (q_ef[q] & 0xffffu);
+    uint8_t f = (uint8_t)(q_ef[q] >> 16);
+    const int v = col[e];
+    int gu = 0;
+    if (batch) gu = bv.gid[u];
+    const long long lam = batch ? (long long)*(volatile unsigned long long*)&bv.lam_g[gu] : lam_global;
+    const long long c = (long long)w[e];
+    const long long du = (long long)deg[u], dv = (long long)deg[v];
+    // Without a flags output an edge whose endpoints are already joined in
+    // the union-find (by marks hooked so far) cannot change the contraction:
+    // skip its intersection.
+    bool joined = false;
+    if (!exact && r == 0) joined = uf_find(parent, u) == uf_find(parent, v);
+    joined = __shfl_sync(gmask, joined, 0, g);
+    if (!joined) {
+      const long long bu = rp[u], eu = rp[u + 1], bv_ = rp[v], ev = rp[v + 1];
+      const bool a_is_u = eu - bu <= ev - bv_;
+      const long long ab = a_is_u ? bu : bv_, ae = a_is_u ? eu : ev;
+      const long long bb = a_is_u ? bv_ : bu, be = a_is_u ? ev : eu;
+      const long long da = a_is_u ? du : dv;
+      long long sum = c;
+      bool pr3 = false;
+      // Without a flags output only "some test passes" matters, so the scan
+      // stops once the answer is known: PR4 reached, PR3 found, or neither
+      // still possible (rem = weight of a's unscanned edges bounds the PR4
+      // sum still to come; PR3 needs a single edge heavier than da/2 - c).
+      long long rem = da - c;
+      long long lo = bb;
+      bool lane_done = false;
+      // lane r of the group takes a's entries ab + r, ab + r + g, ...
+      for (long long base = ab; base < ae; base += g) {
+        const long long ea = base + r;
+        long long add = 0, used = 0;
+        bool p3 = false;
+        if (ea < ae && !lane_done) {
+          const int x = col[ea];
+          if (x != u && x != v) {
+            const long long cax = (long long)w[ea];
+            used = cax;
+            // a lane's neighbours ascend, so its search window only moves right
+            long long hi = be;
+            while (lo < hi) {
+              const long long mid = (lo + hi) >> 1;
+              if (col[mid] < x) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= be) {
+              lane_done = true;
+            } else if (col[lo] == x) {
+              const long long cbx = (long long)w[lo];
+              const long long cux = a_is_u ? cax : cbx, cvx = a_is_u ? cbx : cax;
+              add = cux < cvx ? cux : cvx;
+              p3 = du < 2 * (c + cux) && dv < 2 * (c + cvx);
+            }
+          }
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) {
+          add += __shfl_xor_sync(gmask, add, o, g);
+          used += __shfl_xor_sync(gmask, used, o, g);
+          p3 |= __shfl_xor_sync(gmask, (int)p3, o, g) != 0;
+        }
+        sum += add;
+        rem -= used;
+        pr3 = pr3 || p3;
+        if (!exact) {
+          if (((mask & 8u) && sum >= lam) || ((mask & 4u) && pr3)) break;
+          if (sum + rem < lam && !((mask & 4u) && 2 * (c + rem) > da)) break;
+        }
+        if (__all_sync(gmask, lane_done)) break;
+      }
+      if ((mask & 4u) && pr3) f |= 4;
+      if ((mask & 8u) && sum >= lam) f |= 8;
+    }
+    if (r == 0) {
+      if (exact) flags_out[e] = f;
+      if (f && u < v) {
+        if (!uf_union(parent, u, v)) uf_fail = true;
+        ++nmarks;
+        if (batch) atomicAdd(&bv.marks_g[gu], 1);
+      }
     }
   }
   if (uf_fail) set_error(st, ERR_INTERNAL);
