@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kETThreads)
 constexpr int kPrQueue = kET;
 
 template <typename WT>
-__global__ void __launch_bounds__(kETThreads)
+__global__ void __launch_bounds__(kETThreads, 5)
     pr_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
               const WT* __restrict__ w, const WT* __restrict__ deg,
               const int* __restrict__ tile_row, int ntiles, uint32_t mask, long long budget,
@@ -412,17 +412,25 @@ __global__ void __launch_bounds__(kETThreads)
   __shared__ int q_n;
   if (threadIdx.x == 0) q_n = 0;
   tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  // entry offsets fit 32 bits: graphs hold fewer than 2^31 entries
   const bool exact = flags_out != nullptr;
   const long long lam_global = (long long)*(volatile unsigned long long*)&st->lambda;
   const long long e0 = (long long)blockIdx.x * kET;
   unsigned long long nmarks = 0;
   bool uf_fail = false;
   // ---- phase 1: PR1/PR2, budget, queue
+  int pv[kETItems];
+#pragma unroll
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    pv[i] = e < M ? col[e] : 0;
+  }
+#pragma unroll
   for (int i = 0; i < kETItems; ++i) {
     const long long e = e0 + i * kETThreads + threadIdx.x;
     if (e >= M) break;
     const int u = tile_row_of(tr, rp, e);
-    const int v = col[e];
+    const int v = pv[i];
     if (u > v && !exact) continue;
     int gu = 0;
     if (batch) {
@@ -436,7 +444,7 @@ __global__ void __launch_bounds__(kETThreads)
     if ((mask & 1u) && c >= lam) f |= 1;
     if ((mask & 2u) && (du < 2 * c || dv < 2 * c)) f |= 2;
     if ((mask & 12u) && (exact || f == 0)) {
-      const long long lu = rp[u + 1] - rp[u], lv = rp[v + 1] - rp[v];
+      const int lu = (int)(rp[u + 1] - rp[u]), lv = (int)(rp[v + 1] - rp[v]);
       if (budget < 0 || min(lu, lv) <= budget) {
         const int slot = atomicAdd(&q_n, 1);
         q_u[slot] = u;
@@ -476,10 +484,10 @@ __global__ void __launch_bounds__(kETThreads)
     if (!exact && r == 0) joined = uf_find(parent, u) == uf_find(parent, v);
     joined = __shfl_sync(gmask, joined, 0, g);
     if (!joined) {
-      const long long bu = rp[u], eu = rp[u + 1], bv_ = rp[v], ev = rp[v + 1];
+      const int bu = (int)rp[u], eu = (int)rp[u + 1], bv_ = (int)rp[v], ev = (int)rp[v + 1];
       const bool a_is_u = eu - bu <= ev - bv_;
-      const long long ab = a_is_u ? bu : bv_, ae = a_is_u ? eu : ev;
-      const long long bb = a_is_u ? bv_ : bu, be = a_is_u ? ev : eu;
+      const int ab = a_is_u ? bu : bv_, ae = a_is_u ? eu : ev;
+      const int bb = a_is_u ? bv_ : bu, be = a_is_u ? ev : eu;
       const long long da = a_is_u ? du : dv;
       long long sum = c;
       bool pr3 = false;
@@ -488,11 +496,11 @@ __global__ void __launch_bounds__(kETThreads)
       // still possible (rem = weight of a's unscanned edges bounds the PR4
       // sum still to come; PR3 needs a single edge heavier than da/2 - c).
       long long rem = da - c;
-      long long lo = bb;
+      int lo = bb;
       bool lane_done = false;
       // lane r of the group takes a's entries ab + r, ab + r + g, ...
-      for (long long base = ab; base < ae; base += g) {
-        const long long ea = base + r;
+      for (int base = ab; base < ae; base += g) {
+        const int ea = base + r;
         long long add = 0, used = 0;
         bool p3 = false;
         if (ea < ae && !lane_done) {
@@ -501,9 +509,9 @@ __global__ void __launch_bounds__(kETThreads)
             const long long cax = (long long)w[ea];
             used = cax;
             // a lane's neighbours ascend, so its search window only moves right
-            long long hi = be;
+            int hi = be;
             while (lo < hi) {
-              const long long mid = (lo + hi) >> 1;
+              const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
               if (col[mid] < x) lo = mid + 1; else hi = mid;
             }
             if (lo >= be) {
@@ -551,6 +559,7 @@ __global__ void __launch_bounds__(kETThreads)
 constexpr int kLpShort = 128;       // rows up to this length use a warp table
 constexpr int kLpSlots = 256;       // slots of a warp table (power of two)
 constexpr int kLpWarps = 8;
+constexpr int kLpMidSmall = 1024;   // medium rows up to this length: small block tables
 constexpr int kLpMedium = 4096;     // rows up to this length use a block table
 constexpr int kLpMidSlots = 8192;
 
@@ -583,7 +592,8 @@ __global__ void __launch_bounds__(kLpWarps * 32)
     lp_short_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
                     const WT* __restrict__ w, const int* __restrict__ lab_in,
                     int* __restrict__ lab_out, int sweep, int* __restrict__ long_rows,
-                    int* long_count, int* __restrict__ mid_rows, int* mid_count) {
+                    int* long_count, int* __restrict__ mid_rows, int* mid_count,
+                    int* big_count) {
   __shared__ int s_key[kLpWarps][kLpSlots];
   __shared__ long long s_sc[kLpWarps][kLpSlots];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -604,7 +614,8 @@ __global__ void __launch_bounds__(kLpWarps * 32)
     }
     if (d > kLpShort) {
       if (lane == 0) {
-        if (d <= kLpMedium) mid_rows[atomicAdd(mid_count, 1)] = v;
+        if (d <= kLpMidSmall) mid_rows[atomicAdd(mid_count, 1)] = v;
+        else if (d <= kLpMedium) mid_rows[n - 1 - atomicAdd(big_count, 1)] = v;
         else long_rows[atomicAdd(long_count, 1)] = v;
       }
       continue;
@@ -640,36 +651,39 @@ __global__ void __launch_bounds__(kLpWarps * 32)
   }
 }
 
-// Medium rows: one block per row with a shared-memory table of 8192 slots.
-template <typename WT>
+// Medium rows: one block per row with a shared-memory table of up to SLOTS
+// slots (the smallest power of two >= 2d).  Scores are kept in the weight
+// type: a row's weighted degree fits it.  Rows are read as rows[dir * r].
+template <typename WT, int SLOTS>
 __global__ void __launch_bounds__(256)
     lp_mid_kernel(const int64_t* __restrict__ rp, const int* __restrict__ col,
                   const WT* __restrict__ w, const int* __restrict__ lab_in,
-                  int* __restrict__ lab_out, const int* __restrict__ rows, const int* count) {
+                  int* __restrict__ lab_out, const int* __restrict__ rows, int dir,
+                  const int* count) {
   extern __shared__ __align__(16) unsigned char lp_smem[];
-  long long* sc = reinterpret_cast<long long*>(lp_smem);
-  int* key = reinterpret_cast<int*>(sc + kLpMidSlots);
+  WT* sc = reinterpret_cast<WT*>(lp_smem);
+  int* key = reinterpret_cast<int*>(sc + SLOTS);
   __shared__ long long s_bs[8];
   __shared__ int s_bl[8];
   __shared__ long long s_own[8];
   const int cnt = *count;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int r = blockIdx.x; r < cnt; r += gridDim.x) {
-    const int v = rows[r];
+    const int v = rows[(long long)dir * r];
     const int own = lab_in[v];
     const long long b = rp[v], e = rp[v + 1];
     int slots = 256;  // smallest power of two >= 2d
-    while (slots < 2 * (e - b) && slots < kLpMidSlots) slots <<= 1;
+    while (slots < 2 * (e - b) && slots < SLOTS) slots <<= 1;
     for (int i = threadIdx.x; i < slots; i += blockDim.x) { key[i] = -1; sc[i] = 0; }
     __syncthreads();
     for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
       const int l = lab_in[col[i]];
-      const long long c = (long long)w[i];
+      const WT c = w[i];
       unsigned h = lp_hash(l) & (slots - 1);
       for (int p = 0; p < slots; ++p) {
         const int prev = atomicCAS(&key[h], -1, l);
         if (prev == -1 || prev == l) {
-          atomicAdd((unsigned long long*)&sc[h], (unsigned long long)c);
+          atomic_add_w(&sc[h], c);
           break;
         }
         h = (h + 1) & (slots - 1);
@@ -681,8 +695,8 @@ __global__ void __launch_bounds__(256)
     for (int i = threadIdx.x; i < slots; i += blockDim.x) {
       const int l = key[i];
       if (l < 0) continue;
-      best = ls_best(best, LabScore{sc[i], l});
-      if (l == own) own_s = sc[i];
+      best = ls_best(best, LabScore{(long long)sc[i], l});
+      if (l == own) own_s = (long long)sc[i];
     }
     best = warp_ls_best(best);
     own_s = warp_sum(own_s);
@@ -1273,19 +1287,26 @@ cudaError_t lp_sweep(int n, const int64_t* rp, const int* col, const WT* w, cons
   cudaMemsetAsync(sc.counts, 0, 4 * sizeof(int), s);
   cudaMemsetAsync(sc.pool_cursor, 0, sizeof(unsigned long long), s);
   lp_short_kernel<WT><<<grid_for((long long)n * 32, kLpWarps * 32), kLpWarps * 32, 0, s>>>(
-      n, rp, col, w, lab_in, lab_out, sweep, sc.long_rows, sc.counts, mid_rows, sc.counts + 1);
-  const size_t mid_smem = (size_t)kLpMidSlots * (sizeof(long long) + sizeof(int));
-  static bool mid_attr = false;
-  if (!mid_attr) {
-    cudaFuncSetAttribute(lp_mid_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)mid_smem);
-    cudaFuncSetAttribute(lp_mid_kernel<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)mid_smem);
-    mid_attr = true;
+      n, rp, col, w, lab_in, lab_out, sweep, sc.long_rows, sc.counts, mid_rows, sc.counts + 1,
+      sc.counts + 3);
+  // medium rows in two table sizes: up to kLpMidSmall entries (many blocks
+  // per SM) from the front of the list, longer ones from its back
+  constexpr int kSmallSlots = 2 * kLpMidSmall;
+  const size_t small_smem = (size_t)kSmallSlots * (sizeof(WT) + sizeof(int));
+  const size_t big_smem = (size_t)kLpMidSlots * (sizeof(WT) + sizeof(int));
+  static bool mid_attr[2] = {false, false};
+  if (!mid_attr[sizeof(WT) == 8]) {
+    cudaFuncSetAttribute(lp_mid_kernel<WT, kSmallSlots>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem);
+    cudaFuncSetAttribute(lp_mid_kernel<WT, kLpMidSlots>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
+    mid_attr[sizeof(WT) == 8] = true;
   }
-  lp_mid_kernel<WT><<<num_sms() * 2, 256, mid_smem, s>>>(rp, col, w, lab_in, lab_out, mid_rows,
-                                                         sc.counts + 1);
-  *launches += 2;
+  lp_mid_kernel<WT, kSmallSlots><<<num_sms() * 8, 256, small_smem, s>>>(
+      rp, col, w, lab_in, lab_out, mid_rows, 1, sc.counts + 1);
+  lp_mid_kernel<WT, kLpMidSlots><<<num_sms() * (sizeof(WT) == 8 ? 2 : 3), 256, big_smem, s>>>(
+      rp, col, w, lab_in, lab_out, mid_rows + (n - 1), -1, sc.counts + 3);
+  *launches += 3;
   if (sizeof(WT) == 8) {  // scores may exceed 32 bits: one block per long row
     lp_long_kernel<WT><<<num_sms() * 2, 512, 0, s>>>(rp, col, w, lab_in, lab_out, sc.long_rows,
                                                      sc.counts, sc.pool_lab, sc.pool_sc,

@@ -367,13 +367,30 @@ def test_lp_labels_bit_exact_short_rows():
         _lp_case((s.row_ptr, s.col, s.w.astype(np.int64)), n, int(rng.integers(1, 5)))
 
 
-def test_lp_labels_bit_exact_medium_and_long_rows():
-    # R-MAT cores have rows of every length class (warp, block, pooled tables)
+def _sym_weights(n, rp, col, lo, span):
+    """Symmetric pseudo-random weights in [lo, lo + span) keyed by the edge."""
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    a = np.minimum(src, col.astype(np.int64))
+    b = np.maximum(src, col.astype(np.int64))
+    return lo + (a * 1000003 + b * 7919) % span
+
+
+@pytest.mark.parametrize("weights", ["unit", "small", "int64_totals"])
+def test_lp_labels_bit_exact_medium_and_long_rows(weights):
+    # R-MAT cores have rows of every length class (warp table, small and large
+    # block tables, pooled tables for rows longer than 4096)
     s = synth.workload_rmat_core(scale=15, k=8, seed=9)
     d = np.diff(s.row_ptr)
-    assert d.max() > 1024 and ((d > 128) & (d <= 1024)).any()
+    assert ((d > 128) & (d <= 1024)).any() and ((d > 1024) & (d <= 4096)).any()
+    assert (d > 4096).any()
+    w = s.w.astype(np.int64)
+    if weights == "small":
+        w = _sym_weights(s.n, s.row_ptr, s.col, 1, 100)
+    elif weights == "int64_totals":
+        w = _sym_weights(s.n, s.row_ptr, s.col, 1 << 22, 1 << 23)
+        assert int(w.sum()) > 2 ** 31
     for iters in (1, 2, 3):
-        _lp_case((s.row_ptr, s.col, s.w.astype(np.int64)), s.n, iters)
+        _lp_case((s.row_ptr, s.col, w), s.n, iters)
 
 
 def test_lp_two_communities_bound():
