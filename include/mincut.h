@@ -244,6 +244,14 @@ int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t
  * 2^31); used by the server's admission control. */
 int64_t mincut_graph_footprint(int64_t n, int64_t m_directed);
 
+/* Graphs created without a user allocator take device memory from a pool per
+ * device owned by the library; blocks freed by mincut_graph_destroy stay in
+ * the pool for the next graph.  This returns the unused blocks of `device`'s
+ * pool to the driver (memory of live graphs is not touched).  The paper has
+ * no counterpart: this is memory management of the library.
+ * Returns MINCUT_ERR_INVALID for a device index outside [0, 64). */
+int mincut_release_cached(int device);
+
 /* ---- Serving: continuous batching of solve requests ------------------------
  * A server owns `workers` device workers, each with its own CUDA stream, so
  * admitted requests run concurrently.  A request is admitted when a worker

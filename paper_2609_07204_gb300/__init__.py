@@ -171,6 +171,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mincut_batch_solve.restype = ctypes.c_int
     lib.mincut_graph_footprint.argtypes = [i64, i64]
     lib.mincut_graph_footprint.restype = i64
+    lib.mincut_release_cached.argtypes = [ctypes.c_int]
+    lib.mincut_release_cached.restype = ctypes.c_int
     lib.mincut_server_default_options.argtypes = [ctypes.POINTER(MincutServerOptions)]
     lib.mincut_server_create.argtypes = [ctypes.POINTER(MincutServerOptions), ctypes.POINTER(vp)]
     lib.mincut_server_create.restype = ctypes.c_int
@@ -461,6 +463,12 @@ def mincut_contract_csr_noalloc(n: int, row_ptr, col, w, labels, n2: int, row_pt
         row_ptr_out.data_ptr(), col_out.data_ptr(), w_out.data_ptr(), ctypes.byref(m),
         ctypes.c_void_p(stream or 0)))
     return int(m.value)
+
+
+def mincut_release_cached(device: int = 0) -> None:
+    """Return the unused blocks of the library's device memory pool to the
+    driver (graphs created without a user allocator draw from that pool)."""
+    _check(load_library().mincut_release_cached(int(device)))
 
 
 def mincut_graph_footprint(n: int, m_directed: int) -> int:

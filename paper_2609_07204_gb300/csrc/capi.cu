@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -111,6 +112,7 @@ struct mincut_graph {
   int64_t* rp0 = nullptr;
   int* col0 = nullptr;
   void* w0 = nullptr;
+  cudaMemPool_t pool = nullptr;  // library pool of the graph's device (no user allocator)
   // current state (cur < 0: the input)
   int n = 0;
   long long M = 0;
@@ -206,14 +208,76 @@ struct ProfGuard {
   }
 };
 
+// Without a user allocator, device memory comes from a stream-ordered pool
+// per device owned by the library.  The pool keeps the blocks that graphs
+// free (no release threshold), so creating and destroying graphs of similar
+// size reuses mapped memory instead of mapping it again for every graph;
+// mincut_release_cached() hands the unused blocks back to the driver.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaMemPool_t lib_pool(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+// Pinned host mirrors of DevState, handed out from slabs that live as long
+// as the process (a page-locking call per graph costs more than the graph's
+// small solves).
+std::mutex g_pin_mu;
+std::vector<DevState*> g_pin_free;
+
+DevState* pinned_state_get() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    constexpr int kSlab = 64;
+    DevState* slab = nullptr;
+    if (cudaMallocHost(&slab, kSlab * sizeof(DevState)) != cudaSuccess) return nullptr;
+    for (int i = kSlab - 1; i >= 0; --i) g_pin_free.push_back(slab + i);
+  }
+  DevState* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return p;
+}
+
+void pinned_state_put(DevState* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
 void* dev_alloc(mincut_graph* g, size_t bytes) {
   bytes = std::max<size_t>(bytes, 16);
   bytes = (bytes + 255) / 256 * 256;
   void* p = nullptr;
   if (g->user_alloc) {
     p = g->alloc.alloc(bytes, (void*)g->stream, g->alloc.ctx);
-  } else if (cudaMallocAsync(&p, bytes, g->stream) != cudaSuccess) {
-    p = nullptr;
+  } else {
+    if (!g->pool) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      g->pool = lib_pool(dev);
+    }
+    const cudaError_t rc = g->pool ? cudaMallocFromPoolAsync(&p, bytes, g->pool, g->stream)
+                                   : cudaMallocAsync(&p, bytes, g->stream);
+    if (rc != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
   }
   if (p) g->allocs.push_back({p, bytes});
   return p;
@@ -241,7 +305,11 @@ void free_all(mincut_graph* g) {
     else cudaFreeAsync(a.p, g->stream);
   }
   g->allocs.clear();
-  if (g->hst) cudaFreeHost(g->hst);
+  if (g->hst) {
+    // the mirror may still be the target of a copy on the graph's stream
+    cudaStreamSynchronize(g->stream);
+    pinned_state_put(g->hst);
+  }
   g->hst = nullptr;
 }
 
@@ -741,8 +809,7 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
     delete g;
     return rc;
   };
-  if (cudaMallocHost(&g->hst, sizeof(DevState)) != cudaSuccess)
-    return bail(fail(MINCUT_ERR_OOM, "pinned state"));
+  if (!(g->hst = pinned_state_get())) return bail(fail(MINCUT_ERR_OOM, "pinned state"));
   if (!galloc(g, &g->st, 1) || !galloc(g, &g->m2_dev, 1)) return bail(fail(MINCUT_ERR_OOM, "state"));
   if (cudaMemsetAsync(g->st, 0, sizeof(DevState), s) != cudaSuccess)
     return bail(fail(MINCUT_ERR_CUDA, "memset state"));
@@ -1095,6 +1162,14 @@ const char* mincut_status_string(int status) {
 }
 
 const char* mincut_last_error(void) { return g_last_error.c_str(); }
+
+int mincut_release_cached(int device) {
+  if (device < 0 || device >= kMaxDevices) return fail(MINCUT_ERR_INVALID, "device %d", device);
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pools[device] && cudaMemPoolTrimTo(g_pools[device], 0) != cudaSuccess)
+    return fail(MINCUT_ERR_CUDA, "trim pool: %s", cudaGetErrorString(cudaGetLastError()));
+  return MINCUT_OK;
+}
 
 int64_t mincut_graph_footprint(int64_t n, int64_t m_directed) {
   if (n < 0 || m_directed < 0) return -1;

@@ -48,6 +48,7 @@ struct DevState {
   long long tile_counter[8];   // per-pass tile counters of the radix sort
   int lambda_src;              // 1 degree, 2 LP, 3 CAPFOREST (set by the witness step)
   int batch_done;              // graphs of a batch that finished
+  long long sym_balance;       // symmetry check: entries u < v minus entries u > v
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -354,8 +354,12 @@ __global__ void rp_fill_kernel(int64_t* rp2, int n2) {
     rp2[r] = 0;
 }
 
-// Symmetry: every entry (u, v, W) has the entry (v, u, W) (binary search in
-// the sorted row v).
+// Symmetry of a canonical graph (rows strictly increasing): every entry
+// (u, v, W) with u < v has its mirror (v, u, W) (binary search in the sorted
+// row v), and there are as many entries with u < v as with u > v.  The
+// mirrors found are distinct, so together the two facts give a one-to-one
+// pairing of all entries.  Each block adds its (u < v) - (u > v) count to
+// st->sym_balance; sym_final_kernel flags a non-zero balance.
 template <typename WT>
 __global__ void __launch_bounds__(kETThreads)
     symmetric_kernel(int n, long long M, const int64_t* __restrict__ rp,
@@ -365,11 +369,17 @@ __global__ void __launch_bounds__(kETThreads)
   tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
   const long long e0 = (long long)blockIdx.x * kET;
   bool bad = false;
+  int balance = 0;
   for (int i = 0; i < kETItems; ++i) {
     const long long e = e0 + i * kETThreads + threadIdx.x;
     if (e >= M) break;
     const int u = tile_row_of(tr, rp, e);
     const int v = col[e];
+    if (u > v) {
+      --balance;
+      continue;
+    }
+    ++balance;
     long long lo = rp[v], hi = rp[v + 1];
     while (lo < hi) {
       long long mid = (lo + hi) >> 1;
@@ -378,6 +388,13 @@ __global__ void __launch_bounds__(kETThreads)
     if (lo >= rp[v + 1] || col[lo] != u || w[lo] != w[e]) bad = true;
   }
   if (bad) set_error(st, ERR_ASYM);
+  balance = __reduce_add_sync(FULL, balance);
+  if ((threadIdx.x & 31) == 0 && balance)
+    atomicAdd((unsigned long long*)&st->sym_balance, (unsigned long long)(long long)balance);
+}
+
+__global__ void sym_final_kernel(DevState* st) {
+  if (st->sym_balance != 0) set_error(st, ERR_ASYM);
 }
 
 // ------------------------------------------------------------------ PR tests
@@ -1241,8 +1258,10 @@ cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* co
                             const int* tile_row, DevState* st, cudaStream_t s, int* launches) {
   if (M <= 0) return cudaSuccess;
   const int ntiles = (int)((M + kET - 1) / kET);
+  cudaMemsetAsync(&st->sym_balance, 0, sizeof(st->sym_balance), s);
   symmetric_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, tile_row, ntiles, st);
-  ++*launches;
+  sym_final_kernel<<<1, 1, 0, s>>>(st);
+  *launches += 2;
   return cudaGetLastError();
 }
 

@@ -69,6 +69,11 @@ def test_null_arguments(lib):
     lib.mincut_graph_destroy(None)  # ignored
 
 
+def test_release_cached_rejects_bad_device(lib):
+    assert lib.mincut_release_cached(-1) == mc.MINCUT_ERR_INVALID
+    assert lib.mincut_release_cached(64) == mc.MINCUT_ERR_INVALID
+
+
 def test_package_fails_loudly_without_library(tmp_path):
     with pytest.raises(RuntimeError, match="missing"):
         mc.load_library(str(tmp_path / "nope.so"))

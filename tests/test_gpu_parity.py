@@ -136,6 +136,23 @@ def test_from_csr_canonical_input_and_single_defects(defect, big):
     assert v == oracle.stoer_wagner(n, *c)[0]
 
 
+def test_graphs_reuse_pooled_memory_and_release():
+    """Graphs created one after another (library pool, pinned state mirrors
+    reused) give the same results; releasing the cached blocks between
+    graphs changes nothing."""
+    rng = np.random.default_rng(8)
+    rp, col, w = noncanonical(700, rng, 9000)
+    c = canon(700, rp, col, w)
+    exp = oracle.stoer_wagner(700, *c)[0]
+    for i in range(6):
+        g = make(700, rp, col, w)
+        assert_csr_equal(mc.mincut_graph_export_csr(g), c)
+        assert mc.mincut_solve(g, bitmap=False)[0] == exp
+        g.destroy()
+        if i % 2:
+            mc.mincut_release_cached(torch.cuda.current_device())
+
+
 def test_from_csr_device_pointers_and_torch_allocator():
     rng = np.random.default_rng(5)
     rp, col, w = noncanonical(400, rng, 5000)
@@ -148,10 +165,15 @@ def test_from_csr_device_pointers_and_torch_allocator():
     g.destroy()
 
 
-@pytest.mark.parametrize("case", ["asym", "neg", "range", "weight_asym"])
+@pytest.mark.parametrize("case", ["asym", "neg", "range", "weight_asym", "unpaired_lower"])
 def test_from_csr_rejects_malformed(case):
     rp, col, w = G.from_edges(4, [(0, 1), (1, 2), (2, 3)], [1, 2, 3])
     col = col.copy(); w = w.copy()
+    if case == "unpaired_lower":
+        # every entry u -> v with u < v has its mirror, but 3 -> 0 has none
+        rp = np.array([0, 1, 3, 5, 7], np.int64)
+        col = np.array([1, 0, 2, 1, 3, 0, 2], np.int32)
+        w = np.array([1, 1, 2, 2, 3, 4, 3], np.int64)
     if case == "asym":
         col[0] = 3  # 0->3 without 3->0
     elif case == "neg":
