@@ -113,6 +113,7 @@ struct mincut_graph {
   int* col0 = nullptr;
   void* w0 = nullptr;
   cudaMemPool_t pool = nullptr;  // library pool of the graph's device (no user allocator)
+  bool rowwise = true;           // contraction may take the row-wise path
   // current state (cur < 0: the input)
   int n = 0;
   long long M = 0;
@@ -138,6 +139,12 @@ struct mincut_graph {
   unsigned long long* lp_best = nullptr;
   long long* lp_cut = nullptr;
   int *lp_size = nullptr, *long_rows = nullptr, *long_count = nullptr, *pool_lab = nullptr;
+  // row-wise contraction (allocated at the first contraction that uses it)
+  RowScratch rows{};
+  int64_t* rpG = nullptr;
+  int* colG = nullptr;
+  void* wG = nullptr;
+  void* side_w = nullptr;
   long long* pool_sc = nullptr;
   long long pool_slots = 0;
   unsigned long long* pool_cursor = nullptr;
@@ -332,6 +339,24 @@ int set_lambda(mincut_graph* g, long long lam) {
   return MINCUT_OK;
 }
 
+int ensure_rows(mincut_graph* g) {
+  if (g->rows.cnt) return MINCUT_OK;
+  const size_t wsz = g->wt64 ? 8 : 4;
+  const long long n = g->n0, M = std::max<long long>(g->M0, 1);
+  RowScratch& r = g->rows;
+  if (!galloc(g, &r.cnt, n + 1) || !galloc(g, &r.gen, n + 1) || !galloc(g, &r.len, n + 1) ||
+      !galloc(g, &r.kcnt, n + 1) || !galloc(g, &r.off, n + 1) ||
+      !galloc(g, &r.part, (n + 1) / 4096 + 3) || !galloc(g, &r.total, 1) ||
+      !galloc(g, &r.side_v, M) || !galloc(g, &r.vinfo, n + 1) || !galloc(g, &g->rpG, n + 1) ||
+      !galloc(g, &g->colG, M) ||
+      !(g->wG = dev_alloc(g, (size_t)M * wsz)) || !(g->side_w = dev_alloc(g, (size_t)M * wsz))) {
+    r.cnt = nullptr;
+    return fail(MINCUT_ERR_OOM, "row-wise contraction buffers");
+  }
+  r.single_entries = &g->st->single_entries;
+  return MINCUT_OK;
+}
+
 int ensure_lp(mincut_graph* g) {
   if (g->lab[0]) return MINCUT_OK;
   const size_t wsz = g->wt64 ? 8 : 4;
@@ -350,6 +375,53 @@ int ensure_lp(mincut_graph* g) {
 
 // Contraction of the current graph by the union-find state in g->parent:
 // relabel, emit, sort, build; the result becomes the current graph.
+// Row-wise contraction of the current graph (most groups single vertices):
+// singleton rows rebuilt in place, the other rows through emit / sort /
+// build into a general CSR, then both placed into the next buffers.
+template <typename WT>
+int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out) {
+  cudaStream_t s = g->stream;
+  const int n = g->n;
+  const long long M = g->M;
+  const int vbits = bits_for(n2);
+  RowScratch& rs = g->rows;
+  { ProfScope ps(P_ROWS, M, s);
+    CK(rows_count<WT>(n, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, rs, (WT*)g->side_w, s,
+                      &g->launches)); }
+  CK(cudaMemsetAsync(&g->st->emit_count, 0, sizeof(long long), s));
+  { ProfScope ps(P_EMIT, M, s);
+    CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
+                      g->keys[0], (WT*)g->vals[0], g->st, 0, s, &g->launches, rs.gen)); }
+  int rc = sync_state(g);
+  if (rc) return rc;
+  const long long N = g->hst->emit_count;
+  bool alt = false;
+  CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
+                          2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
+  { ProfScope ps(P_BUILD, N, s);
+    CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
+                     vbits, n2, g->uid, g->part, g->rpG, g->colG, (WT*)g->wG, g->st, g->m2_dev,
+                     reinterpret_cast<int*>(alt ? g->keys[0] : g->keys[1]), s, &g->launches)); }
+  int mG = 0;
+  CK(cudaMemcpyAsync(&mG, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  { ProfScope ps(P_ROWS, M, s);
+    CK(rows_finish<WT>(n, n2, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, rs,
+                       (const WT*)g->side_w, g->rpG, g->colG, (const WT*)g->wG, mG, g->tile_row,
+                       g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], (WT*)g->degb[nxt], s,
+                       &g->launches)); }
+  int m2 = 0;
+  CK(cudaMemcpyAsync(&m2, rs.total, sizeof(int), cudaMemcpyDeviceToHost, s));
+  rc = sync_state(g);
+  if (rc) return rc;
+  *m2_out = m2;
+  return MINCUT_OK;
+}
+
+// Contraction of the current graph by the union-find state in g->parent:
+// relabel, then either the row-wise path (when at least a quarter of the
+// entries lie in rows of single-vertex groups) or emit / sort / build of all
+// entries; the result becomes the current graph.
 template <typename WT>
 int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compose) {
   cudaStream_t s = g->stream;
@@ -360,33 +432,51 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   int rc = sync_state(g);
   if (rc) return rc;
   const int n2 = g->hst->n_next;
-  const int vbits = bits_for(n2);
-  CK(cudaMemsetAsync(&g->st->emit_count, 0, sizeof(long long), s));
-  { ProfScope ps(P_EMIT, M, s);
-    CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
-                      g->keys[0], (WT*)g->vals[0], g->st, 0, s, &g->launches)); }
-  rc = sync_state(g);
-  if (rc) return rc;
-  const long long N = g->hst->emit_count;
-  bool alt = false;
-  CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
-                          2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
   const int nxt = g->cur == 0 ? 1 : 0;
-  { ProfScope ps(P_BUILD, N, s);
-    CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
-                     vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], g->st,
-                     g->m2_dev, s, &g->launches)); }
+  bool rowwise = false;
+  if (g->rowwise && n2 > 1 && M > 0) {
+    rc = ensure_rows(g);
+    if (rc) return rc;
+    { ProfScope ps(P_ROWS, n, s);
+      CK(rows_classify(n, n2, g->crp(), g->L, g->rows, s, &g->launches)); }
+    rc = sync_state(g);
+    if (rc) return rc;
+    rowwise = 4 * (long long)g->hst->single_entries >= M;
+  }
+  long long m2 = 0;
+  if (rowwise) {
+    rc = contract_rows<WT>(g, n2, nxt, &m2);
+    if (rc) return rc;
+  } else {
+    const int vbits = bits_for(n2);
+    CK(cudaMemsetAsync(&g->st->emit_count, 0, sizeof(long long), s));
+    { ProfScope ps(P_EMIT, M, s);
+      CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
+                        g->keys[0], (WT*)g->vals[0], g->st, 0, s, &g->launches)); }
+    rc = sync_state(g);
+    if (rc) return rc;
+    const long long N = g->hst->emit_count;
+    bool alt = false;
+    CK(radix_sort_pairs<WT>(g->keys[0], (WT*)g->vals[0], g->keys[1], (WT*)g->vals[1], (int)N,
+                            2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
+    { ProfScope ps(P_BUILD, N, s);
+      CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]),
+                       (int)N, vbits, n2, g->uid, g->part, g->rp[nxt], g->col[nxt],
+                       (WT*)g->w[nxt], g->st, g->m2_dev,
+                       reinterpret_cast<int*>(alt ? g->keys[0] : g->keys[1]), s, &g->launches)); }
+    int m2i = 0;
+    CK(cudaMemcpyAsync(&m2i, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    rc = sync_state(g);
+    if (rc) return rc;
+    m2 = m2i;
+    { ProfScope ps(P_DEGREE, m2, s);
+      CK(row_degrees<WT>(n2, m2, g->rp[nxt], (const WT*)g->w[nxt], g->tile_row, (WT*)g->degb[nxt],
+                         s, &g->launches)); }
+  }
   if (compose) {
     ProfScope ps(P_UF, g->n0, s);
     CK(compose_map(g->map0, g->L, g->n0, s, &g->launches));
   }
-  int m2 = 0;
-  CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-  rc = sync_state(g);
-  if (rc) return rc;
-  { ProfScope ps(P_DEGREE, m2, s);
-    CK(row_degrees<WT>(n2, m2, g->rp[nxt], (const WT*)g->w[nxt], g->tile_row, (WT*)g->degb[nxt], s,
-                       &g->launches)); }
   g->cur = nxt;
   g->n = n2;
   g->M = m2;
@@ -755,7 +845,8 @@ int canonicalize_input(mincut_graph* g, int n, long long Mraw, bool validate) {
                           2 * vbits, g->sort, g->st, g->spin_limit, s, &alt, &g->launches));
   CK(build_csr<WT>(alt ? g->keys[1] : g->keys[0], (WT*)(alt ? g->vals[1] : g->vals[0]), (int)N,
                    vbits, n, g->uid, g->part, g->rp[0], g->col[0], (WT*)g->w[0], g->st,
-                   g->m2_dev, s, &g->launches));
+                   g->m2_dev,
+                   reinterpret_cast<int*>(alt ? g->keys[0] : g->keys[1]), s, &g->launches));
   int m2 = 0;
   CK(cudaMemcpyAsync(&m2, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   rc = sync_state(g);
@@ -1179,8 +1270,9 @@ int64_t mincut_graph_footprint(int64_t n, int64_t m_directed) {
   cudaGetLastError();
   const long long P = graph_max_passes(n, sms);
   // 8-byte weights and sums double the weight terms; this bound assumes
-  // 4-byte ones (total weight < 2^31) plus the label-propagation buffers
-  return (int64_t)(140 * n + 90 * m_directed + 4096 * P + (1 << 20));
+  // 4-byte ones (total weight < 2^31) plus the label-propagation and the
+  // row-wise contraction buffers
+  return (int64_t)(164 * n + 106 * m_directed + 4096 * P + (1 << 20));
 }
 
 int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,

@@ -49,6 +49,7 @@ struct DevState {
   int lambda_src;              // 1 degree, 2 LP, 3 CAPFOREST (set by the witness step)
   int batch_done;              // graphs of a batch that finished
   long long sym_balance;       // symmetry check: entries u < v minus entries u > v
+  unsigned long long single_entries;  // contraction: entries of single-vertex groups' rows
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -71,7 +71,7 @@ void set_last_error(const char* msg);
 // stream (category, units processed).  Resolved after the stream synchronises.
 enum ProfCat {
   P_DEGREE, P_LP_SWEEP, P_LP_BOUND, P_PR, P_CF_PASSES, P_CF_SEQ, P_UF, P_EMIT,
-  P_SORT_HIST, P_SORT_PASS, P_BUILD, P_TILES, P_WITNESS, P_OTHER, P_NCAT
+  P_SORT_HIST, P_SORT_PASS, P_BUILD, P_TILES, P_WITNESS, P_OTHER, P_ROWS, P_NCAT
 };
 const char* prof_name(int cat);
 struct Profiler;
@@ -127,17 +127,22 @@ template <typename WT>
 cudaError_t degrees_min(const WT* deg, int n, unsigned long long* blk, DevState* st,
                         cudaStream_t s, int* launches);
 
+// Relabelled entries (L[u] << vbits | L[v], w) appended to keys/vals
+// (st->emit_count counts them); self-loops and zero weights dropped; with
+// keep_row, only entries whose new row r = L[u] has keep_row[r] != 0.
 template <typename WT>
 cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                        const int* L, int vbits, const int* tile_row, u64* keys, WT* vals,
-                       DevState* st, int validate, cudaStream_t s, int* launches);
+                       DevState* st, int validate, cudaStream_t s, int* launches,
+                       const int* keep_row = nullptr);
 
 // After sorting: unique keys -> canonical CSR (rp2[n2+1], col2, w2); the
-// number of unique entries goes to *m2_dev.  uid/part: N and N/4096+1 ints.
+// number of unique entries goes to *m2_dev.  uid/part: N and N/4096+1 ints;
+// urow: N ints of scratch (row of each unique entry).
 template <typename WT>
 cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
                       int* part, int64_t* rp2, int* col2, WT* w2, DevState* st, int* m2_dev,
-                      cudaStream_t s, int* launches);
+                      int* urow, cudaStream_t s, int* launches);
 
 template <typename WT>
 cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* col, const WT* w,
@@ -252,5 +257,41 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
                                        int* order, int max_graph_n, int always,
                                        const BatchView& bv, DevState* st, cudaStream_t s,
                                        int* launches);
+
+// ------------------------------------------------------------- contract.cu
+// Row-wise contraction when most groups are single vertices: singleton rows
+// are rebuilt in place, the rows of multi-member groups (and singleton rows
+// that do not fit) go through emit / sort / build as a general CSR.
+struct RowScratch {
+  int* cnt;     // n: members per group
+  int* gen;     // n: group's row takes the general path
+  int* len;     // n + 1: final row lengths
+  int* kcnt;    // n: distinct moved labels of a singleton row
+  int* off;     // n + 1: exclusive scan of len
+  int* part;    // scan partials (n / 4096 + 2)
+  int* total;   // 1: sum of len (the contracted entry count)
+  int* side_v;  // M: a singleton row's moved labels at the row's own offset
+  int* vinfo;   // n: L[x], with the top bit set when x's group has several members
+  unsigned long long* single_entries;  // entries of singleton groups' rows
+};
+
+// cnt, gen (multi-member groups) and *single_entries.
+cudaError_t rows_classify(int n, int n2, const int64_t* rp, const int* L, const RowScratch& rs,
+                          cudaStream_t s, int* launches);
+
+// Singleton rows: len, kcnt and the moved labels with their summed weights
+// (side_v / side_w); rows that do not fit are added to gen.
+template <typename WT>
+cudaError_t rows_count(int n, const int64_t* rp, const int* col, const WT* w, const int* L,
+                       const RowScratch& rs, WT* side_w, cudaStream_t s, int* launches);
+
+// Final CSR (rp2, col2, w2) and degrees deg2 from the singleton rows and the
+// general CSR (rpG over n2 rows, NG entries); rs.total = entries.
+template <typename WT>
+cudaError_t rows_finish(int n, int n2, const int64_t* rp, const int* col, const WT* w,
+                        const int* L, const RowScratch& rs, const WT* side_w,
+                        const int64_t* rpG, const int* colG, const WT* wG, long long NG,
+                        int* tile_row, int64_t* rp2, int* col2, WT* w2, WT* deg2,
+                        cudaStream_t s, int* launches);
 
 }  // namespace mc

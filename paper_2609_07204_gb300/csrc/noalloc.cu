@@ -140,7 +140,8 @@ int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t
   if (radix_sort_pairs<int32_t>(keys0, vals0, keys1, vals1, (int)N, 2 * vbits, sc, st,
                                 1ll << 22, s, &alt, &launches) != cudaSuccess ||
       build_csr<int32_t>(alt ? keys1 : keys0, alt ? vals1 : vals0, (int)N, vbits, n2i, uid, part,
-                         row_ptr_out, col_out, w_out, st, m2_dev, s, &launches) != cudaSuccess)
+                         row_ptr_out, col_out, w_out, st, m2_dev,
+                         reinterpret_cast<int*>(alt ? keys0 : keys1), s, &launches) != cudaSuccess)
     return na_fail(MINCUT_ERR_CUDA, "launch failed (sort/build)");
   int m2 = 0;
   if (cudaMemcpyAsync(&m2, m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -16,77 +16,11 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tiles.cuh"
 
 namespace mc {
 
 namespace {
-
-constexpr int kET = kEntryTile;
-constexpr int kETThreads = 256;
-constexpr int kETItems = kET / kETThreads;  // 8
-
-int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
-  }
-  return sms;
-}
-
-template <typename P>
-__device__ __forceinline__ int row_in(const P* a, int lo, int hi, long long x) {
-  while (hi - lo > 1) {
-    int mid = lo + ((hi - lo) >> 1);
-    if ((long long)a[mid] <= x) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// Shared-memory description of the rows covering one entry tile.
-struct TileRowsSmem {
-  long long rp[kET + 2];
-  int r0, r1, use;
-};
-
-__device__ __forceinline__ void tile_rows_load(TileRowsSmem& s, const int64_t* rp, int n,
-                                               const int* tile_row, int ntiles, int t) {
-  if (threadIdx.x == 0) {
-    s.r0 = tile_row[t];
-    s.r1 = (t + 1 < ntiles) ? tile_row[t + 1] : n - 1;
-    s.use = (s.r1 - s.r0 + 2) <= (kET + 2);
-  }
-  __syncthreads();
-  if (s.use)
-    for (int i = threadIdx.x; i < s.r1 - s.r0 + 2; i += blockDim.x) s.rp[i] = rp[s.r0 + i];
-  __syncthreads();
-}
-
-__device__ __forceinline__ int tile_row_of(const TileRowsSmem& s, const int64_t* rp, long long e) {
-  return s.use ? s.r0 + row_in(s.rp, 0, s.r1 - s.r0 + 1, e) : row_in(rp, s.r0, s.r1 + 1, e);
-}
-
-// Warp-level segmented sum over 32 consecutive entries whose segment keys
-// (row ids) are non-decreasing across lanes; the last lane of each segment
-// adds the segment's total to out[target].  Lanes with valid == false must
-// come after all valid lanes (tile tails).
-template <typename T, typename O>
-__device__ __forceinline__ void warp_segment_add(int seg, int target, T val, bool valid, O* out) {
-  const int lane = threadIdx.x & 31;
-  T x = valid ? val : T(0);
-  const int r = valid ? seg : -1;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const T y = __shfl_up_sync(FULL, x, o);
-    const int ry = __shfl_up_sync(FULL, r, o);
-    if (lane >= o && ry == r) x += y;
-  }
-  const int rn = __shfl_down_sync(FULL, r, 1);
-  const bool last = lane == 31 || rn != r;
-  if (valid && last && x != T(0)) atomic_add_w(&out[target], (O)x);
-}
 
 // Warp-level segmented maximum of packed 64-bit values (same layout rules).
 __device__ __forceinline__ void warp_segment_max(int seg, unsigned long long val, bool valid,
@@ -209,12 +143,20 @@ __global__ void __launch_bounds__(kETThreads)
     emit_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
                 const WT* __restrict__ w, const int* __restrict__ L, int vbits,
                 const int* __restrict__ tile_row, int ntiles, u64* __restrict__ keys,
-                WT* __restrict__ vals, DevState* st, int validate) {
+                WT* __restrict__ vals, DevState* st, int validate,
+                const int* __restrict__ keep_row) {
   __shared__ TileRowsSmem tr;
   __shared__ int s_cnt[kETItems][kETThreads / 32];
   __shared__ long long s_base;
   const int t = blockIdx.x;
   tile_rows_load(tr, rp, n, tile_row, ntiles, t);
+  if (keep_row) {
+    // a tile whose rows are all filtered out reads none of its entries
+    bool any = false;
+    for (int r = tr.r0 + threadIdx.x; r <= tr.r1 && !any; r += blockDim.x)
+      any = keep_row[L ? L[r] : r] != 0;
+    if (!__syncthreads_or(any)) return;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long e0 = (long long)t * kET;
   u64 key[kETItems];
@@ -227,16 +169,20 @@ __global__ void __launch_bounds__(kETThreads)
     bool keep = false;
     if (e < M) {
       const int u = tile_row_of(tr, rp, e);
-      const int v = col[e];
-      const WT c = w[e];
-      if (validate && (v < 0 || v >= n || c < 0)) {
-        bad = true;
+      const int lu = L ? L[u] : u;
+      if (keep_row && !keep_row[lu]) {
+        // row not emitted: its entries are not read
       } else {
-        const int lu = L ? L[u] : u;
-        const int lv = L ? L[v] : v;
-        keep = (lu != lv) && (c != 0);
-        key[i] = ((u64)(unsigned)lu << vbits) | (u64)(unsigned)lv;
-        val[i] = c;
+        const int v = col[e];
+        const WT c = w[e];
+        if (validate && (v < 0 || v >= n || c < 0)) {
+          bad = true;
+        } else {
+          const int lv = L ? L[v] : v;
+          keep = (lu != lv) && (c != 0);
+          key[i] = ((u64)(unsigned)lu << vbits) | (u64)(unsigned)lv;
+          val[i] = c;
+        }
       }
     }
     ball[i] = __ballot_sync(FULL, keep);
@@ -279,8 +225,7 @@ __global__ void head_flags_kernel(const u64* __restrict__ keys, int N, int* __re
 // rows before it.
 template <typename WT>
 __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict__ vals, int N,
-                              const int* __restrict__ uid, int vbits, int n2,
-                              const int* __restrict__ m2p, int64_t* __restrict__ rp2,
+                              const int* __restrict__ uid, int vbits, int* __restrict__ urow,
                               int* __restrict__ col2, WT* __restrict__ w2) {
   const u64 vmask = (vbits >= 64) ? ~0ull : ((1ull << vbits) - 1);
   const long long nchunks = ((long long)N + 7) / 8;
@@ -303,9 +248,7 @@ __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict
         acc = 0;
         run_started_here = true;
         col2[cur_uid] = (int)(k & vmask);
-        const int cu = (int)(k >> vbits);
-        const int pu = (i == 0) ? -1 : (int)(prev >> vbits);
-        for (int r = pu + 1; r <= cu; ++r) rp2[r] = cur_uid;
+        urow[cur_uid] = (int)(k >> vbits);
       } else if (cur_uid < 0) {
         // run continues from the previous chunk; uid is an exclusive scan of
         // head flags, so a non-head entry of run k holds k + 1
@@ -320,11 +263,21 @@ __global__ void segsum_kernel(const u64* __restrict__ keys, const WT* __restrict
       if (run_started_here && run_ends_here) w2[cur_uid] = (WT)acc;
       else atomic_add_w(&w2[cur_uid], (WT)acc);
     }
-    if (i1 == N) {
-      const int cu = (int)(prev >> vbits);
-      const int m2 = *m2p;
-      for (int r = cu + 1; r <= n2; ++r) rp2[r] = m2;
+  }
+}
+
+// rp2[r] = first unique entry whose row is >= r (rows of the unique entries
+// ascend); rp2[n2] = m2.
+__global__ void rp_search_kernel(const int* __restrict__ urow, const int* __restrict__ m2p, int n2,
+                                 int64_t* __restrict__ rp2) {
+  const int m2 = *m2p;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= n2; r += gridDim.x * blockDim.x) {
+    int lo = 0, hi = m2;
+    while (lo < hi) {
+      const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
+      if (urow[mid] < r) lo = mid + 1; else hi = mid;
     }
+    rp2[r] = lo;
   }
 }
 
@@ -1211,11 +1164,12 @@ cudaError_t degrees_min(const WT* deg, int n, unsigned long long* blk, DevState*
 template <typename WT>
 cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                        const int* L, int vbits, const int* tile_row, u64* keys, WT* vals,
-                       DevState* st, int validate, cudaStream_t s, int* launches) {
+                       DevState* st, int validate, cudaStream_t s, int* launches,
+                       const int* keep_row) {
   if (M <= 0) return cudaSuccess;
   const int ntiles = (int)((M + kET - 1) / kET);
   emit_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, L, vbits, tile_row, ntiles,
-                                                 keys, vals, st, validate);
+                                                 keys, vals, st, validate, keep_row);
   ++*launches;
   return cudaGetLastError();
 }
@@ -1223,7 +1177,7 @@ cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, co
 template <typename WT>
 cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
                       int* part, int64_t* rp2, int* col2, WT* w2, DevState* st,
-                      int* m2_dev, cudaStream_t s, int* launches) {
+                      int* m2_dev, int* urow, cudaStream_t s, int* launches) {
   if (N <= 0) {
     rp_fill_kernel<<<grid_for(n2 + 1, 256), 256, 0, s>>>(rp2, n2);
     cudaMemsetAsync(m2_dev, 0, sizeof(int), s);
@@ -1235,9 +1189,10 @@ cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2,
   cudaError_t err = scan_exclusive_i32(uid, uid, N, part, m2_dev, s, launches);
   if (err != cudaSuccess) return err;
   cudaMemsetAsync(w2, 0, (size_t)N * sizeof(WT), s);
-  segsum_kernel<WT><<<grid_for((N + 7) / 8, 256), 256, 0, s>>>(keys, vals, N, uid, vbits, n2,
-                                                               m2_dev, rp2, col2, w2);
-  ++*launches;
+  segsum_kernel<WT><<<grid_for((N + 7) / 8, 256), 256, 0, s>>>(keys, vals, N, uid, vbits, urow,
+                                                               col2, w2);
+  rp_search_kernel<<<grid_for(n2 + 1, 256), 256, 0, s>>>(urow, m2_dev, n2, rp2);
+  *launches += 2;
   return cudaGetLastError();
 }
 
@@ -1451,9 +1406,9 @@ cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream
                                        cudaStream_t, int*);                                      \
   template cudaError_t emit_pairs<WT>(int, long long, const int64_t*, const int*, const WT*,     \
                                       const int*, int, const int*, u64*, WT*, DevState*, int,    \
-                                      cudaStream_t, int*);                                       \
+                                      cudaStream_t, int*, const int*);                           \
   template cudaError_t build_csr<WT>(const u64*, const WT*, int, int, int, int*, int*, int64_t*, \
-                                     int*, WT*, DevState*, int*, cudaStream_t, int*);            \
+                                     int*, WT*, DevState*, int*, int*, cudaStream_t, int*);      \
   template cudaError_t row_degrees<WT>(int, long long, const int64_t*, const WT*, int*, WT*,      \
                                        cudaStream_t, int*);                                      \
   template cudaError_t check_symmetric<WT>(int, long long, const int64_t*, const int*,           \

@@ -226,6 +226,63 @@ def test_contract_by_pairs_bit_exact_and_chained():
     assert mc.mincut_graph_info(g) == (g0.n, g0.M)
 
 
+def _singleton_entry_share(n, rp, L):
+    cnt = np.bincount(L)
+    deg = np.diff(rp)
+    return float(deg[cnt[L] == 1].sum()) / max(int(rp[-1]), 1)
+
+
+@pytest.mark.parametrize("weights", ["unit", "int64_totals"])
+def test_contract_rowwise_bit_exact(weights):
+    """Rounds where most groups are single vertices take the row-wise path:
+    singleton rows rebuilt in place with the labels of multi-member groups
+    merged in (duplicates summed), rows longer than 4096 entries and rows
+    with more than 32 distinct multi-member neighbours through the sort.
+    Three chained contractions, each against the oracle's contraction."""
+    rng = np.random.default_rng(21)
+    s = synth.workload_rmat_core(scale=15, k=8, seed=9)
+    n, rp, col = s.n, s.row_ptr.copy(), s.col.copy()
+    w = s.w.astype(np.int64)
+    if weights == "int64_totals":
+        w = _sym_weights(n, rp, col, 1 << 22, 1 << 23)
+    deg = np.diff(rp)
+    assert deg.max() > 4096
+    g = make(n, rp, col, w)
+    n0, rp0, col0, w0 = n, rp, col, w
+    for step in range(3):
+        pu, pv = [], []
+        # groups of 2-6 random vertices
+        for _ in range(60):
+            mem = rng.choice(n, size=int(rng.integers(2, 7)), replace=False)
+            pu += [int(mem[0])] * (len(mem) - 1)
+            pv += [int(x) for x in mem[1:]]
+        # a row of 64..4096 entries whose neighbours fall into 40 groups
+        d = np.diff(rp)
+        cand = np.flatnonzero((d >= 64) & (d <= 4096))
+        h = int(cand[rng.integers(0, len(cand))])
+        nb = col[rp[h]:rp[h + 1]][:40]
+        others = rng.choice(n, size=40, replace=False)
+        pu += [int(x) for x in nb]
+        pv += [int(x) for x in others]
+        pu = np.asarray(pu, np.int32)
+        pv = np.asarray(pv, np.int32)
+        n2, L = oracle.labels_from_pairs(n, pu, pv)
+        assert _singleton_entry_share(n, rp, np.asarray(L)) >= 0.25
+        ro = mc.default_round_options()
+        ro.npairs = len(pu)
+        ro.pair_u = pu.ctypes.data
+        ro.pair_v = pv.ctypes.data
+        res = mc.mincut_contract_round(g, ro)
+        rp, col, w = oracle.contract(n, rp, col, w, L, n2)
+        n = n2
+        assert res["n_out"] == n2
+        assert_csr_equal(mc.mincut_graph_export_csr(g), (rp, col, w))
+    # a solve starts again from the input graph; its own rounds contract
+    # row-wise too
+    v, _, _ = mc.mincut_solve(g, bitmap=False)
+    assert v == oracle.noi(n0, rp0, col0, w0)[0]
+
+
 # ------------------------------------------------------------------ PR flags
 @pytest.mark.parametrize("budget", [-1, 3])
 def test_pr_flags_bit_exact(budget):
