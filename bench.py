@@ -54,6 +54,17 @@ ALG_BYTES = {
     "sort_pass": 24,        # read key + value (12), write key + value (12)
     "sort_hist": 8,         # read key
     "build_csr": 20,        # read key + value (12), write col + w (8)
+    "contract_rows": 10,    # row-wise contraction, two scopes per round over the
+                            # round's entries: count (read col, 4) and write
+                            # (read col + w, write col + w, 16)
+}
+
+# DRAM bytes per unit measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch on the R-MAT core's first round, the
+# capture summarised under profiles/), scaled to a launch by its units.  A
+# kernel changed since its capture has no entry here (traffic: null).
+TRAFFIC_PER_UNIT = {
+    "pr_marks": (566.063360e6 + 3.687424e6) / 29031216,
 }
 
 
@@ -371,8 +382,10 @@ def run_gpu(args, rank, world):
         alg_bytes = d["units"] * ALG_BYTES[dom] / d["launches"]
         avg_s = d["ms"] / d["launches"] / 1e3
         ach = alg_bytes / avg_s / 1e9
+        tpu = TRAFFIC_PER_UNIT.get(dom)
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": ach / peak, "peak_kind": peak_kind,
+                "traffic": (tpu * d["units"] / d["launches"]) if tpu else None,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": d["ms"] / d["launches"]}
     total_prof_ms = sum(v["ms"] for v in prof.values())
     line = {

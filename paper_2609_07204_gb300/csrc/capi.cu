@@ -437,7 +437,7 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   if (g->rowwise && n2 > 1 && M > 0) {
     rc = ensure_rows(g);
     if (rc) return rc;
-    { ProfScope ps(P_ROWS, n, s);
+    { ProfScope ps(P_UF, n, s);
       CK(rows_classify(n, n2, g->crp(), g->L, g->rows, s, &g->launches)); }
     rc = sync_state(g);
     if (rc) return rc;
