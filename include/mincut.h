@@ -81,6 +81,13 @@ typedef struct mincut_options {
     int32_t max_rounds;      /* 0 = unlimited */
     int64_t spin_limit;      /* iteration limit of bounded device waits (0 = default) */
     int32_t profile;         /* 1: time every kernel with CUDA events (mincut_profile_read) */
+    int32_t init_bound;      /* 0: bounds inside the rounds only (default); 1: first run the
+                                coarsening heuristic of Sec. 2.1 "Lowering the upper bound"
+                                (label-propagation clusters contracted, PR tests, repeated, then
+                                the coarse graph solved exactly) on graphs with n >= lp_min_n */
+    int32_t cf_visit;        /* visit array of the concurrent CAPFOREST passes (Sec. 4, parallel
+                                session (1)): 0 shared (default), 1 private to each pass,
+                                2 alternate over the first two rounds and keep the faster */
     int32_t reserved;
 } mincut_options;
 
@@ -92,7 +99,8 @@ typedef struct mincut_stats {
     int64_t marks_pr;            /* edges marked by PR1..PR4 over all rounds */
     int64_t marks_cf;            /* edges marked by CAPFOREST over all rounds */
     int64_t entries_processed;   /* sum over rounds of the round graph's directed entries */
-    int32_t lambda_source;       /* 1 degree, 2 label propagation, 3 CAPFOREST alpha */
+    int32_t lambda_source;       /* 1 degree, 2 label propagation, 3 CAPFOREST alpha,
+                                    4 coarsening heuristic (init_bound = 1) */
     int32_t kernel_launches;     /* kernels launched by the solve */
     double ms_total;             /* host wall time of the solve */
 } mincut_stats;

@@ -8,6 +8,10 @@
 // if r(y) < lambda <= r(y) + c(x, y) the edge is contractible (union-find
 // hook), r(y) += c(x, y), Q(y) = min(r(y), lambda).
 //
+// With private visit sets (private_visit = 1, Sec. 4 parallel session (1))
+// no vertex is claimed: every pass is its own maximum-adjacency ordering of
+// G from its start vertex, up to its table's capacity.
+//
 // capforest_passes: Algorithm 1 proper.  Many passes run at once, one warp
 // each, from seeded start vertices; the shared visit array T is `owner`
 // (a vertex is claimed by CAS, so each vertex is scanned by one pass; a pass
@@ -72,7 +76,7 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
                                  unsigned long long* __restrict__ pass_best,
                                  int* __restrict__ pass_len, int total_passes, int table,
                                  unsigned long long seed, int* pass_counter, DevState* st,
-                                 BatchView bv, int batch) {
+                                 BatchView bv, int batch, int priv) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -103,6 +107,7 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
     {
       const unsigned long long h = mix64(seed ^ mix64((unsigned long long)p + 1));
       const int s0 = (int)(h % (unsigned long long)n);
+      if (priv) start = s0;
       for (int tries = 0; tries < 4 && start < 0; ++tries) {
         const int c = (int)(((long long)s0 + tries * 32 + lane) % n);
         const unsigned free_mask = __ballot_sync(FULL, vowner[c] == 0);
@@ -165,9 +170,11 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
         __syncwarp();
         const long long rb = rp[x], re = rp[x + 1];
         if (count + (re - rb) > load_cap) break;  // the row might not fit: stop
-        int claimed = 0;
-        if (lane == 0) claimed = atomicCAS(&owner[x], 0, p + 1) == 0;
-        claimed = __shfl_sync(FULL, claimed, 0);
+        int claimed = 1;
+        if (!priv) {
+          if (lane == 0) claimed = atomicCAS(&owner[x], 0, p + 1) == 0;
+          claimed = __shfl_sync(FULL, claimed, 0);
+        }
         if (!claimed) continue;  // blacklisted: visited by another pass
         ++nscanned;
         if (lane == 0) visit_log[(long long)p * table + nscanned - 1] = x;
@@ -184,7 +191,7 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
           bool ins = false;
           if (e < re) {
             const int y = col[e];
-            if (vowner[y] == 0) {
+            if (priv || vowner[y] == 0) {
               unsigned h = slot_hash(y) & (table - 1);
               int s = -1;
               for (int probe = 0; probe < table; ++probe) {
@@ -571,7 +578,7 @@ cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT*
   if (bv) v = *bv;
   cf_passes_kernel<WT><<<blocks, pc.warps_per_block * 32, smem, s>>>(
       n, rp, col, w, deg, owner, parent, visit_log, pass_best, pass_len, pc.passes, pc.table,
-      pc.seed, pass_counter, st, v, bv ? 1 : 0);
+      pc.seed, pass_counter, st, v, bv ? 1 : 0, pc.private_visit);
   ++*launches;
   if (!bv) {
     cf_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, pc.passes, st);

@@ -491,6 +491,8 @@ struct RoundCfg {
   uint32_t pr_mask;
   long long pr_budget;
   int capforest;  // 0 none, 1 concurrent (+ sequential fallback), 2 sequential from cf_start
+  int cf_private = 0;  // concurrent passes with private visit sets
+  bool coarsen = false;  // heuristic round: also join every label-propagation cluster
   int cf_start;
   int passes, table;
   unsigned long long seed;
@@ -574,7 +576,9 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
                          cudaMemcpyDeviceToHost, s));
   }
   { ProfScope ps(P_UF, n, s);
-    CK(uf_init(g->parent, n, s, &g->launches)); }
+    CK(uf_init(g->parent, n, s, &g->launches));
+    if (c.coarsen && lab_final)
+      CK(uf_from_groups(g->parent, lab_final, g->gmin, n, g->st, s, &g->launches)); }
   uint8_t* flags_dev = c.pr_flags_host ? reinterpret_cast<uint8_t*>(g->vals[1]) : nullptr;
   if (c.pr_mask) {
     ProfScope ps(P_PR, M, s);
@@ -588,6 +592,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     pc.warps_per_block = 4;
     pc.passes = std::min(c.passes, g->max_passes);
     pc.seed = c.seed;
+    pc.private_visit = c.cf_private;
     ProfScope ps(P_CF_PASSES, M, s);
     CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log,
                             g->pass_best, g->pass_len, g->pass_counter, pc, g->st, s,
@@ -650,6 +655,118 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   return MINCUT_OK;
 }
 
+// Exact rounds (Algorithm 2 with the round of Sec. 2.1) from the graph's
+// current state until it stops; lambda is the best bound so far (its witness
+// already in side0).  cf_visit 2 runs the first round with the shared visit
+// array and the second with private ones, then keeps the mode that removed
+// more vertices per millisecond.
+template <typename WT>
+int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_allowed,
+                 long long* lambda_io, mincut_stats* stl, int* round_io) {
+  long long lambda = *lambda_io;
+  double rate[2] = {-1.0, -1.0};
+  int mode = op.cf_visit == 1 ? 1 : 0;
+  for (;; ++*round_io) {
+    const int round = *round_io;
+    if (op.max_rounds > 0 && round >= op.max_rounds) break;
+    if (op.cf_visit == 2) {
+      if (rate[0] < 0) mode = 0;
+      else if (rate[1] < 0) mode = 1;
+      else mode = rate[1] > rate[0] ? 1 : 0;
+    }
+    c.cf_private = mode;
+    c.lp_now = lp_allowed && (op.lp_every_round || round == 0);
+    c.passes = op.passes > 0 ? op.passes : std::max(32, std::min(g->max_passes, g->n / 4));
+    c.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int n_before = g->n;
+    RoundOut o;
+    int rc = mark_round<WT>(g, c, lambda, &o);
+    if (rc) return rc;
+    if (o.src) stl->lambda_source = o.src;
+    const bool improved = o.lambda < lambda;
+    lambda = std::min(lambda, o.lambda);
+    if (o.stopped) break;
+    stl->rounds++;
+    stl->entries_processed += g->M;
+    stl->marks_pr += o.marks_pr;
+    stl->marks_cf += o.marks_cf;
+    if (o.seq_pass) stl->seq_passes++;
+    if (lambda == 0) break;
+    if (o.marks_pr + o.marks_cf == 0) {
+      if (!improved) return fail(MINCUT_ERR_INTERNAL, "round made no progress");
+      continue;
+    }
+    int n2 = 0;
+    long long m2 = 0;
+    rc = contract_current<WT>(g, &n2, &m2, true);
+    if (rc) return rc;
+    if (op.cf_visit == 2 && rate[mode] < 0) {
+      const double ms = std::chrono::duration<double, std::milli>(
+                            std::chrono::steady_clock::now() - t0).count();
+      rate[mode] = (double)(n_before - n2) / std::max(ms, 1e-3);
+    }
+    if (n2 <= 1) break;
+  }
+  *lambda_io = lambda;
+  return MINCUT_OK;
+}
+
+// The coarsening heuristic of Sec. 2.1 ("Lowering the upper bound"): label
+// propagation clusters and the PR tests are contracted repeatedly while the
+// graph shrinks, then the coarse graph is solved exactly.  Every vertex of a
+// coarse graph is a set of input vertices, so the result is a cut of the
+// input graph (an upper bound, not necessarily minimum: a cluster may
+// straddle a minimum cut).  Leaves the bound in *lambda_io, its witness in
+// side0, and the graph reset to the input.
+template <typename WT>
+int coarsening_bound(mincut_graph* g, const mincut_options& op, const RoundCfg& base,
+                     long long* lambda_io, mincut_stats* stl) {
+  constexpr int kSmall = 1000;      // coarse graphs this small are solved exactly
+  constexpr int kMaxLevels = 32;
+  long long lambda = *lambda_io;
+  RoundCfg h = base;
+  h.lp_now = true;
+  h.lp_min_n = 2;  // the clustering runs at every level, down to the small graph
+  h.capforest = 0;
+  h.coarsen = true;
+  int src = 0;
+  for (int level = 0; level < kMaxLevels && g->n > kSmall; ++level) {
+    h.seed = op.seed ^ (0xC0A25E11ull * (unsigned long long)(level + 1));
+    RoundOut o;
+    int rc = mark_round<WT>(g, h, lambda, &o);
+    if (rc) return rc;
+    if (o.src) src = o.src;
+    lambda = std::min(lambda, o.lambda);
+    if (o.stopped || lambda == 0) break;
+    const int n_before = g->n;
+    int n2 = 0;
+    long long m2 = 0;
+    rc = contract_current<WT>(g, &n2, &m2, true);
+    if (rc) return rc;
+    if (n2 <= 1 || n2 > n_before - n_before / 10) break;  // clusters stopped shrinking it
+  }
+  if (g->n > 1 && lambda > 0) {
+    mincut_stats inner{};
+    int round = 0;
+    const long long before = lambda;
+    int rc = exact_rounds<WT>(g, op, base, false, &lambda, &inner, &round);
+    if (rc) return rc;
+    if (lambda < before) src = inner.lambda_source;
+  }
+  if (src) stl->lambda_source = 4;
+  // back to the input graph; the bound and its witness (side0) stay
+  g->cur = -1;
+  g->n = g->n0;
+  g->M = g->M0;
+  iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, g->stream>>>(g->map0, g->n0);
+  ++g->launches;
+  int rc = set_lambda(g, lambda);
+  if (rc) return rc;
+  *lambda_io = lambda;
+  return MINCUT_OK;
+}
+
 template <typename WT>
 int solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_value,
                uint64_t* side_bitmap, mincut_stats* stats) {
@@ -679,33 +796,16 @@ int solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_value,
   c.table = op.pass_table > 0 ? op.pass_table : g->max_table;
   c.table = std::min(c.table, g->max_table);
   c.seed = op.seed;
-  for (int round = 0;; ++round) {
-    if (op.max_rounds > 0 && round >= op.max_rounds) break;
-    c.lp_now = op.lp_every_round || round == 0;
-    c.passes = op.passes > 0 ? op.passes : std::max(32, std::min(g->max_passes, g->n / 4));
-    c.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
-    RoundOut o;
-    rc = mark_round<WT>(g, c, lambda, &o);
+  const bool heuristic = op.init_bound == 1 && op.lp_iters > 0 && g->n0 >= op.lp_min_n;
+  if (heuristic) {
+    rc = coarsening_bound<WT>(g, op, c, &lambda, &stl);
     if (rc) return rc;
-    if (o.src) stl.lambda_source = o.src;
-    const bool improved = o.lambda < lambda;
-    lambda = std::min(lambda, o.lambda);
-    if (o.stopped) break;
-    stl.rounds++;
-    stl.entries_processed += g->M;
-    stl.marks_pr += o.marks_pr;
-    stl.marks_cf += o.marks_cf;
-    if (o.seq_pass) stl.seq_passes++;
-    if (lambda == 0) break;
-    if (o.marks_pr + o.marks_cf == 0) {
-      if (!improved) return fail(MINCUT_ERR_INTERNAL, "round made no progress");
-      continue;
-    }
-    int n2 = 0;
-    long long m2 = 0;
-    rc = contract_current<WT>(g, &n2, &m2, true);
+  }
+  int round = 0;
+  if (lambda > 0) {
+    // with the heuristic's bound in hand, the rounds skip the LP bound
+    rc = exact_rounds<WT>(g, op, c, !heuristic, &lambda, &stl, &round);
     if (rc) return rc;
-    if (n2 <= 1) break;
   }
   *cut_value = lambda;
   if (side_bitmap) {
@@ -771,7 +871,8 @@ int contract_round_impl(mincut_graph* g, const mincut_round_options* ro,
   c.lp_now = true;
   c.pr_mask = ro->pr_mask;
   c.pr_budget = ro->pr_budget;
-  c.capforest = ro->capforest;
+  c.capforest = ro->capforest == 3 ? 1 : ro->capforest;
+  c.cf_private = ro->capforest == 3 ? 1 : 0;
   c.cf_start = ro->cf_start;
   if (c.capforest == 2 && (c.cf_start < 0 || c.cf_start >= n))
     return fail(MINCUT_ERR_INVALID, "cf_start out of range");
@@ -1077,6 +1178,7 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
       pc.passes = op.passes > 0 ? std::min(op.passes, g->max_passes)
                                 : std::max(32, std::min(g->max_passes, n / 4));
       pc.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
+      pc.private_visit = op.cf_visit == 1 ? 1 : 0;
       CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log, g->pass_best,
                               g->pass_len, g->pass_counter, pc, g->st, s, &g->launches, &v));
     }
@@ -1188,7 +1290,7 @@ int mincut_contract_round(mincut_graph* g, const mincut_round_options* ro,
   if (ro->pass_table != 0 && (ro->pass_table < 256 || ro->pass_table > 2048 ||
                               (ro->pass_table & (ro->pass_table - 1))))
     return fail(MINCUT_ERR_INVALID, "pass_table must be a power of two in [256, 2048]");
-  if (ro->capforest < 0 || ro->capforest > 2) return fail(MINCUT_ERR_INVALID, "capforest mode");
+  if (ro->capforest < 0 || ro->capforest > 3) return fail(MINCUT_ERR_INVALID, "capforest mode");
   return g->wt64 ? contract_round_impl<int64_t>(g, ro, res) : contract_round_impl<int32_t>(g, ro, res);
 }
 

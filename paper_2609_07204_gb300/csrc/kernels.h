@@ -219,6 +219,7 @@ struct PassConfig {
   int table;            // slots per pass (power of two, 256..2048)
   int warps_per_block;
   unsigned long long seed;
+  int private_visit = 0;  // 1: each pass has its own visit set (owner is not used)
 };
 // Concurrent CAPFOREST passes (Algorithm 1).  owner[n] must be zero on entry
 // (the shared visit array T); visit_log[passes*table], pass_best/pass_len

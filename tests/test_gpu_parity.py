@@ -478,8 +478,9 @@ def test_lp_two_communities_bound():
 
 
 # ---------------------------------------------------------- concurrent passes
-def test_concurrent_round_sound_brute_force():
-    rng = np.random.default_rng(51)
+@pytest.mark.parametrize("mode", [1, 3])  # shared / private visit sets
+def test_concurrent_round_sound_brute_force(mode):
+    rng = np.random.default_rng(51 + mode)
     for trial in range(60):
         n = int(rng.integers(4, 15))
         g0 = G.random_graph(n, float(rng.uniform(0.2, 1.0)), rng, 1, int(rng.integers(1, 9)))
@@ -487,7 +488,7 @@ def test_concurrent_round_sound_brute_force():
         lam_true, _ = oracle.mincut_brute(n, *c)
         g = make(n, c[0], c[1], c[2])
         ro = mc.default_round_options()
-        ro.capforest = 1
+        ro.capforest = mode
         ro.passes = int(rng.integers(1, 8))
         ro.seed = trial
         ro.lp_min_n = 4
@@ -510,6 +511,33 @@ def _check_solve(n, c, opts=None, expect=None):
     assert oracle.cut_weight(n, *c, side) == v
     g.destroy()
     return st
+
+
+@pytest.mark.parametrize("variant", ["private", "alternate", "coarsen", "coarsen_private"])
+def test_solve_paper_variants(variant):
+    """The variants of Sec. 4 (visit arrays private to each pass, or the two
+    settings alternated over the first rounds) and the coarsening heuristic
+    of Sec. 2.1 for the first bound give the exact minimum cut and a witness
+    of that weight on random, planted and R-MAT inputs."""
+    kw = {"private": dict(cf_visit=1), "alternate": dict(cf_visit=2),
+          "coarsen": dict(init_bound=1, lp_min_n=200),
+          "coarsen_private": dict(init_bound=1, cf_visit=1, lp_min_n=200)}[variant]
+    rng = np.random.default_rng(17)
+    cases = []
+    for trial in range(4):
+        n = int(rng.integers(300, 900))
+        g0 = G.random_graph(n, float(rng.uniform(0.01, 0.05)), rng, 1, 30, connected=True)
+        cases.append((n, canon(n, *g0), None))
+    s = synth.planted(1 << 10, 21 << 10, 30, 3, 1, 7)
+    c = (s.row_ptr, s.col, s.w.astype(np.int64))
+    cases.append((s.n, c, oracle.noi(s.n, *c)[0]))
+    s = synth.workload_rmat_core(scale=13, k=6, seed=4)
+    c = (s.row_ptr, s.col, s.w.astype(np.int64))
+    cases.append((s.n, c, oracle.noi(s.n, *c)[0]))
+    for n, c, exp in cases:
+        st = _check_solve(n, c, mc.default_options(seed=3, **kw), expect=exp)
+        if variant.startswith("coarsen") and n >= 200:
+            assert st["lambda_source"] in (1, 2, 3, 4)
 
 
 def test_solve_closed_forms():
