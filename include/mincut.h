@@ -88,7 +88,10 @@ typedef struct mincut_options {
     int32_t cf_visit;        /* visit array of the concurrent CAPFOREST passes (Sec. 4, parallel
                                 session (1)): 0 shared (default), 1 private to each pass,
                                 2 alternate over the first two rounds and keep the faster */
-    int32_t reserved;
+    int32_t seq_passes;      /* passes of the sequential CAPFOREST a round runs when the
+                                concurrent passes mark nothing, each a whole pass from its own
+                                start vertex with private arrays: 1 = the single pass of
+                                Algorithm 2; 0 = auto (one per SM, device memory permitting) */
 } mincut_options;
 
 /* Statistics of a solve (all optional to read). */

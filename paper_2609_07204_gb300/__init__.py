@@ -52,7 +52,7 @@ class MincutOptions(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("deterministic", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
                 ("profile", ctypes.c_int32), ("init_bound", ctypes.c_int32),
-                ("cf_visit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cf_visit", ctypes.c_int32), ("seq_passes", ctypes.c_int32)]
 
 
 class MincutStats(ctypes.Structure):

@@ -553,6 +553,78 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// Best of the simultaneous sequential passes: when one of them lowered the
+// bound it started from, cf_val / cf_pass / cf_len name it, with cf_pass =
+// -2 - k for pass k (the earlier concurrent passes' best stays otherwise).
+__global__ void cf_multi_best_kernel(const unsigned long long* __restrict__ pass_best,
+                                     const int* __restrict__ pass_len, int passes, DevState* st) {
+  __shared__ unsigned long long sv[32];
+  __shared__ int sp[32];
+  unsigned long long bv = ~0ull;
+  int bp = 0x7fffffff;
+  for (int p = threadIdx.x; p < passes; p += blockDim.x) {
+    const unsigned long long v = pass_best[p];
+    if (v < bv || (v == bv && p < bp)) { bv = v; bp = p; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v2 = __shfl_xor_sync(FULL, bv, o);
+    const int p2 = __shfl_xor_sync(FULL, bp, o);
+    if (v2 < bv || (v2 == bv && p2 < bp)) { bv = v2; bp = p2; }
+  }
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = bv; sp[threadIdx.x >> 5] = bp; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2)
+      if (sv[w2] < bv || (sv[w2] == bv && sp[w2] < bp)) { bv = sv[w2]; bp = sp[w2]; }
+    if (bv != ~0ull) {
+      st->cf_val = bv;
+      st->cf_pass = -2 - bp;
+      st->cf_len = pass_len[bp];
+    }
+  }
+}
+
+// Several sequential passes at once (private visit arrays): block k runs the
+// pass of Algorithm 2 from its own start vertex over the whole graph with its
+// own keys, tree and visit order (order + k*n), so each is a complete
+// maximum-adjacency ordering of G and its marks are sound by themselves.  A
+// pass lowers only its own copy of the bound; pass_best[k] / pass_len[k]
+// give its best alpha and prefix length for the witness.
+template <typename WT, typename KT>
+__global__ void __launch_bounds__(512)
+    cf_seq_multi_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
+                        const WT* __restrict__ w, const WT* __restrict__ deg,
+                        unsigned long long seed, int* parent, WT* g_r, KT* g_levels,
+                        long long tree_words, int* __restrict__ order,
+                        unsigned long long* __restrict__ pass_best, int* __restrict__ pass_len,
+                        int smem_from, int r_in_smem, DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int k = blockIdx.x;
+  const SeqTree tl = seq_tree(n);
+  KT* lev[8];
+  WT* rr;
+  seq_layout<WT, KT>(tl, smem_from, r_in_smem, smem, g_levels + (long long)k * tree_words,
+                     g_r + (long long)k * n, lev, &rr);
+  const int start = k == 0 ? 0 : (int)(mix64(seed ^ mix64((unsigned long long)k)) % (unsigned long long)n);
+  long long best_alpha;
+  int best_len, ns;
+  unsigned long long my_marks;
+  bool uf_fail;
+  seq_pass_body<WT, KT>(n, rp, col, 0, w, deg, start, parent, lev, tl, rr,
+                        order + (long long)k * n, nullptr, 0,
+                        (long long)*(volatile unsigned long long*)&st->lambda, &best_alpha,
+                        &best_len, &ns, &my_marks, &uf_fail);
+  const int lane = threadIdx.x & 31;
+  if (uf_fail) set_error(st, ERR_INTERNAL);
+  my_marks = warp_sum(my_marks);
+  if (lane == 0 && my_marks) atomicAdd(&st->marks_cf, my_marks);
+  if (threadIdx.x == 0) {
+    pass_best[k] = best_alpha >= 0 ? (unsigned long long)best_alpha : ~0ull;
+    pass_len[k] = best_len;
+    if (best_alpha >= 0) atomicMin(&st->lambda, (unsigned long long)best_alpha);
+  }
+}
+
 }  // namespace
 
 template <typename WT>
@@ -638,6 +710,47 @@ cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const
 }
 
 template <typename WT>
+cudaError_t capforest_sequential_multi(int n, const int64_t* rp, const int* col, const WT* w,
+                                       const WT* deg, int passes, unsigned long long seed,
+                                       int* parent, WT* r_pool, unsigned long long* tree_pool,
+                                       int* order_pool, unsigned long long* pass_best,
+                                       int* pass_len, DevState* st, cudaStream_t s,
+                                       int* launches) {
+  using KT = typename std::conditional<sizeof(WT) == 4, unsigned, unsigned long long>::type;
+  const size_t limit = 200 * 1024;
+  const SeqTree t = seq_tree(n);
+  size_t used = 0;
+  int smem_from = t.levels + 1;
+  for (int l = t.levels; l >= 1; --l) {
+    const size_t b = (size_t)t.size[l] * sizeof(KT);
+    if (used + b > limit) break;
+    used += b;
+    smem_from = l;
+  }
+  const size_t lev_bytes = (used + 15) / 16 * 16;
+  int r_in_smem = 0;
+  size_t smem = used;
+  if (smem_from == 1 && lev_bytes + (size_t)n * sizeof(WT) <= limit) {
+    r_in_smem = 1;
+    smem = lev_bytes + (size_t)n * sizeof(WT);
+  }
+  static bool attr[2] = {false, false};
+  const int ai = sizeof(WT) == 8 ? 1 : 0;
+  if (!attr[ai]) {
+    cudaFuncSetAttribute(cf_seq_multi_kernel<WT, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)limit);
+    attr[ai] = true;
+  }
+  cf_seq_multi_kernel<WT, KT><<<passes, 512, smem, s>>>(
+      n, rp, col, w, deg, seed, parent, r_pool, reinterpret_cast<KT*>(tree_pool),
+      seq_tree_words(n) * (long long)(sizeof(unsigned long long) / sizeof(KT)), order_pool,
+      pass_best, pass_len, smem_from, r_in_smem, st);
+  cf_multi_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, passes, st);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+template <typename WT>
 cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col, const WT* w,
                                        const WT* deg, int* parent, WT* r,
                                        unsigned long long* levels, const long long* level_off,
@@ -675,6 +788,9 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
                                                 const WT*, int, int*, WT*, uint8_t*,          \
                                                 unsigned long long*, int*, int*, long long,   \
                                                 DevState*, cudaStream_t, int*);               \
+  template cudaError_t capforest_sequential_multi<WT>(                                        \
+      int, const int64_t*, const int*, const WT*, const WT*, int, unsigned long long, int*,    \
+      WT*, unsigned long long*, int*, unsigned long long*, int*, DevState*, cudaStream_t, int*); \
   template cudaError_t capforest_sequential_batch<WT>(                                        \
       int, const int64_t*, const int*, const WT*, const WT*, int*, WT*, unsigned long long*,   \
       const long long*, int*, int, int, const BatchView&, DevState*, cudaStream_t, int*);

@@ -157,6 +157,11 @@ struct mincut_graph {
   uint8_t* seq_vis = nullptr;
   unsigned long long* seq_tree = nullptr;
   int* seq_order = nullptr;
+  // several sequential passes at once (allocated at first use)
+  int seq_multi_k = 0;
+  void* seq_multi_r = nullptr;
+  unsigned long long* seq_multi_tree = nullptr;
+  int* seq_multi_order = nullptr;
   // sort
   SortScratch sort{};
   // state
@@ -357,6 +362,25 @@ int ensure_rows(mincut_graph* g) {
   return MINCUT_OK;
 }
 
+// Buffers of up to `want` simultaneous sequential passes over graphs of up
+// to n0 vertices, capped at about 2 GB; returns the number of passes they
+// hold (at least 1 when the allocation succeeded, 0 on failure).
+int ensure_seq_multi(mincut_graph* g, int want) {
+  if (g->seq_multi_k >= want) return want;
+  if (g->seq_multi_k > 0) return g->seq_multi_k;
+  const size_t wsz = g->wt64 ? 8 : 4;
+  const long long n = g->n0;
+  const long long per = n * (long long)(4 + wsz) + seq_tree_words((int)n) * 8;
+  const long long cap = std::max<long long>(1, (2ll << 30) / std::max<long long>(per, 1));
+  const int k = (int)std::min<long long>(want, cap);
+  if (!(g->seq_multi_r = dev_alloc(g, (size_t)k * n * wsz)) ||
+      !galloc(g, &g->seq_multi_tree, (long long)k * seq_tree_words((int)n)) ||
+      !galloc(g, &g->seq_multi_order, (long long)k * n))
+    return 0;
+  g->seq_multi_k = k;
+  return k;
+}
+
 int ensure_lp(mincut_graph* g) {
   if (g->lab[0]) return MINCUT_OK;
   const size_t wsz = g->wt64 ? 8 : 4;
@@ -492,6 +516,7 @@ struct RoundCfg {
   long long pr_budget;
   int capforest;  // 0 none, 1 concurrent (+ sequential fallback), 2 sequential from cf_start
   int cf_private = 0;  // concurrent passes with private visit sets
+  int seq_passes = 1;  // sequential passes when the concurrent ones mark nothing
   bool coarsen = false;  // heuristic round: also join every label-propagation cluster
   int cf_start;
   int passes, table;
@@ -605,6 +630,26 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   long long marks = (long long)(g->hst->marks_pr + g->hst->marks_cf);
   o->marks_pr = (long long)g->hst->marks_pr;
   bool need_seq = c.capforest == 2 || (c.capforest == 1 && marks == 0);
+  // several whole passes from different start vertices, each with private
+  // arrays, when the concurrent passes found nothing (not in the modes that
+  // report the single pass's order and marks)
+  if (need_seq && (long long)g->hst->lambda > 0 && c.capforest == 1 && c.seq_passes > 1 &&
+      !c.cf_marks_host && !c.cf_order_host) {
+    const int k = ensure_seq_multi(g, std::min({c.seq_passes, std::max(2, n / 2), g->max_passes}));
+    if (k > 1) {
+      {
+        ProfScope ps(P_CF_SEQ, M, s);
+        CK(capforest_sequential_multi<WT>(n, rp, col, w, deg, k, c.seed, g->parent,
+                                          (WT*)g->seq_multi_r, g->seq_multi_tree,
+                                          g->seq_multi_order, g->pass_best, g->pass_len, g->st, s,
+                                          &g->launches));
+      }
+      rc = sync_state(g);
+      if (rc) return rc;
+      o->seq_pass = true;
+      need_seq = false;
+    }
+  }
   // the sequential pass is only useful while the bound is positive
   if (need_seq && (long long)g->hst->lambda > 0) {
     const long long cap = c.cf_marks_host ? std::min(c.cf_marks_cap, M / 2 + 1) : 0;
@@ -641,8 +686,9 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
       CK(side_from_label(g->side0, g->map0, g->n0, lab_final, h.lp_label, s, &g->launches));
       o->src = 2;
     } else if (h.cf_val == (unsigned long long)lam) {
-      const int* list = h.cf_pass >= 0 ? g->visit_log + (long long)h.cf_pass * c.table
-                                       : g->seq_order;
+      const int* list = h.cf_pass <= -2 ? g->seq_multi_order + (long long)(-2 - h.cf_pass) * n
+                        : h.cf_pass >= 0  ? g->visit_log + (long long)h.cf_pass * c.table
+                                          : g->seq_order;
       ProfScope ps(P_WITNESS, g->n0, s);
       CK(side_from_list(g->side0, g->map0, g->n0, g->cur_side, n, list, h.cf_len, s,
                         &g->launches));
@@ -796,6 +842,7 @@ int solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_value,
   c.table = op.pass_table > 0 ? op.pass_table : g->max_table;
   c.table = std::min(c.table, g->max_table);
   c.seed = op.seed;
+  c.seq_passes = op.seq_passes > 0 ? op.seq_passes : g->sms;
   const bool heuristic = op.init_bound == 1 && op.lp_iters > 0 && g->n0 >= op.lp_min_n;
   if (heuristic) {
     rc = coarsening_bound<WT>(g, op, c, &lambda, &stl);

@@ -251,6 +251,20 @@ long long seq_tree_words(int n);
 // round (always != 0: regardless of marks).  r[] is indexed by current
 // vertex; levels at level_off[g] (words of the key type); order at the
 // graph's vertex offset, as local ids.
+// `passes` sequential passes at once, pass k from its own start vertex (pass
+// 0 from vertex 0) with private keys and visit order: r_pool passes*n WT,
+// tree_pool passes*seq_tree_words(n) u64 (only the parts that do not fit in
+// shared memory are used), order_pool passes*n ints.  A pass that lowers the
+// bound lowers st->lambda; the best such pass k sets st->cf_val, cf_len and
+// cf_pass = -2 - k (its visit order is order_pool + k*n).
+template <typename WT>
+cudaError_t capforest_sequential_multi(int n, const int64_t* rp, const int* col, const WT* w,
+                                       const WT* deg, int passes, unsigned long long seed,
+                                       int* parent, WT* r_pool, unsigned long long* tree_pool,
+                                       int* order_pool, unsigned long long* pass_best,
+                                       int* pass_len, DevState* st, cudaStream_t s,
+                                       int* launches);
+
 template <typename WT>
 cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col, const WT* w,
                                        const WT* deg, int* parent, WT* r,

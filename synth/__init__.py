@@ -62,6 +62,8 @@ def _load():
         lib.synth_planted.argtypes = [i64, i64, i64, i64, i32, u64, G,
                                       ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8))]
         lib.synth_cycle_plus.argtypes = [i64, dbl, i32, i32, u64, G]
+        lib.synth_wheel.argtypes = [i64, u64, G]
+        lib.synth_dblcyc.argtypes = [i64, i32, i32, u64, G]
         lib.synth_truncate_lcc.argtypes = [G, i64, ctypes.c_int, G]
         lib.synth_batch_params.argtypes = [u64, i64, i64, i64, dbl, dbl, ctypes.POINTER(i64),
                                            ctypes.POINTER(dbl), ctypes.POINTER(u64)]
@@ -171,6 +173,24 @@ def planted(nb: int, mb: int, kcore: int, cross: int, cross_w: int = 1, seed: in
                     "seed": seed})
     out.meta["block"] = block
     return out
+
+
+def wheel(n: int, seed: int = 6) -> Graph:
+    """Hub plus a rim cycle of n-1 vertices, spokes 2, rim edges n-2: every
+    vertex has weighted degree 2(n-1) = lambda (all trivial cuts minimum)."""
+    g = _CGraph()
+    if _load().synth_wheel(n, seed, ctypes.byref(g)) != 0:
+        raise ValueError(f"synth_wheel({n}) failed")
+    return _take(g, {"kind": "wheel", "n": n, "seed": seed, "lambda": 2 * (n - 1)})
+
+
+def dblcyc(n: int, heavy: int = 1000, light: int = 3, seed: int = 7) -> Graph:
+    """Hamiltonian cycle of weight `heavy` plus a stride-2 cycle of weight
+    `light` on each half (n = 2h, h odd): lambda = 2*heavy, the halves."""
+    g = _CGraph()
+    if _load().synth_dblcyc(n, heavy, light, seed, ctypes.byref(g)) != 0:
+        raise ValueError(f"synth_dblcyc({n}) failed")
+    return _take(g, {"kind": "dblcyc", "n": n, "seed": seed, "lambda": 2 * heavy})
 
 
 def cycle_plus(n: int, d: float, wlo: int = 1, whi: int = 100, seed: int = 4) -> Graph:

@@ -494,6 +494,85 @@ int synth_cycle_plus(int64_t n, double d, int32_t wlo, int32_t whi, uint64_t see
     return 0;
 }
 
+/* ---- adversarial families: every edge fails the PR tests and each round
+ * of a contraction algorithm that relies on them can merge only a few
+ * vertices.  Both are built from pairs with weights, ids permuted by seed. */
+typedef struct { uint64_t key; int32_t w; } wpair;
+
+static int wpair_cmp(const void* a, const void* b) {
+    const uint64_t x = ((const wpair*)a)->key, y = ((const wpair*)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static void csr_from_wpairs(int64_t n, wpair* pr, int64_t m, uint64_t seed, synth_graph* g) {
+    uint64_t s = seed;
+    int32_t* perm = (int32_t*)xmalloc((size_t)n * sizeof(int32_t));
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    for (int64_t i = n - 1; i > 0; --i) {
+        int64_t j = (int64_t)sm64_below(&s, (uint64_t)(i + 1));
+        int32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        const int64_t u = (int64_t)(pr[i].key >> 32), v = (int64_t)(pr[i].key & 0xffffffffull);
+        pr[i].key = pair_key(perm[u], perm[v]);
+    }
+    qsort(pr, (size_t)m, sizeof(wpair), wpair_cmp);
+    uint64_t* keys = (uint64_t*)xmalloc((size_t)m * sizeof(uint64_t));
+    int32_t* wt = (int32_t*)xmalloc((size_t)m * sizeof(int32_t));
+    for (int64_t i = 0; i < m; ++i) { keys[i] = pr[i].key; wt[i] = pr[i].w; }
+    csr_from_pairs(n, keys, wt, m, g);
+    free(keys);
+    free(wt);
+    free(perm);
+}
+
+/* Wheel: hub plus a rim cycle of n-1 vertices; spokes of weight 2, rim edges
+ * of weight n-2, so every vertex has weighted degree 2(n-1) and all n trivial
+ * cuts are minimum: a cut that keeps the hub on one side and a proper part S
+ * of the rim on the other crosses at least two rim edges, 2(n-2) + 2|S| >=
+ * 2(n-1).  lambda = 2(n-1).  n >= 5. */
+int synth_wheel(int64_t n, uint64_t seed, synth_graph* g) {
+    if (n < 5 || 2 * (n - 1) > 0x7fffffffll) return -1;
+    const int64_t r = n - 1, m = 2 * r;
+    wpair* pr = (wpair*)xmalloc((size_t)m * sizeof(wpair));
+    for (int64_t i = 0; i < r; ++i) {
+        pr[i].key = pair_key(0, 1 + i);
+        pr[i].w = 2;
+        pr[r + i].key = pair_key(1 + i, 1 + (i + 1) % r);
+        pr[r + i].w = (int32_t)(n - 2);
+    }
+    csr_from_wpairs(n, pr, m, seed, g);
+    free(pr);
+    return 0;
+}
+
+/* Two interleaved cycles: a Hamiltonian cycle 0-1-...-(n-1)-0 of weight
+ * `heavy`, and on each half {0..h-1}, {h..n-1} (h = n/2, odd) the cycle
+ * j -> j+2 (mod h) of weight `light`.  Any proper cut crosses the Hamiltonian
+ * cycle at least twice; it avoids the light cycles only if each half lies on
+ * one side, so the two halves are the unique minimum cut and lambda =
+ * 2*heavy; every other cut is at least 2*heavy + 2*light.  n = 2h, h >= 5
+ * odd. */
+int synth_dblcyc(int64_t n, int32_t heavy, int32_t light, uint64_t seed, synth_graph* g) {
+    const int64_t h = n / 2;
+    if (n != 2 * h || h < 5 || (h & 1) == 0 || heavy < 1 || light < 1) return -1;
+    const int64_t m = n + n;
+    wpair* pr = (wpair*)xmalloc((size_t)m * sizeof(wpair));
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        pr[k].key = pair_key(i, (i + 1) % n);
+        pr[k++].w = heavy;
+    }
+    for (int64_t half = 0; half < 2; ++half)
+        for (int64_t j = 0; j < h; ++j) {
+            pr[k].key = pair_key(half * h + j, half * h + (j + 2) % h);
+            pr[k++].w = light;
+        }
+    csr_from_wpairs(n, pr, m, seed, g);
+    free(pr);
+    return 0;
+}
+
 /* Parameters of graph i of the batched workload, drawn from seed: n
  * log-uniform in [nlo, nhi], average degree uniform in [dlo, dhi]. */
 void synth_batch_params(uint64_t seed, int64_t i, int64_t nlo, int64_t nhi, double dlo,

@@ -540,6 +540,30 @@ def test_solve_paper_variants(variant):
             assert st["lambda_source"] in (1, 2, 3, 4)
 
 
+@pytest.mark.parametrize("kind", ["wheel", "dblcyc"])
+@pytest.mark.parametrize("seq_passes,cf_visit", [(1, 0), (0, 0), (0, 1), (0, 2)])
+def test_solve_adversarial_families(kind, seq_passes, cf_visit):
+    """Families that defeat the PR tests (all trivial cuts minimum; a hidden
+    unique minimum below many near-minimum cuts) solved exactly with the
+    single sequential pass of Algorithm 2 or several whole passes at once."""
+    n = 257 if kind == "wheel" else 258
+    g = synth.wheel(n, seed=3) if kind == "wheel" else synth.dblcyc(n, 1000, 3, seed=3)
+    c = (g.row_ptr, g.col, g.w.astype(np.int64))
+    st = _check_solve(n, c, mc.default_options(seq_passes=seq_passes, cf_visit=cf_visit),
+                      expect=g.meta["lambda"])
+    if kind == "dblcyc" and seq_passes == 1 and cf_visit == 0:
+        assert st["rounds"] > n // 4  # one merge per round: Theta(n) rounds
+
+
+def test_solve_dblcyc_private_passes_then_sequential_passes():
+    """Private concurrent passes that lower the bound without marking, then
+    several sequential passes that do not lower it further: the witness of
+    the bound stays the concurrent pass's prefix."""
+    g = synth.dblcyc(1026, 1000, 3, seed=7)
+    c = (g.row_ptr, g.col, g.w.astype(np.int64))
+    _check_solve(g.n, c, mc.default_options(cf_visit=1, seq_passes=0), expect=2000)
+
+
 def test_solve_closed_forms():
     cases = [(G.cycle(50), 50, 2), (G.complete(12), 12, 11), (G.hypercube(6), 64, 6),
              (G.grid(9, 11), 99, 2), (G.complete_bipartite(3, 9), 12, 3),

@@ -184,6 +184,43 @@ def test_noi_planted_cut_small():
     assert np.array_equal(side, blk ^ blk[0])
 
 
+@pytest.mark.parametrize("n", [5, 6, 9, 16, 17])
+def test_wheel_all_trivial_cuts_minimum(n):
+    # closed form: every vertex has weighted degree 2(n-1) and no cut is lighter
+    g = synth.wheel(n, seed=n)
+    c = (g.row_ptr, g.col, g.w.astype(np.int64))
+    deg = oracle.degrees(n, *c)
+    assert (deg == 2 * (n - 1)).all()
+    b, s_, q, *_ = mincut_all(n, c)
+    assert b == s_ == q == 2 * (n - 1)
+
+
+@pytest.mark.parametrize("n", [10, 14, 18])
+def test_dblcyc_halves_are_the_unique_minimum(n):
+    # closed form: lambda = 2*heavy, attained only by the two halves (brute
+    # force over all cuts for n <= 18 checks uniqueness)
+    heavy, light = 50, 3
+    g = synth.dblcyc(n, heavy, light, seed=n)
+    c = (g.row_ptr, g.col, g.w.astype(np.int64))
+    b, s_, q, *_ = mincut_all(n, c)
+    assert b == s_ == q == 2 * heavy
+    vals = []
+    for mask in range(1, 1 << (n - 1)):
+        side = np.array([(mask >> v) & 1 for v in range(n)], np.uint8)
+        vals.append(oracle.cut_weight(n, *c, side))
+    vals = np.sort(np.array(vals))
+    assert vals[0] == 2 * heavy and vals[1] >= 2 * heavy + 2 * light
+
+
+def test_adversarial_families_noi_larger():
+    for n in (202, 403):
+        g = synth.wheel(n, seed=1)
+        assert oracle.noi(n, g.row_ptr, g.col, g.w.astype(np.int64))[0] == 2 * (n - 1)
+    for n in (202, 302):
+        g = synth.dblcyc(n, 1000, 3, seed=2)
+        assert oracle.noi(n, g.row_ptr, g.col, g.w.astype(np.int64))[0] == 2000
+
+
 def test_noi_accepts_noncanonical_input():
     # duplicates, a self-loop and a zero-weight entry
     rp, col, w = G.from_edges(4, [(0, 1), (0, 1), (1, 2), (2, 3), (3, 0), (2, 2), (1, 3)],
