@@ -205,6 +205,70 @@ def measure_batched(mc, n_graphs: int = 4096, alone: int = 256, reps: int = 3):
             "one_at_a_time_sample": alone}
 
 
+def measure_variants(mc, g, val, reps: int = 3):
+    """The paper's variants on the same workload: concurrent CAPFOREST passes
+    with private visit arrays, the shared/private settings alternated over
+    the first rounds, and the coarsening heuristic for the first bound.
+    Host wall time of one solve (median of reps after one warm-up)."""
+    import torch
+    G = mc.mincut_graph_from_csr(g.n, g.row_ptr, g.col, g.w)
+    out = {}
+    for name, kw in [("default", {}), ("private_visit", {"cf_visit": 1}),
+                     ("alternate_visit", {"cf_visit": 2}), ("coarsening_bound", {"init_bound": 1})]:
+        o = mc.default_options(**kw)
+        mc.mincut_solve(G, o, bitmap=False)
+        ts, rounds = [], 0
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            v, _, st = mc.mincut_solve(G, o, bitmap=False)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+            rounds = st["rounds"]
+            assert v == val, (name, v, val)
+        out[name] = {"ms": statistics.median(ts), "rounds": rounds,
+                     "lambda_source": st["lambda_source"]}
+    G.destroy()
+    return out
+
+
+def measure_adversarial(mc, reps: int = 2):
+    """Families that defeat the PR tests: a wheel whose n trivial cuts are all
+    minimum, and two interleaved cycles hiding one minimum cut (Theta(n)
+    rounds).  Solve time and rounds with one sequential pass per round
+    (Algorithm 2 as written) and with several whole passes at once (default);
+    the CPU oracle's sequential NOI on the same graphs for context."""
+    import synth
+    import torch
+    out = {}
+    for name, gg in [("wheel_4097", synth.wheel(4097, seed=1)),
+                     ("dblcyc_1026", synth.dblcyc(1026, 1000, 3, seed=2))]:
+        G = mc.mincut_graph_from_csr(gg.n, gg.row_ptr, gg.col, gg.w)
+        rec = {"n": gg.n, "m": int(gg.row_ptr[-1]) // 2, "lambda": gg.meta["lambda"]}
+        for mode, kw in [("seq_passes_1", {"seq_passes": 1}), ("default", {})]:
+            o = mc.default_options(**kw)
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                v, _, st = mc.mincut_solve(G, o, bitmap=False)
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e3)
+                assert v == gg.meta["lambda"], (name, mode, v)
+            ms = min(ts)
+            rec[mode] = {"ms": ms, "rounds": st["rounds"],
+                         "ms_per_round": ms / max(st["rounds"], 1),
+                         "gpu_launches": st["kernel_launches"]}
+        G.destroy()
+        import oracle
+        t0 = time.perf_counter()
+        v, _, r = oracle.noi(gg.n, gg.row_ptr, gg.col, gg.w.astype(np.int64))
+        rec["cpu_oracle_noi"] = {"ms": (time.perf_counter() - t0) * 1e3, "rounds": r, "cores": 1}
+        assert v == gg.meta["lambda"]
+        out[name] = rec
+    return out
+
+
 def measure_serving(mc, n_req: int = 300, nhi: int = 1 << 14, seed: int = 5):
     """Open-loop Poisson stream of n_req requests (n log-uniform in [100, nhi],
     R-MAT or G(n, 8n) 50/50, weights in [1, 100], largest component) served by
@@ -411,6 +475,9 @@ def run_gpu(args, rank, world):
     if not args.no_extra:
         line["batched"] = measure_batched(mc)
         line["serving"] = measure_serving(mc)
+        line["variants"] = measure_variants(mc, g, val)
+        if not args.no_cpu_baseline:
+            line["adversarial"] = measure_adversarial(mc)
     if not args.no_cpu_baseline:
         cb, lam = cpu_oracle_time(g)
         assert lam == val, (lam, val)

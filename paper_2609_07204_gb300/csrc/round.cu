@@ -1000,9 +1000,16 @@ __global__ void __launch_bounds__(kETThreads)
   }
 }
 
+// Cluster sizes; lanes of a warp with the same label add once (large
+// clusters would otherwise serialise on one counter).
 __global__ void lp_size_kernel(const int* __restrict__ lab, int n, int* __restrict__ size) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    atomicAdd(&size[lab[v]], 1);
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int v = base + threadIdx.x;
+    const int l = v < n ? lab[v] : -1;
+    const unsigned peers = __match_any_sync(FULL, l);
+    if (l >= 0 && lane == __ffs(peers) - 1) atomicAdd(&size[l], __popc(peers));
+  }
 }
 
 __global__ void lp_min_kernel(const long long* __restrict__ cut, const int* __restrict__ size,
