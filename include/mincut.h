@@ -70,9 +70,10 @@ typedef struct mincut_graph mincut_graph; /* opaque, device-resident */
 typedef struct mincut_options {
     int32_t lp_iters;        /* label-propagation sweeps per bound (default 2; 0 = off) */
     int32_t lp_min_n;        /* run LP only on graphs with n >= lp_min_n (default 10000) */
-    int32_t lp_every_round;  /* 1: LP bound in every round (default); 0: first round only */
+    int32_t lp_every_round;  /* 0: LP bound in the first round only (default, the paper's
+                                once-per-solve bound); 1: in every round */
     uint32_t pr_mask;        /* PR1..PR4 as bits 0..3 (default 0xF) */
-    int64_t pr_budget;       /* PR3/PR4 only if min(|N(u)|,|N(v)|) <= budget (default 32; <0 = all) */
+    int64_t pr_budget;       /* PR3/PR4 only if min(|N(u)|,|N(v)|) <= budget (default 16; <0 = all) */
     int32_t passes;          /* concurrent CAPFOREST passes per wave (0 = auto) */
     int32_t pass_table;      /* per-pass table slots, power of two in [256, 2048] (0 = auto) */
     int32_t waves;           /* CAPFOREST waves per round (0 = auto) */
@@ -116,7 +117,8 @@ typedef struct mincut_round_options {
     uint32_t pr_mask;
     int64_t pr_budget;
     int32_t capforest;       /* 0 none; 1 concurrent passes (+ sequential pass if no
-                                marks); 2 one sequential pass from cf_start */
+                                marks); 2 one sequential pass from cf_start; 3 as 1
+                                with visit sets private to each pass */
     int32_t cf_start;
     int32_t passes, pass_table, waves;
     uint64_t seed;

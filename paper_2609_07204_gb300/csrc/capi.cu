@@ -1284,9 +1284,9 @@ void mincut_default_options(mincut_options* o) {
   memset(o, 0, sizeof(*o));
   o->lp_iters = 2;
   o->lp_min_n = 10000;
-  o->lp_every_round = 1;
+  o->lp_every_round = 0;
   o->pr_mask = 0xF;
-  o->pr_budget = 32;
+  o->pr_budget = 16;
   o->seed = 0x5eed;
 }
 
@@ -1297,7 +1297,7 @@ void mincut_default_round_options(mincut_round_options* ro) {
   ro->lp_iters = 2;
   ro->lp_min_n = 10000;
   ro->pr_mask = 0xF;
-  ro->pr_budget = 32;
+  ro->pr_budget = 16;
   ro->capforest = 1;
   ro->seed = 0x5eed;
 }
