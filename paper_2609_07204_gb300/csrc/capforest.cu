@@ -480,22 +480,52 @@ __device__ __forceinline__ void seq_layout(const SeqTree& tl, int smem_from, int
   *r_out = r_in_smem ? reinterpret_cast<WT*>(smem + sbytes) : g_r;
 }
 
+// A small graph's CSR (row offsets, columns, weights, degrees) copied into
+// shared memory at byte offset `at`, so that the pass's row reads stay on
+// chip; the pointers are redirected to the copies.
+template <typename WT>
+__device__ void seq_csr_to_smem(unsigned char* smem, long long at, int n, long long M,
+                                const int64_t*& rp, const int*& col, const WT*& w,
+                                const WT*& deg) {
+  int64_t* srp = reinterpret_cast<int64_t*>(smem + at);
+  WT* sw = reinterpret_cast<WT*>(srp + (n + 1));
+  WT* sdeg = sw + M;
+  int* scol = reinterpret_cast<int*>(sdeg + n);
+  for (long long i = threadIdx.x; i <= n; i += blockDim.x) srp[i] = rp[i];
+  for (long long i = threadIdx.x; i < M; i += blockDim.x) {
+    scol[i] = col[i];
+    sw[i] = w[i];
+  }
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) sdeg[i] = deg[i];
+  __syncthreads();
+  rp = srp;
+  col = scol;
+  w = sw;
+  deg = sdeg;
+}
+
 template <typename WT, typename KT>
 __global__ void __launch_bounds__(512)
     cf_seq_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
                   const WT* __restrict__ w, const WT* __restrict__ deg, int start, int* parent,
                   WT* g_r, KT* g_levels, int* __restrict__ order, int* __restrict__ marks_out,
-                  long long marks_cap, int smem_from, int r_in_smem, DevState* st) {
+                  long long marks_cap, int smem_from, int r_in_smem, long long csr_at,
+                  long long M, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SeqTree tl = seq_tree(n);
   KT* lev[8];
   WT* rr;
   seq_layout<WT, KT>(tl, smem_from, r_in_smem, smem, g_levels, g_r, lev, &rr);
+  const int64_t* rp_ = rp;
+  const int* col_ = col;
+  const WT* w_ = w;
+  const WT* deg_ = deg;
+  if (csr_at >= 0) seq_csr_to_smem<WT>(smem, csr_at, n, M, rp_, col_, w_, deg_);
   long long best_alpha;
   int best_len, ns;
   unsigned long long my_marks;
   bool uf_fail;
-  seq_pass_body<WT, KT>(n, rp, col, 0, w, deg, start, parent, lev, tl, rr, order, marks_out,
+  seq_pass_body<WT, KT>(n, rp_, col_, 0, w_, deg_, start, parent, lev, tl, rr, order, marks_out,
                         marks_cap, (long long)st->lambda, &best_alpha, &best_len, &ns, &my_marks,
                         &uf_fail);
   const int lane = threadIdx.x & 31;
@@ -597,7 +627,8 @@ __global__ void __launch_bounds__(512)
                         unsigned long long seed, int* parent, WT* g_r, KT* g_levels,
                         long long tree_words, int* __restrict__ order,
                         unsigned long long* __restrict__ pass_best, int* __restrict__ pass_len,
-                        int smem_from, int r_in_smem, DevState* st) {
+                        int smem_from, int r_in_smem, long long csr_at, long long M,
+                        DevState* st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = blockIdx.x;
   const SeqTree tl = seq_tree(n);
@@ -605,12 +636,17 @@ __global__ void __launch_bounds__(512)
   WT* rr;
   seq_layout<WT, KT>(tl, smem_from, r_in_smem, smem, g_levels + (long long)k * tree_words,
                      g_r + (long long)k * n, lev, &rr);
+  const int64_t* rp_ = rp;
+  const int* col_ = col;
+  const WT* w_ = w;
+  const WT* deg_ = deg;
+  if (csr_at >= 0) seq_csr_to_smem<WT>(smem, csr_at, n, M, rp_, col_, w_, deg_);
   const int start = k == 0 ? 0 : (int)(mix64(seed ^ mix64((unsigned long long)k)) % (unsigned long long)n);
   long long best_alpha;
   int best_len, ns;
   unsigned long long my_marks;
   bool uf_fail;
-  seq_pass_body<WT, KT>(n, rp, col, 0, w, deg, start, parent, lev, tl, rr,
+  seq_pass_body<WT, KT>(n, rp_, col_, 0, w_, deg_, start, parent, lev, tl, rr,
                         order + (long long)k * n, nullptr, 0,
                         (long long)*(volatile unsigned long long*)&st->lambda, &best_alpha,
                         &best_len, &ns, &my_marks, &uf_fail);
@@ -626,6 +662,12 @@ __global__ void __launch_bounds__(512)
 }
 
 }  // namespace
+
+// Bytes of a CSR copy in shared memory (int64 offsets, weights, degrees,
+// int32 columns, in that order).
+size_t seq_csr_bytes(int n, long long M, size_t wt) {
+  return (size_t)(n + 1) * 8 + (size_t)M * wt + (size_t)n * wt + (size_t)M * 4;
+}
 
 template <typename WT>
 cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT* w,
@@ -670,8 +712,8 @@ long long seq_tree_words(int n) {
 }
 
 template <typename WT>
-cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const WT* w,
-                                 const WT* deg, int start, int* parent, WT* r,
+cudaError_t capforest_sequential(int n, long long M, const int64_t* rp, const int* col,
+                                 const WT* w, const WT* deg, int start, int* parent, WT* r,
                                  uint8_t* visited, unsigned long long* tree, int* order,
                                  int* marks_out, long long marks_cap, DevState* st,
                                  cudaStream_t s, int* launches) {
@@ -695,6 +737,12 @@ cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const
     r_in_smem = 1;
     smem = lev_bytes + (size_t)n * sizeof(WT);
   }
+  long long csr_at = -1;
+  const size_t csr_bytes = seq_csr_bytes(n, M, sizeof(WT));
+  if (r_in_smem && (smem + 15) / 16 * 16 + csr_bytes <= limit) {
+    csr_at = (long long)((smem + 15) / 16 * 16);
+    smem = (size_t)csr_at + csr_bytes;
+  }
   static bool attr[2] = {false, false};
   const int ai = sizeof(WT) == 8 ? 1 : 0;
   if (!attr[ai]) {
@@ -704,14 +752,15 @@ cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const
   }
   cf_seq_kernel<WT, KT><<<1, 512, smem, s>>>(n, rp, col, w, deg, start, parent, r,
                                              reinterpret_cast<KT*>(tree), order, marks_out,
-                                             marks_cap, smem_from, r_in_smem, st);
+                                             marks_cap, smem_from, r_in_smem, csr_at, M, st);
   ++*launches;
   return cudaGetLastError();
 }
 
 template <typename WT>
-cudaError_t capforest_sequential_multi(int n, const int64_t* rp, const int* col, const WT* w,
-                                       const WT* deg, int passes, unsigned long long seed,
+cudaError_t capforest_sequential_multi(int n, long long M, const int64_t* rp, const int* col,
+                                       const WT* w, const WT* deg, int passes,
+                                       unsigned long long seed,
                                        int* parent, WT* r_pool, unsigned long long* tree_pool,
                                        int* order_pool, unsigned long long* pass_best,
                                        int* pass_len, DevState* st, cudaStream_t s,
@@ -734,6 +783,12 @@ cudaError_t capforest_sequential_multi(int n, const int64_t* rp, const int* col,
     r_in_smem = 1;
     smem = lev_bytes + (size_t)n * sizeof(WT);
   }
+  long long csr_at = -1;
+  const size_t csr_bytes = seq_csr_bytes(n, M, sizeof(WT));
+  if (r_in_smem && (smem + 15) / 16 * 16 + csr_bytes <= limit) {
+    csr_at = (long long)((smem + 15) / 16 * 16);
+    smem = (size_t)csr_at + csr_bytes;
+  }
   static bool attr[2] = {false, false};
   const int ai = sizeof(WT) == 8 ? 1 : 0;
   if (!attr[ai]) {
@@ -744,7 +799,7 @@ cudaError_t capforest_sequential_multi(int n, const int64_t* rp, const int* col,
   cf_seq_multi_kernel<WT, KT><<<passes, 512, smem, s>>>(
       n, rp, col, w, deg, seed, parent, r_pool, reinterpret_cast<KT*>(tree_pool),
       seq_tree_words(n) * (long long)(sizeof(unsigned long long) / sizeof(KT)), order_pool,
-      pass_best, pass_len, smem_from, r_in_smem, st);
+      pass_best, pass_len, smem_from, r_in_smem, csr_at, M, st);
   cf_multi_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, passes, st);
   *launches += 2;
   return cudaGetLastError();
@@ -784,12 +839,14 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
                                             const WT*, int*, int*, int*, unsigned long long*, \
                                             int*, int*, PassConfig, DevState*, cudaStream_t,  \
                                             int*, const BatchView*);                          \
-  template cudaError_t capforest_sequential<WT>(int, const int64_t*, const int*, const WT*,   \
+  template cudaError_t capforest_sequential<WT>(int, long long, const int64_t*, const int*,     \
+                                                const WT*,                                     \
                                                 const WT*, int, int*, WT*, uint8_t*,          \
                                                 unsigned long long*, int*, int*, long long,   \
                                                 DevState*, cudaStream_t, int*);               \
   template cudaError_t capforest_sequential_multi<WT>(                                        \
-      int, const int64_t*, const int*, const WT*, const WT*, int, unsigned long long, int*,    \
+      int, long long, const int64_t*, const int*, const WT*, const WT*, int,                   \
+      unsigned long long, int*,                                                               \
       WT*, unsigned long long*, int*, unsigned long long*, int*, DevState*, cudaStream_t, int*); \
   template cudaError_t capforest_sequential_batch<WT>(                                        \
       int, const int64_t*, const int*, const WT*, const WT*, int*, WT*, unsigned long long*,   \

@@ -639,7 +639,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     if (k > 1) {
       {
         ProfScope ps(P_CF_SEQ, M, s);
-        CK(capforest_sequential_multi<WT>(n, rp, col, w, deg, k, c.seed, g->parent,
+        CK(capforest_sequential_multi<WT>(n, M, rp, col, w, deg, k, c.seed, g->parent,
                                           (WT*)g->seq_multi_r, g->seq_multi_tree,
                                           g->seq_multi_order, g->pass_best, g->pass_len, g->st, s,
                                           &g->launches));
@@ -657,7 +657,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     const int start = (c.capforest == 2) ? c.cf_start : 0;
     {
       ProfScope ps(P_CF_SEQ, M, s);
-      CK(capforest_sequential<WT>(n, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_vis,
+      CK(capforest_sequential<WT>(n, M, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_vis,
                                   g->seq_tree, g->seq_order, marks_dev, cap, g->st, s,
                                   &g->launches));
     }

@@ -75,6 +75,17 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
+// 32-bit unsigned maximum in one warp reduction instruction.
+template <>
+__device__ __forceinline__ unsigned warp_max<unsigned>(unsigned v) {
+  return __reduce_max_sync(FULL, v);
+}
+
+template <>
+__device__ __forceinline__ int warp_max<int>(int v) {
+  return __reduce_max_sync(FULL, v);
+}
+
 __device__ __forceinline__ void set_error(DevState* st, unsigned bits) {
   atomicOr(&st->error, bits);
 }

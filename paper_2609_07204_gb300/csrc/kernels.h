@@ -239,8 +239,8 @@ size_t capforest_pass_smem(int table, int warps_per_block, size_t wt_size);
 // (nullable) up to marks_cap pairs.  The best alpha goes to st->cf_val/cf_len
 // with st->cf_pass = -1; st->cf_nscanned counts the visited vertices.
 template <typename WT>
-cudaError_t capforest_sequential(int n, const int64_t* rp, const int* col, const WT* w,
-                                 const WT* deg, int start, int* parent, WT* r,
+cudaError_t capforest_sequential(int n, long long M, const int64_t* rp, const int* col,
+                                 const WT* w, const WT* deg, int start, int* parent, WT* r,
                                  uint8_t* visited, unsigned long long* tree, int* order,
                                  int* marks_out, long long marks_cap, DevState* st,
                                  cudaStream_t s, int* launches);
@@ -258,8 +258,9 @@ long long seq_tree_words(int n);
 // bound lowers st->lambda; the best such pass k sets st->cf_val, cf_len and
 // cf_pass = -2 - k (its visit order is order_pool + k*n).
 template <typename WT>
-cudaError_t capforest_sequential_multi(int n, const int64_t* rp, const int* col, const WT* w,
-                                       const WT* deg, int passes, unsigned long long seed,
+cudaError_t capforest_sequential_multi(int n, long long M, const int64_t* rp, const int* col,
+                                       const WT* w, const WT* deg, int passes,
+                                       unsigned long long seed,
                                        int* parent, WT* r_pool, unsigned long long* tree_pool,
                                        int* order_pool, unsigned long long* pass_best,
                                        int* pass_len, DevState* st, cudaStream_t s,
