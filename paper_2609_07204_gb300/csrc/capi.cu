@@ -353,12 +353,19 @@ int ensure_rows(mincut_graph* g) {
       !galloc(g, &r.kcnt, n + 1) || !galloc(g, &r.off, n + 1) ||
       !galloc(g, &r.part, (n + 1) / 4096 + 3) || !galloc(g, &r.total, 1) ||
       !galloc(g, &r.side_v, M) || !galloc(g, &r.vinfo, n + 1) || !galloc(g, &g->rpG, n + 1) ||
+      !galloc(g, &r.dsum, n + 1) || !galloc(g, &r.did, n + 1) || !galloc(g, &r.ndense, 1) ||
+      !galloc(g, &r.chunk, 4 * M / kDenseChunk + n + 64) ||
+      !galloc(g, &r.dense_group, n + 1) ||
+      !(r.acc = dev_alloc(g, (size_t)4 * M * wsz)) ||
       !galloc(g, &g->colG, M) ||
       !(g->wG = dev_alloc(g, (size_t)M * wsz)) || !(g->side_w = dev_alloc(g, (size_t)M * wsz))) {
     r.cnt = nullptr;
     return fail(MINCUT_ERR_OOM, "row-wise contraction buffers");
   }
   r.single_entries = &g->st->single_entries;
+  r.dense_entries = &g->st->dense_entries;
+  r.dense_slots = 4 * M;
+  CK(cudaMemsetAsync(r.acc, 0, (size_t)r.dense_slots * wsz, g->stream));
   return MINCUT_OK;
 }
 
@@ -411,7 +418,9 @@ int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out) {
   RowScratch& rs = g->rows;
   { ProfScope ps(P_ROWS, M, s);
     CK(rows_count<WT>(n, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, rs, (WT*)g->side_w, s,
-                      &g->launches)); }
+                      &g->launches));
+    CK(rows_dense_accumulate<WT>(n, M, n2, g->crp(), g->ccol(), (const WT*)g->cw(), g->L,
+                                 g->tile_row, rs, s, &g->launches)); }
   CK(cudaMemsetAsync(&g->st->emit_count, 0, sizeof(long long), s));
   { ProfScope ps(P_EMIT, M, s);
     CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
@@ -444,8 +453,8 @@ int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out) {
 
 // Contraction of the current graph by the union-find state in g->parent:
 // relabel, then either the row-wise path (when at least a quarter of the
-// entries lie in rows of single-vertex groups) or emit / sort / build of all
-// entries; the result becomes the current graph.
+// entries lie in rows of single-vertex groups or of dense groups) or emit /
+// sort / build of all entries; the result becomes the current graph.
 template <typename WT>
 int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compose) {
   cudaStream_t s = g->stream;
@@ -462,10 +471,11 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
     rc = ensure_rows(g);
     if (rc) return rc;
     { ProfScope ps(P_UF, n, s);
-      CK(rows_classify(n, n2, g->crp(), g->L, g->rows, s, &g->launches)); }
+      CK(rows_classify(n, n2, g->crp(), g->L, g->rows, s, &g->launches));
+      CK(rows_dense_mark(n2, g->rows, s, &g->launches)); }
     rc = sync_state(g);
     if (rc) return rc;
-    rowwise = 4 * (long long)g->hst->single_entries >= M;
+    rowwise = 4 * (long long)(g->hst->single_entries + g->hst->dense_entries) >= M;
   }
   long long m2 = 0;
   if (rowwise) {
@@ -1421,7 +1431,7 @@ int64_t mincut_graph_footprint(int64_t n, int64_t m_directed) {
   // 8-byte weights and sums double the weight terms; this bound assumes
   // 4-byte ones (total weight < 2^31) plus the label-propagation and the
   // row-wise contraction buffers
-  return (int64_t)(164 * n + 106 * m_directed + 4096 * P + (1 << 20));
+  return (int64_t)(172 * n + 122 * m_directed + 4096 * P + (1 << 20));
 }
 
 int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,

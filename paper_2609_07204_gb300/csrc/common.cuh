@@ -50,6 +50,7 @@ struct DevState {
   int batch_done;              // graphs of a batch that finished
   long long sym_balance;       // symmetry check: entries u < v minus entries u > v
   unsigned long long single_entries;  // contraction: entries of single-vertex groups' rows
+  unsigned long long dense_entries;   // contraction: entries of dense groups' rows
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

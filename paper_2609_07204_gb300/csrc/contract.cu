@@ -51,21 +51,177 @@ __global__ void group_count_kernel(const int* __restrict__ L, int n, int* __rest
 // entries of rows whose group is a single vertex.
 __global__ void single_entries_kernel(const int64_t* __restrict__ rp, const int* __restrict__ L,
                                       int n, const int* __restrict__ cnt, int* __restrict__ gen,
-                                      int* __restrict__ vinfo,
+                                      int* __restrict__ vinfo, int* __restrict__ dsum,
                                       unsigned long long* single_entries) {
   unsigned long long s = 0;
-  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-    const int g = L[x];
-    if (cnt[g] == 1) {
-      s += (unsigned long long)(rp[x + 1] - rp[x]);
-      vinfo[x] = g;
-    } else {
-      gen[g] = 1;
-      vinfo[x] = g | kMovedBit;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int x = base + threadIdx.x;
+    int g = -1, len = 0;
+    if (x < n) {
+      g = L[x];
+      len = (int)(rp[x + 1] - rp[x]);
+      if (cnt[g] == 1) {
+        s += (unsigned long long)len;
+        vinfo[x] = g;
+      } else {
+        gen[g] = 1;
+        vinfo[x] = g | kMovedBit;
+      }
     }
+    // entries per group (one atomic per distinct group of the warp)
+    const unsigned peers = __match_any_sync(FULL, g);
+    const int tot = (int)__reduce_add_sync(peers, (unsigned)len);
+    if (g >= 0 && lane == __ffs(peers) - 1 && tot) atomicAdd(&dsum[g], tot);
   }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(single_entries, s);
+}
+
+// Dense groups: big enough that an n2-slot accumulator (n2 slots read to
+// count and to write, ~8 B each) costs less than sorting their entries
+// (~120 B each through emit, radix passes and segmented sum).
+__global__ void dense_mark_kernel(int n2, const int* __restrict__ dsum, int* __restrict__ gen,
+                                  int* __restrict__ did, int* ndense, int max_dense,
+                                  unsigned long long* dense_entries) {
+  const int thr = max(n2 / 16, 256);
+  unsigned long long tot = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n2; g += gridDim.x * blockDim.x) {
+    if (dsum[g] < thr) continue;
+    const int d = atomicAdd(ndense, 1);
+    if (d < max_dense) {
+      gen[g] = 2;
+      did[g] = d;
+      tot += (unsigned long long)dsum[g];
+    }
+  }
+  tot = warp_sum(tot);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(dense_entries, tot);
+}
+
+// Entry tiles: every entry of a dense group's member rows adds its weight to
+// the group's accumulator slot of the far end's label (self-loops dropped).
+template <typename WT>
+__global__ void __launch_bounds__(kETThreads)
+    dense_acc_kernel(int n, long long M, int n2, const int64_t* __restrict__ rp,
+                     const int* __restrict__ col, const WT* __restrict__ w,
+                     const int* __restrict__ L, const int* __restrict__ gen,
+                     const int* __restrict__ did, const int* __restrict__ tile_row, int ntiles,
+                     WT* __restrict__ acc) {
+  __shared__ TileRowsSmem tr;
+  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
+  bool any = false;
+  for (int r = tr.r0 + threadIdx.x; r <= tr.r1 && !any; r += blockDim.x) any = gen[L[r]] == 2;
+  if (!__syncthreads_or(any)) return;
+  const long long e0 = (long long)blockIdx.x * kET;
+  for (int i = 0; i < kETItems; ++i) {
+    const long long e = e0 + i * kETThreads + threadIdx.x;
+    if (e >= M) break;
+    const int u = tile_row_of(tr, rp, e);
+    const int g = L[u];
+    if (gen[g] != 2) continue;
+    const int vp = L[col[e]];
+    if (vp == g) continue;
+    atomic_add_w(&acc[(long long)did[g] * n2 + vp], w[e]);
+  }
+}
+
+// Per chunk of kDenseChunk accumulator slots: the nonzero slots (blockIdx.y =
+// dense slot).  chunk[d * nchunks + c]; len[g] gets the total.
+template <typename WT>
+__global__ void __launch_bounds__(256)
+    dense_count_kernel(int n2, const WT* __restrict__ acc, const int* ndense, int max_dense,
+                       int* __restrict__ chunk, int nchunks) {
+  const int d = blockIdx.y;
+  if (d >= min(*ndense, max_dense)) return;
+  const int c = blockIdx.x;
+  const long long base = (long long)d * n2;
+  int cntv = 0;
+  for (int i = c * kDenseChunk + threadIdx.x; i < min(n2, (c + 1) * kDenseChunk); i += blockDim.x)
+    cntv += acc[base + i] != 0;
+  cntv = (int)__reduce_add_sync(FULL, (unsigned)cntv);
+  __shared__ int s_w[8];
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = cntv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_w[k];
+    chunk[(long long)d * nchunks + c] = t;
+  }
+}
+
+// One block per dense group: chunk counts -> exclusive offsets, len[g].
+__global__ void dense_scan_kernel(int n2, const int* __restrict__ gen, const int* __restrict__ did,
+                                  const int* ndense, int max_dense, int* __restrict__ chunk,
+                                  int nchunks, int* __restrict__ len) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n2; g += gridDim.x * blockDim.x) {
+    if (gen[g] != 2) continue;
+    int* ch = chunk + (long long)did[g] * nchunks;
+    int run = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      const int v = ch[c];
+      ch[c] = run;
+      run += v;
+    }
+    len[g] = run;
+  }
+}
+
+// Writes each dense group's nonzero slots in slot order (its canonical row)
+// at rp2[g] + chunk offset + rank in the chunk, adds the row weight to
+// deg2[g] and clears the slots for the next round.
+template <typename WT>
+__global__ void __launch_bounds__(256)
+    dense_write_kernel(int n2, const int* __restrict__ gen, const int* __restrict__ did,
+                       const int* ndense, int max_dense, const int* __restrict__ chunk,
+                       int nchunks, WT* __restrict__ acc, const int* __restrict__ dense_group,
+                       const int64_t* __restrict__ rp2, int* __restrict__ col2,
+                       WT* __restrict__ w2, WT* __restrict__ deg2) {
+  const int d = blockIdx.y;
+  if (d >= min(*ndense, max_dense)) return;
+  const int g = dense_group[d];
+  const int c = blockIdx.x;
+  const long long base = (long long)d * n2;
+  __shared__ int s_w[8];
+  __shared__ int s_run;
+  if (threadIdx.x == 0) s_run = 0;
+  __syncthreads();
+  const long long out0 = rp2[g] + chunk[(long long)d * nchunks + c];
+  long long dsumv = 0;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int i0 = c * kDenseChunk; i0 < min(n2, (c + 1) * kDenseChunk); i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    WT v = 0;
+    if (i < n2 && i < (c + 1) * kDenseChunk) v = acc[base + i];
+    const bool nz = v != 0;
+    const unsigned b = __ballot_sync(FULL, nz);
+    if (lane == 0) s_w[wp] = __popc(b);
+    __syncthreads();
+    int before = s_run;
+    for (int k = 0; k < wp; ++k) before += s_w[k];
+    if (nz) {
+      const long long pos = out0 + before + __popc(b & lanemask_lt());
+      col2[pos] = i;
+      w2[pos] = v;
+      acc[base + i] = 0;
+      dsumv += (long long)v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_w[k];
+      s_run += t;
+    }
+    __syncthreads();
+  }
+  dsumv = warp_sum(dsumv);
+  if (lane == 0 && dsumv) atomic_add_w(&deg2[g], (WT)dsumv);
+}
+
+__global__ void dense_group_list_kernel(int n2, const int* __restrict__ gen,
+                                        const int* __restrict__ did, int* __restrict__ dense_group) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n2; g += gridDim.x * blockDim.x)
+    if (gen[g] == 2) dense_group[did[g]] = g;
 }
 
 // Pass A: one warp per singleton row u (g = L[u]).  Counts the clean entries,
@@ -88,6 +244,7 @@ __global__ void __launch_bounds__(kSrWarps * 32)
   const int b = (int)rp[u], e = (int)rp[u + 1];
   if (vu & kMovedBit) return;
   const int g = vu;
+  if (gen[g]) return;  // dense
   if (e - b > kSrMaxRow) {
     if (lane == 0) gen[g] = 1;
     return;
@@ -191,7 +348,7 @@ __global__ void __launch_bounds__(kSrWarps * 32)
 __global__ void gen_len_kernel(const int64_t* __restrict__ rpG, const int* __restrict__ gen, int n2,
                                int* __restrict__ len) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n2; g += gridDim.x * blockDim.x)
-    if (gen[g]) len[g] = (int)(rpG[g + 1] - rpG[g]);
+    if (gen[g] == 1) len[g] = (int)(rpG[g + 1] - rpG[g]);
 }
 
 __global__ void rp_from_offsets_kernel(const int* __restrict__ off, const int* __restrict__ total,
@@ -313,10 +470,44 @@ cudaError_t rows_classify(int n, int n2, const int64_t* rp, const int* L, const 
   cudaMemsetAsync(rs.cnt, 0, (size_t)n2 * sizeof(int), s);
   cudaMemsetAsync(rs.gen, 0, (size_t)n2 * sizeof(int), s);
   cudaMemsetAsync(rs.single_entries, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(rs.dsum, 0, (size_t)n2 * sizeof(int), s);
   group_count_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(L, n, rs.cnt);
   single_entries_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(rp, L, n, rs.cnt, rs.gen, rs.vinfo,
-                                                            rs.single_entries);
+                                                            rs.dsum, rs.single_entries);
   *launches += 2;
+  return cudaGetLastError();
+}
+
+int dense_capacity(int n2, const RowScratch& rs) {
+  return (int)std::min<long long>(n2, rs.dense_slots / std::max(n2, 1));
+}
+
+cudaError_t rows_dense_mark(int n2, const RowScratch& rs, cudaStream_t s, int* launches) {
+  cudaMemsetAsync(rs.ndense, 0, sizeof(int), s);
+  cudaMemsetAsync(rs.dense_entries, 0, sizeof(unsigned long long), s);
+  const int max_dense = dense_capacity(n2, rs);
+  if (max_dense <= 0) return cudaGetLastError();
+  dense_mark_kernel<<<grid_blocks(n2, 256), 256, 0, s>>>(n2, rs.dsum, rs.gen, rs.did, rs.ndense,
+                                                         max_dense, rs.dense_entries);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t rows_dense_accumulate(int n, long long M, int n2, const int64_t* rp, const int* col,
+                                  const WT* w, const int* L, const int* tile_row,
+                                  const RowScratch& rs, cudaStream_t s, int* launches) {
+  const int max_dense = dense_capacity(n2, rs);
+  if (max_dense <= 0 || M <= 0) return cudaGetLastError();
+  const int ntiles = (int)((M + kET - 1) / kET);
+  dense_acc_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, n2, rp, col, w, L, rs.gen, rs.did,
+                                                     tile_row, ntiles, (WT*)rs.acc);
+  const int nchunks = (n2 + kDenseChunk - 1) / kDenseChunk;
+  dense_count_kernel<WT><<<dim3(nchunks, max_dense), 256, 0, s>>>(
+      n2, (const WT*)rs.acc, rs.ndense, max_dense, rs.chunk, nchunks);
+  dense_scan_kernel<<<grid_blocks(n2, 256), 256, 0, s>>>(n2, rs.gen, rs.did, rs.ndense, max_dense,
+                                                         rs.chunk, nchunks, rs.len);
+  *launches += 3;
   return cudaGetLastError();
 }
 
@@ -346,6 +537,16 @@ cudaError_t rows_finish(int n, int n2, const int64_t* rp, const int* col, const 
   sr_write_kernel<WT><<<blocks, kSrWarps * 32, 0, s>>>(n, rp, col, w, rs.vinfo, rs.gen, rs.kcnt,
                                                        rs.side_v, side_w, rp2, col2, w2, deg2);
   *launches += 2;
+  const int max_dense = dense_capacity(n2, rs);
+  if (max_dense > 0) {
+    const int nchunks = (n2 + kDenseChunk - 1) / kDenseChunk;
+    dense_group_list_kernel<<<grid_blocks(n2, 256), 256, 0, s>>>(n2, rs.gen, rs.did,
+                                                                 rs.dense_group);
+    dense_write_kernel<WT><<<dim3(nchunks, max_dense), 256, 0, s>>>(
+        n2, rs.gen, rs.did, rs.ndense, max_dense, rs.chunk, nchunks, (WT*)rs.acc,
+        rs.dense_group, rp2, col2, w2, deg2);
+    *launches += 2;
+  }
   if (NG > 0) {
     err = tile_rows(rpG, n2, NG, tile_row, s, launches);
     if (err != cudaSuccess) return err;
@@ -358,6 +559,9 @@ cudaError_t rows_finish(int n, int n2, const int64_t* rp, const int* col, const 
 }
 
 #define MC_ROWS_INST(WT)                                                                         \
+  template cudaError_t rows_dense_accumulate<WT>(int, long long, int, const int64_t*, const int*, \
+                                                 const WT*, const int*, const int*,              \
+                                                 const RowScratch&, cudaStream_t, int*);         \
   template cudaError_t rows_count<WT>(int, const int64_t*, const int*, const WT*, const int*,     \
                                       const RowScratch&, WT*, cudaStream_t, int*);               \
   template cudaError_t rows_finish<WT>(int, int, const int64_t*, const int*, const WT*,           \

@@ -129,7 +129,7 @@ cudaError_t degrees_min(const WT* deg, int n, unsigned long long* blk, DevState*
 
 // Relabelled entries (L[u] << vbits | L[v], w) appended to keys/vals
 // (st->emit_count counts them); self-loops and zero weights dropped; with
-// keep_row, only entries whose new row r = L[u] has keep_row[r] != 0.
+// keep_row, only entries whose new row r = L[u] has keep_row[r] == 1.
 template <typename WT>
 cudaError_t emit_pairs(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                        const int* L, int vbits, const int* tile_row, u64* keys, WT* vals,
@@ -289,11 +289,33 @@ struct RowScratch {
   int* side_v;  // M: a singleton row's moved labels at the row's own offset
   int* vinfo;   // n: L[x], with the top bit set when x's group has several members
   unsigned long long* single_entries;  // entries of singleton groups' rows
+  int* dsum;    // n: entries of each group's member rows
+  int* did;     // n: dense accumulator slot of a dense group
+  int* ndense;  // 1: dense groups this round
+  int* chunk;   // dense_slots / kDenseChunk + n + 64: per-chunk counts, then offsets
+  void* acc;    // dense_slots weights: dense accumulators, n2 per dense group (zero between
+                // rounds: the writing kernel clears what it read)
+  long long dense_slots;
+  int* dense_group;  // n: group of each dense slot
+  unsigned long long* dense_entries;  // entries of the dense groups' rows
 };
+constexpr int kDenseChunk = 2048;  // accumulator slots per block of the dense kernels
 
 // cnt, gen (multi-member groups) and *single_entries.
 cudaError_t rows_classify(int n, int n2, const int64_t* rp, const int* L, const RowScratch& rs,
                           cudaStream_t s, int* launches);
+
+// Groups whose member rows hold at least max(n2 / 16, 256) entries take a
+// dense accumulator of n2 slots (gen = 2) while accumulators are left
+// (min(n2, dense_slots / n2) of them); their entries go to *dense_entries.
+cudaError_t rows_dense_mark(int n2, const RowScratch& rs, cudaStream_t s, int* launches);
+
+// Dense groups: accumulate their entries (acc must be zero), count the
+// distinct labels into len.
+template <typename WT>
+cudaError_t rows_dense_accumulate(int n, long long M, int n2, const int64_t* rp, const int* col,
+                                  const WT* w, const int* L, const int* tile_row,
+                                  const RowScratch& rs, cudaStream_t s, int* launches);
 
 // Singleton rows: len, kcnt and the moved labels with their summed weights
 // (side_v / side_w); rows that do not fit are added to gen.

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kETThreads)
     // a tile whose rows are all filtered out reads none of its entries
     bool any = false;
     for (int r = tr.r0 + threadIdx.x; r <= tr.r1 && !any; r += blockDim.x)
-      any = keep_row[L ? L[r] : r] != 0;
+      any = keep_row[L ? L[r] : r] == 1;
     if (!__syncthreads_or(any)) return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kETThreads)
     if (e < M) {
       const int u = tile_row_of(tr, rp, e);
       const int lu = L ? L[u] : u;
-      if (keep_row && !keep_row[lu]) {
+      if (keep_row && keep_row[lu] != 1) {
         // row not emitted: its entries are not read
       } else {
         const int v = col[e];

@@ -256,8 +256,13 @@ def test_contract_rowwise_bit_exact(weights):
             mem = rng.choice(n, size=int(rng.integers(2, 7)), replace=False)
             pu += [int(mem[0])] * (len(mem) - 1)
             pv += [int(x) for x in mem[1:]]
-        # a row of 64..4096 entries whose neighbours fall into 40 groups
+        # one group of the highest-degree vertices: its rows hold more than a
+        # quarter of n entries (the dense-accumulator path)
         d = np.diff(rp)
+        top = np.argsort(-d, kind="stable")[:5]
+        pu += [int(top[0])] * 4
+        pv += [int(x) for x in top[1:]]
+        # a row of 64..4096 entries whose neighbours fall into 40 groups
         cand = np.flatnonzero((d >= 64) & (d <= 4096))
         h = int(cand[rng.integers(0, len(cand))])
         nb = col[rp[h]:rp[h + 1]][:40]
@@ -268,6 +273,8 @@ def test_contract_rowwise_bit_exact(weights):
         pv = np.asarray(pv, np.int32)
         n2, L = oracle.labels_from_pairs(n, pu, pv)
         assert _singleton_entry_share(n, rp, np.asarray(L)) >= 0.25
+        La = np.asarray(L)
+        assert np.bincount(La, weights=d, minlength=n2).max() >= max(n2 / 4, 1024)
         ro = mc.default_round_options()
         ro.npairs = len(pu)
         ro.pair_u = pu.ctypes.data
