@@ -68,6 +68,28 @@ TRAFFIC_PER_UNIT = {
 }
 
 
+CONTRACTION = ("contract_rows", "emit", "sort_hist", "sort_pass", "build_csr")
+
+
+def contraction_gbs(prof, peak, peak_kind):
+    """The metric's contraction HBM GB/s: algorithmic bytes of the contraction
+    kernels (ALG_BYTES per unit) over their CUDA-event time in the timed
+    steps, per category and together, with the fraction of the HBM peak."""
+    out, tot_b, tot_ms = {}, 0.0, 0.0
+    for k in CONTRACTION:
+        d = prof.get(k)
+        if not d or d["ms"] <= 0:
+            continue
+        b = d["units"] * ALG_BYTES[k]
+        out[k] = {"gbs": b / (d["ms"] / 1e3) / 1e9, "ms": d["ms"], "alg_bytes": b}
+        tot_b += b
+        tot_ms += d["ms"]
+    if tot_ms > 0:
+        gbs = tot_b / (tot_ms / 1e3) / 1e9
+        out["total"] = {"gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": peak_kind}
+    return out
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -470,6 +492,7 @@ def run_gpu(args, rank, world):
         "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                         "share": v["ms"] / total_prof_ms if total_prof_ms else None}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "contraction": contraction_gbs(prof, peak, peak_kind),
         "clocks": clk,
     }
     if not args.no_extra:
