@@ -54,9 +54,9 @@ ALG_BYTES = {
     "sort_pass": 24,        # read key + value (12), write key + value (12)
     "sort_hist": 8,         # read key
     "build_csr": 20,        # read key + value (12), write col + w (8)
-    "contract_rows": 10,    # row-wise contraction, two scopes per round over the
-                            # round's entries: count (read col, 4) and write
-                            # (read col + w, write col + w, 16)
+    "contract_rows": 8,     # row-wise contraction, two scopes per round over the
+                            # round's entries: together read col + w once (8)
+                            # and write col + w of the contracted graph (<= 8)
 }
 
 # DRAM bytes per unit measured by ncu (dram__bytes_read.sum +
