@@ -155,7 +155,12 @@ void mincut_default_round_options(mincut_round_options* ro);
  * summed, self-loops and zero weights dropped.  n >= 2 (a cut needs two
  * non-empty sides, Sec. 2) else MINCUT_ERR_INVALID.  cuda_stream is a
  * cudaStream_t (NULL: the legacy default stream).  On success *out owns the
- * graph. */
+ * graph.  Host col / w arrays in pinned (page-locked, mapped) memory are read
+ * in place by the device; pageable ones are copied first.  The caller's
+ * arrays are not referenced after the call returns.  Symmetry of an input
+ * already in canonical form is checked by a 128-bit fingerprint of its edge
+ * triples (an asymmetric input passes only on a collision); other inputs are
+ * checked exactly after canonicalisation. */
 int mincut_graph_from_csr(int64_t n, const int64_t* row_ptr, const int32_t* col,
                           const int32_t* w, uint32_t flags, void* cuda_stream,
                           const mincut_allocator* alloc, mincut_graph** out);

@@ -57,6 +57,29 @@ __global__ void widen32_kernel(const int32_t* __restrict__ in, int64_t* __restri
        i += (long long)gridDim.x * blockDim.x)
     out[i] = (int64_t)in[i];
 }
+// Device address of the host range [p, p + bytes) when the device can read
+// it in place (pinned or registered host memory mapped into the device's
+// address space, both ends in such memory at the same offset), else NULL.
+const void* mapped_host_range(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  const char* last = static_cast<const char*>(p) + bytes - 1;
+  if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (b.type != cudaMemoryTypeHost || !b.devicePointer) return nullptr;
+  if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) !=
+      (ptrdiff_t)(bytes - 1))
+    return nullptr;
+  return a.devicePointer;
+}
+
 // Sum and minimum of the raw input weights; row_ptr monotonicity.
 __global__ void input_stats_kernel(const int64_t* __restrict__ rp, int n, const int32_t* __restrict__ w,
                                    long long M, unsigned long long* out /* [sum, neg, badrp] */) {
@@ -971,13 +994,12 @@ int contract_round_impl(mincut_graph* g, const mincut_round_options* ro,
 // Degrees of the canonical input rp0/col0/w0 (M0 entries) and, with
 // `validate`, the symmetry check.
 template <typename WT>
-int finish_input(mincut_graph* g, int n, bool validate) {
+int finish_input(mincut_graph* g, int n, bool validate, bool sym_checked) {
   cudaStream_t s = g->stream;
   const long long m = g->M0;
-  if (m > 0) CK(tile_rows(g->rp0, n, m, g->tile_row, s, &g->launches));
   CK(row_degrees<WT>(n, m, g->rp0, (const WT*)g->w0, g->tile_row, (WT*)g->deg0, s,
                      &g->launches));
-  if (validate && m > 0) {
+  if (validate && !sym_checked && m > 0) {
     CK(check_symmetric<WT>(n, m, g->rp0, g->col0, (const WT*)g->w0, g->tile_row, g->st, s,
                            &g->launches));
     int rc = sync_state(g);
@@ -1019,7 +1041,7 @@ int canonicalize_input(mincut_graph* g, int n, long long Mraw, bool validate) {
     CK(cudaMemcpyAsync(g->col0, g->col[0], (size_t)m2 * sizeof(int), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(g->w0, g->w[0], (size_t)m2 * sizeof(WT), cudaMemcpyDeviceToDevice, s));
   }
-  return finish_input<WT>(g, n, validate);
+  return finish_input<WT>(g, n, validate, false);
 }
 
 int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const int32_t* w,
@@ -1063,45 +1085,58 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   if (!galloc(g, &g->st, 1) || !galloc(g, &g->m2_dev, 1)) return bail(fail(MINCUT_ERR_OOM, "state"));
   if (cudaMemsetAsync(g->st, 0, sizeof(DevState), s) != cudaSuccess)
     return bail(fail(MINCUT_ERR_CUDA, "memset state"));
-  // raw copy of row_ptr and the weight statistics decide the weight type
+  // row_ptr first (checked before any entry is read through it), then one
+  // ingestion pass over the entries: copy, weight statistics, canonical
+  // test and symmetry fingerprint together
   int64_t* rp_raw = nullptr;
   int32_t* w_raw = nullptr;
   int* col_raw = nullptr;
   if (!galloc(g, &rp_raw, n + 1) || !galloc(g, &w_raw, Mraw) || !galloc(g, &col_raw, Mraw))
     return bail(fail(MINCUT_ERR_OOM, "raw input"));
   const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if (cudaMemcpyAsync(rp_raw, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind, s) != cudaSuccess ||
-      (Mraw > 0 && cudaMemcpyAsync(w_raw, w, (size_t)Mraw * sizeof(int32_t), kind, s) != cudaSuccess) ||
-      (Mraw > 0 && cudaMemcpyAsync(col_raw, col, (size_t)Mraw * sizeof(int32_t), kind, s) != cudaSuccess))
-    return bail(fail(MINCUT_ERR_CUDA, "copy input: %s", cudaGetErrorString(cudaGetLastError())));
+  if (cudaMemcpyAsync(rp_raw, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind, s) != cudaSuccess)
+    return bail(fail(MINCUT_ERR_CUDA, "copy row_ptr: %s", cudaGetErrorString(cudaGetLastError())));
   unsigned long long* wst = nullptr;
-  if (!galloc(g, &wst, 4)) return bail(fail(MINCUT_ERR_OOM, "stats"));
-  cudaMemsetAsync(wst, 0, 4 * sizeof(unsigned long long), s);
-  input_stats_kernel<<<std::max(1, std::min(g->sms * 8, (int)((std::max<long long>(Mraw, n) + 255) / 256))), 256, 0, s>>>(
-      rp_raw, n, w_raw, Mraw, wst);
-  unsigned long long hws[4] = {0, 0, 0, 0};
-  cudaMemcpyAsync(hws, wst, sizeof(hws), cudaMemcpyDeviceToHost, s);
+  if (!galloc(g, &wst, 10)) return bail(fail(MINCUT_ERR_OOM, "stats"));
+  cudaMemsetAsync(wst, 0, 10 * sizeof(unsigned long long), s);
+  input_stats_kernel<<<std::max(1, std::min(g->sms * 8, (n + 255) / 256)), 256, 0, s>>>(
+      rp_raw, n, w_raw, 0, wst);
+  unsigned long long hws[6] = {0, 0, 0, 0, 0, 0};
+  cudaMemcpyAsync(hws, wst, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess)
-    return bail(fail(MINCUT_ERR_CUDA, "input statistics: %s", cudaGetErrorString(cudaGetLastError())));
+    return bail(fail(MINCUT_ERR_CUDA, "row_ptr check: %s", cudaGetErrorString(cudaGetLastError())));
   if (hws[2]) return bail(fail(MINCUT_ERR_INVALID, "row_ptr is not non-decreasing"));
+  const long long ntiles = (std::max<long long>(Mraw, 1) + kEntryTile - 1) / kEntryTile + 2;
+  if (!galloc(g, &g->tile_row, ntiles)) return bail(fail(MINCUT_ERR_OOM, "tile rows"));
+  unsigned long long* ist = wst + 4;
+  if (Mraw > 0) {
+    // entries the device can address are read in place (device input, or
+    // pinned host memory mapped into the device's address space); others
+    // are copied first
+    const int* col_src = dev_in ? col : (const int*)mapped_host_range(col, (size_t)Mraw * 4);
+    const int* w_src = dev_in ? w : (const int*)mapped_host_range(w, (size_t)Mraw * 4);
+    if (!col_src || !w_src) {
+      if (cudaMemcpyAsync(w_raw, w, (size_t)Mraw * sizeof(int32_t), kind, s) != cudaSuccess ||
+          cudaMemcpyAsync(col_raw, col, (size_t)Mraw * sizeof(int32_t), kind, s) != cudaSuccess)
+        return bail(fail(MINCUT_ERR_CUDA, "copy input: %s", cudaGetErrorString(cudaGetLastError())));
+      col_src = col_raw;
+      w_src = w_raw;
+    }
+    if (tile_rows(rp_raw, n, Mraw, g->tile_row, s, &g->launches) != cudaSuccess ||
+        ingest_csr(n, Mraw, rp_raw, col_src, w_src, col_raw, w_raw, g->tile_row, ist, s,
+                   &g->launches) != cudaSuccess ||
+        cudaMemcpyAsync(hws, ist, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return bail(fail(MINCUT_ERR_CUDA, "input pass: %s", cudaGetErrorString(cudaGetLastError())));
+  }
   if (hws[1]) return bail(fail(MINCUT_ERR_INVALID, "negative weight"));
   g->wt64 = hws[0] > 0x7fffffffull;
   // An input already in canonical form (the form every contraction writes)
-  // is adopted as is: no relabel/sort/sum pass.
-  const long long ntiles = (std::max<long long>(Mraw, 1) + kEntryTile - 1) / kEntryTile + 2;
-  if (!galloc(g, &g->tile_row, ntiles)) return bail(fail(MINCUT_ERR_OOM, "tile rows"));
-  bool canonical = false;
-  if (Mraw > 0) {
-    unsigned* bad = reinterpret_cast<unsigned*>(wst + 3);
-    if (tile_rows(rp_raw, n, Mraw, g->tile_row, s, &g->launches) != cudaSuccess ||
-        canon_check<int32_t>(n, Mraw, rp_raw, col_raw, w_raw, g->tile_row, bad, s,
-                             &g->launches) != cudaSuccess ||
-        cudaMemcpyAsync(&hws[3], wst + 3, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                        s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return bail(fail(MINCUT_ERR_CUDA, "canonical check: %s", cudaGetErrorString(cudaGetLastError())));
-    canonical = hws[3] == 0;
-  }
+  // is adopted as is: no relabel/sort/sum pass; its symmetry is settled by
+  // the fingerprint.
+  const bool canonical = Mraw > 0 && hws[2] == 0;
+  const bool sym_fingerprint_ok = hws[3] == 0 && hws[4] == 0 && hws[5] == 0;
   const size_t wsz = g->wt64 ? 8 : 4;
   g->n0 = n;
   g->Mraw = Mraw;
@@ -1146,7 +1181,10 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
     }
     dev_free(g, wst);
     g->M0 = Mraw;
-    int rc = g->wt64 ? finish_input<int64_t>(g, n, validate) : finish_input<int32_t>(g, n, validate);
+    if (validate && !sym_fingerprint_ok)
+      return bail(fail(MINCUT_ERR_INVALID, "input CSR is not symmetric"));
+    int rc = g->wt64 ? finish_input<int64_t>(g, n, validate, true)
+                     : finish_input<int32_t>(g, n, validate, true);
     if (rc) return bail(rc);
     g->cur = -1;
     g->n = n;

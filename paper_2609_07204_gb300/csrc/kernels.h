@@ -114,13 +114,6 @@ constexpr int kEntryTile = 2048;  // entries per block of the entry-parallel ker
 cudaError_t tile_rows(const int64_t* rp, int n, long long M, int* tile_row, cudaStream_t s,
                       int* launches);
 
-// Sets *bad (atomicOr 1) unless every row is strictly increasing with
-// indices in [0, n), no self-loop and positive weights.  tile_row from
-// tile_rows(rp, ...); rp must be non-decreasing with rp[n] == M.
-template <typename WT>
-cudaError_t canon_check(int n, long long M, const int64_t* rp, const int* col, const WT* w,
-                        const int* tile_row, unsigned* bad, cudaStream_t s, int* launches);
-
 // Minimum degree and its vertex (smallest id) -> st->deg_val/deg_arg; lowers
 // st->lambda.  The degrees come with the CSR (build_csr).
 template <typename WT>
@@ -143,6 +136,17 @@ template <typename WT>
 cudaError_t build_csr(const u64* keys, const WT* vals, int N, int vbits, int n2, int* uid,
                       int* part, int64_t* rp2, int* col2, WT* w2, DevState* st, int* m2_dev,
                       int* urow, cudaStream_t s, int* launches);
+
+// Input pass over a CSR with non-decreasing rp (rp[0] = 0, rp[n] = M):
+// copies col/w from *_src (device memory or mapped host memory) to *_dst
+// (no copy when col_dst == col_src) and accumulates into stats (6 words,
+// zeroed by the caller): [0] sum of the non-negative weights, [1] any
+// negative weight, [2] any entry outside the canonical form, [3], [4] the
+// signed symmetry fingerprints and [5] the (u < v) - (u > v) balance, all
+// zero for a symmetric canonical graph.  tile_row: tile_rows() of rp.
+cudaError_t ingest_csr(int n, long long M, const int64_t* rp, const int* col_src,
+                       const int* w_src, int* col_dst, int* w_dst, const int* tile_row,
+                       unsigned long long* stats, cudaStream_t s, int* launches);
 
 template <typename WT>
 cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* col, const WT* w,

@@ -110,30 +110,6 @@ __global__ void degmin_final_kernel(const unsigned long long* __restrict__ blk, 
   }
 }
 
-// ------------------------------------------------------- canonical check
-// Sets *bad when some entry breaks the canonical form the contraction
-// produces: every row strictly increasing, indices in [0, n), no self-loop,
-// positive weights.  A graph that passes needs no canonicalisation sort.
-template <typename WT>
-__global__ void __launch_bounds__(kETThreads)
-    canon_check_kernel(int n, long long M, const int64_t* __restrict__ rp,
-                       const int* __restrict__ col, const WT* __restrict__ w,
-                       const int* __restrict__ tile_row, int ntiles, unsigned* bad) {
-  __shared__ TileRowsSmem tr;
-  tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
-  bool b = false;
-  const long long e0 = (long long)blockIdx.x * kET;
-  for (int i = 0; i < kETItems; ++i) {
-    const long long e = e0 + i * kETThreads + threadIdx.x;
-    if (e >= M) break;
-    const int u = tile_row_of(tr, rp, e);
-    const int v = col[e];
-    b |= v < 0 || v >= n || v == u || w[e] <= 0;
-    if (e > rp[u]) b |= col[e - 1] >= v;
-  }
-  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1u);
-}
-
 // ---------------------------------------------------------------- emit
 // Relabel every entry (u, v, w) to the key (L[u] << vbits) | L[v]; drop
 // self-loops (L[u] == L[v]) and zero weights.  With `validate`, also flag
@@ -1149,16 +1125,6 @@ cudaError_t tile_rows(const int64_t* rp, int n, long long M, int* tile_row, cuda
 }
 
 template <typename WT>
-cudaError_t canon_check(int n, long long M, const int64_t* rp, const int* col, const WT* w,
-                        const int* tile_row, unsigned* bad, cudaStream_t s, int* launches) {
-  if (M <= 0) return cudaSuccess;
-  const int ntiles = (int)((M + kET - 1) / kET);
-  canon_check_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, tile_row, ntiles, bad);
-  ++*launches;
-  return cudaGetLastError();
-}
-
-template <typename WT>
 cudaError_t degrees_min(const WT* deg, int n, unsigned long long* blk, DevState* st,
                         cudaStream_t s, int* launches) {
   const int nb = std::min(grid_for(n, 256), 1024);
@@ -1407,8 +1373,6 @@ cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream
 
 // ----------------------------------------------------- explicit instances
 #define MC_INST(WT)                                                                              \
-  template cudaError_t canon_check<WT>(int, long long, const int64_t*, const int*, const WT*,   \
-                                       const int*, unsigned*, cudaStream_t, int*);               \
   template cudaError_t degrees_min<WT>(const WT*, int, unsigned long long*, DevState*,           \
                                        cudaStream_t, int*);                                      \
   template cudaError_t emit_pairs<WT>(int, long long, const int64_t*, const int*, const WT*,     \

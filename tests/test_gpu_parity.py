@@ -187,6 +187,69 @@ def test_from_csr_rejects_malformed(case):
     assert e.value.status == mc.MINCUT_ERR_INVALID
 
 
+@pytest.mark.parametrize("case", ["swap_weights", "two_vertex", "moved_mirror"])
+def test_from_csr_rejects_asymmetry_with_balanced_counts(case):
+    """Asymmetric canonical inputs whose (u < v) and (u > v) entry counts
+    agree: only the triples differ (caught by the symmetry fingerprint of
+    the input pass; the exact check covers non-canonical inputs)."""
+    if case == "swap_weights":
+        # 0-1 and 0-2 with weights 1, 2; mirrors carry them swapped
+        rp, col, w = [0, 2, 3, 4], [1, 2, 0, 0], [1, 2, 2, 1]
+        n = 3
+    elif case == "two_vertex":
+        rp, col, w = [0, 1, 2], [1, 0], [1, 2]
+        n = 2
+    else:
+        # 0-1 present both ways; 0->2 is answered by 3->1 instead of 2->0
+        rp, col, w = [0, 2, 3, 3, 4], [1, 2, 0, 1], [1, 1, 1, 1]
+        n = 4
+    for pinned in (False, True):
+        args = [np.asarray(rp, np.int64), np.asarray(col, np.int32), np.asarray(w, np.int32)]
+        if pinned:
+            args = [torch.from_numpy(a).pin_memory().numpy() for a in args]
+        with pytest.raises(mc.MincutError) as e:
+            mc.mincut_graph_from_csr(n, *args)
+        assert e.value.status == mc.MINCUT_ERR_INVALID
+    g = mc.mincut_graph_from_csr(n, np.asarray(rp, np.int64), np.asarray(col, np.int32),
+                                 np.asarray(w, np.int32), skip_validate=True)
+    g.destroy()
+
+
+@pytest.mark.parametrize("canonical", [True, False])
+def test_from_csr_pinned_host_matches_pageable_and_device(canonical):
+    """Entries in pinned host memory are read in place by the input pass;
+    the graph equals the one built from pageable host arrays and from device
+    tensors, and so do the solves."""
+    rng = np.random.default_rng(21)
+    if canonical:
+        g0 = synth.core_lcc(synth.rmat(13, 8, wlo=1, whi=9, seed=21), 3)
+        rp, col, w = g0.row_ptr, g0.col, g0.w
+        n = g0.n
+    else:
+        n = 900
+        rp, col, w = noncanonical(n, rng, 12000)
+    rp = np.asarray(rp, np.int64); col = np.asarray(col, np.int32); w = np.asarray(w, np.int32)
+    c = canon(n, rp, col, w)
+    pin = [torch.from_numpy(a).pin_memory() for a in (rp, col, w)]
+    dev = [torch.from_numpy(a).cuda() for a in (rp, col, w)]
+    ref = None
+    for kind in ("pageable", "pinned", "device"):
+        if kind == "pageable":
+            g = mc.mincut_graph_from_csr(n, rp, col, w)
+        elif kind == "pinned":
+            g = mc.mincut_graph_from_csr(n, *(t.numpy() for t in pin))
+        else:
+            g = mc.mincut_graph_from_csr(n, *dev)
+        assert_csr_equal(mc.mincut_graph_export_csr(g), c)
+        v = mc.mincut_solve(g, bitmap=False)[0]
+        if ref is None:
+            ref = v
+        assert v == ref
+        g.destroy()
+    if n <= 1000:
+        assert ref == oracle.stoer_wagner(n, *c)[0]
+
+
 # -------------------------------------------------------------- contraction
 @pytest.mark.parametrize("n,p,seed", [(3, 0.9, 0), (60, 0.2, 1), (700, 0.05, 2), (3000, 0.01, 3)])
 def test_contract_by_groups_bit_exact(n, p, seed):
