@@ -164,6 +164,7 @@ struct mincut_graph {
   int *lp_size = nullptr, *long_rows = nullptr, *long_count = nullptr, *pool_lab = nullptr;
   // row-wise contraction (allocated at the first contraction that uses it)
   RowScratch rows{};
+  long long acc_zeroed = 0;  // dense accumulator slots known to be zero
   int64_t* rpG = nullptr;
   int* colG = nullptr;
   void* wG = nullptr;
@@ -376,7 +377,7 @@ int ensure_rows(mincut_graph* g) {
       !galloc(g, &r.kcnt, n + 1) || !galloc(g, &r.off, n + 1) ||
       !galloc(g, &r.part, (n + 1) / 4096 + 3) || !galloc(g, &r.total, 1) ||
       !galloc(g, &r.side_v, M) || !galloc(g, &r.vinfo, n + 1) || !galloc(g, &g->rpG, n + 1) ||
-      !galloc(g, &r.dsum, n + 1) || !galloc(g, &r.did, n + 1) || !galloc(g, &r.ndense, 1) ||
+      !galloc(g, &r.dsum, n + 1) || !galloc(g, &r.did, n + 1) ||
       !galloc(g, &r.chunk, 4 * M / kDenseChunk + n + 64) ||
       !galloc(g, &r.dense_group, n + 1) ||
       !(r.acc = dev_alloc(g, (size_t)4 * M * wsz)) ||
@@ -387,8 +388,9 @@ int ensure_rows(mincut_graph* g) {
   }
   r.single_entries = &g->st->single_entries;
   r.dense_entries = &g->st->dense_entries;
+  r.ndense = &g->st->ndense;
   r.dense_slots = 4 * M;
-  CK(cudaMemsetAsync(r.acc, 0, (size_t)r.dense_slots * wsz, g->stream));
+  g->acc_zeroed = 0;  // accumulator slots are cleared as rounds first need them
   return MINCUT_OK;
 }
 
@@ -500,6 +502,18 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
     rc = sync_state(g);
     if (rc) return rc;
     rowwise = 4 * (long long)(g->hst->single_entries + g->hst->dense_entries) >= M;
+    if (rowwise) {
+      // the dense accumulators this round uses must be zero: slots below
+      // acc_zeroed are (the writing kernel clears what it read)
+      const long long need =
+          (long long)std::min(g->hst->ndense, dense_capacity(n2, g->rows)) * n2;
+      if (need > g->acc_zeroed) {
+        const size_t wsz = g->wt64 ? 8 : 4;
+        CK(cudaMemsetAsync(static_cast<char*>(g->rows.acc) + (size_t)g->acc_zeroed * wsz, 0,
+                           (size_t)(need - g->acc_zeroed) * wsz, s));
+        g->acc_zeroed = need;
+      }
+    }
   }
   long long m2 = 0;
   if (rowwise) {

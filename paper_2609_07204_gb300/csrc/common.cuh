@@ -51,6 +51,7 @@ struct DevState {
   long long sym_balance;       // symmetry check: entries u < v minus entries u > v
   unsigned long long single_entries;  // contraction: entries of single-vertex groups' rows
   unsigned long long dense_entries;   // contraction: entries of dense groups' rows
+  int ndense;                         // contraction: dense groups asked for this round
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -295,10 +295,11 @@ struct RowScratch {
   unsigned long long* single_entries;  // entries of singleton groups' rows
   int* dsum;    // n: entries of each group's member rows
   int* did;     // n: dense accumulator slot of a dense group
-  int* ndense;  // 1: dense groups this round
+  int* ndense;  // 1: dense groups asked for this round (in the device state)
   int* chunk;   // dense_slots / kDenseChunk + n + 64: per-chunk counts, then offsets
-  void* acc;    // dense_slots weights: dense accumulators, n2 per dense group (zero between
-                // rounds: the writing kernel clears what it read)
+  void* acc;    // dense_slots weights: dense accumulators, n2 per dense group (the caller
+                // zeroes slots before their first use; the writing kernel clears what
+                // it read)
   long long dense_slots;
   int* dense_group;  // n: group of each dense slot
   unsigned long long* dense_entries;  // entries of the dense groups' rows
@@ -308,6 +309,9 @@ constexpr int kDenseChunk = 2048;  // accumulator slots per block of the dense k
 // cnt, gen (multi-member groups) and *single_entries.
 cudaError_t rows_classify(int n, int n2, const int64_t* rp, const int* L, const RowScratch& rs,
                           cudaStream_t s, int* launches);
+
+// Dense groups the accumulators hold for n2 vertices: min(n2, dense_slots / n2).
+int dense_capacity(int n2, const RowScratch& rs);
 
 // Groups whose member rows hold at least max(n2 / 16, 256) entries take a
 // dense accumulator of n2 slots (gen = 2) while accumulators are left
