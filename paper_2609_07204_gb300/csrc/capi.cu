@@ -165,6 +165,7 @@ struct mincut_graph {
   // row-wise contraction (allocated at the first contraction that uses it)
   RowScratch rows{};
   long long acc_zeroed = 0;  // dense accumulator slots known to be zero
+  bool m_pending = false;    // M of the current graph is in st->m_rows (not yet read)
   int64_t* rpG = nullptr;
   int* colG = nullptr;
   void* wG = nullptr;
@@ -375,7 +376,7 @@ int ensure_rows(mincut_graph* g) {
   RowScratch& r = g->rows;
   if (!galloc(g, &r.cnt, n + 1) || !galloc(g, &r.gen, n + 1) || !galloc(g, &r.len, n + 1) ||
       !galloc(g, &r.kcnt, n + 1) || !galloc(g, &r.off, n + 1) ||
-      !galloc(g, &r.part, (n + 1) / 4096 + 3) || !galloc(g, &r.total, 1) ||
+      !galloc(g, &r.part, (n + 1) / 4096 + 3) ||
       !galloc(g, &r.side_v, M) || !galloc(g, &r.vinfo, n + 1) || !galloc(g, &g->rpG, n + 1) ||
       !galloc(g, &r.dsum, n + 1) || !galloc(g, &r.did, n + 1) ||
       !galloc(g, &r.chunk, 4 * M / kDenseChunk + n + 64) ||
@@ -389,6 +390,7 @@ int ensure_rows(mincut_graph* g) {
   r.single_entries = &g->st->single_entries;
   r.dense_entries = &g->st->dense_entries;
   r.ndense = &g->st->ndense;
+  r.total = &g->st->m_rows;
   r.dense_slots = 4 * M;
   g->acc_zeroed = 0;  // accumulator slots are cleared as rounds first need them
   return MINCUT_OK;
@@ -435,7 +437,7 @@ int ensure_lp(mincut_graph* g) {
 // singleton rows rebuilt in place, the other rows through emit / sort /
 // build into a general CSR, then both placed into the next buffers.
 template <typename WT>
-int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out) {
+int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out, bool defer_m) {
   cudaStream_t s = g->stream;
   const int n = g->n;
   const long long M = g->M;
@@ -469,11 +471,14 @@ int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out) {
                        (const WT*)g->side_w, g->rpG, g->colG, (const WT*)g->wG, mG, g->tile_row,
                        g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], (WT*)g->degb[nxt], s,
                        &g->launches)); }
-  int m2 = 0;
-  CK(cudaMemcpyAsync(&m2, rs.total, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (defer_m) {
+    // the entry count is read with the next synchronisation (st->m_rows)
+    *m2_out = -1;
+    return MINCUT_OK;
+  }
   rc = sync_state(g);
   if (rc) return rc;
-  *m2_out = m2;
+  *m2_out = g->hst->m_rows;
   return MINCUT_OK;
 }
 
@@ -481,26 +486,32 @@ int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out) {
 // relabel, then either the row-wise path (when at least a quarter of the
 // entries lie in rows of single-vertex groups or of dense groups) or emit /
 // sort / build of all entries; the result becomes the current graph.
+// defer_m: on the row-wise path, leave the new entry count in st->m_rows for
+// the caller's next synchronisation (g->m_pending) instead of waiting here.
 template <typename WT>
-int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compose) {
+int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compose,
+                     bool defer_m = false) {
   cudaStream_t s = g->stream;
   const int n = g->n;
   const long long M = g->M;
   { ProfScope ps(P_UF, n, s);
     CK(uf_relabel(g->parent, g->L, g->flags, g->rank, g->part, n, g->st, s, &g->launches)); }
+  // the row classification runs before the vertex count n2 is known on the
+  // host (n bounds it): one synchronisation serves both
+  const bool try_rows = g->rowwise && M > 0 && n > 2;
+  if (try_rows) {
+    int rc = ensure_rows(g);
+    if (rc) return rc;
+    ProfScope ps(P_UF, n, s);
+    CK(rows_classify(n, n, g->crp(), g->L, g->rows, s, &g->launches));
+    CK(rows_dense_mark(n, &g->st->n_next, g->rows, s, &g->launches));
+  }
   int rc = sync_state(g);
   if (rc) return rc;
   const int n2 = g->hst->n_next;
   const int nxt = g->cur == 0 ? 1 : 0;
   bool rowwise = false;
-  if (g->rowwise && n2 > 1 && M > 0) {
-    rc = ensure_rows(g);
-    if (rc) return rc;
-    { ProfScope ps(P_UF, n, s);
-      CK(rows_classify(n, n2, g->crp(), g->L, g->rows, s, &g->launches));
-      CK(rows_dense_mark(n2, g->rows, s, &g->launches)); }
-    rc = sync_state(g);
-    if (rc) return rc;
+  if (try_rows && n2 > 1) {
     rowwise = 4 * (long long)(g->hst->single_entries + g->hst->dense_entries) >= M;
     if (rowwise) {
       // the dense accumulators this round uses must be zero: slots below
@@ -517,7 +528,7 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   }
   long long m2 = 0;
   if (rowwise) {
-    rc = contract_rows<WT>(g, n2, nxt, &m2);
+    rc = contract_rows<WT>(g, n2, nxt, &m2, defer_m);
     if (rc) return rc;
   } else {
     const int vbits = bits_for(n2);
@@ -552,6 +563,7 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   g->cur = nxt;
   g->n = n2;
   g->M = m2;
+  g->m_pending = m2 < 0;
   *n2_out = n2;
   *m2_out = m2;
   return MINCUT_OK;
@@ -592,7 +604,6 @@ template <typename WT>
 int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, RoundOut* o) {
   cudaStream_t s = g->stream;
   const int n = g->n;
-  const long long M = g->M;
   const int64_t* rp = g->crp();
   const int* col = g->ccol();
   const WT* w = (const WT*)g->cw();
@@ -605,6 +616,11 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   }
   int rc = sync_state(g);
   if (rc) return rc;
+  if (g->m_pending) {  // the previous contraction's entry count came with this sync
+    g->M = g->hst->m_rows;
+    g->m_pending = false;
+  }
+  const long long M = g->M;
   long long lam = (long long)g->hst->lambda;
   if (lam < lambda_before) {
     ProfScope ps(P_WITNESS, g->n0, s);
@@ -793,7 +809,8 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
     }
     int n2 = 0;
     long long m2 = 0;
-    rc = contract_current<WT>(g, &n2, &m2, true);
+    // (the visit-mode choice times each round to its end: no deferral then)
+    rc = contract_current<WT>(g, &n2, &m2, true, op.cf_visit != 2);
     if (rc) return rc;
     if (op.cf_visit == 2 && rate[mode] < 0) {
       const double ms = std::chrono::duration<double, std::milli>(
@@ -801,6 +818,12 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
       rate[mode] = (double)(n_before - n2) / std::max(ms, 1e-3);
     }
     if (n2 <= 1) break;
+  }
+  if (g->m_pending) {
+    const int rc = sync_state(g);
+    if (rc) return rc;
+    g->M = g->hst->m_rows;
+    g->m_pending = false;
   }
   *lambda_io = lambda;
   return MINCUT_OK;

@@ -52,6 +52,7 @@ struct DevState {
   unsigned long long single_entries;  // contraction: entries of single-vertex groups' rows
   unsigned long long dense_entries;   // contraction: entries of dense groups' rows
   int ndense;                         // contraction: dense groups asked for this round
+  int m_rows;                         // contraction: entries of the row-wise contracted graph
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -81,9 +81,17 @@ __global__ void single_entries_kernel(const int64_t* __restrict__ rp, const int*
 // Dense groups: big enough that an n2-slot accumulator (n2 slots read to
 // count and to write, ~8 B each) costs less than sorting their entries
 // (~120 B each through emit, radix passes and segmented sum).
-__global__ void dense_mark_kernel(int n2, const int* __restrict__ dsum, int* __restrict__ gen,
-                                  int* __restrict__ did, int* ndense, int max_dense,
+// n2 is read on the device (the union-find relabel's vertex count), so the
+// decision needs no synchronisation of its own; the capacity is
+// dense_capacity(n2): min(n2, dense_slots / n2).
+__global__ void dense_mark_kernel(const int* __restrict__ n2p, long long dense_slots,
+                                  const int* __restrict__ dsum, int* __restrict__ gen,
+                                  int* __restrict__ did, int* ndense,
                                   unsigned long long* dense_entries) {
+  const int n2 = *n2p;
+  if (n2 <= 1) return;
+  const int max_dense = (int)min((long long)n2, dense_slots / n2);
+  if (max_dense <= 0) return;
   const int thr = max(n2 / 16, 256);
   unsigned long long tot = 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n2; g += gridDim.x * blockDim.x) {
@@ -482,13 +490,12 @@ int dense_capacity(int n2, const RowScratch& rs) {
   return (int)std::min<long long>(n2, rs.dense_slots / std::max(n2, 1));
 }
 
-cudaError_t rows_dense_mark(int n2, const RowScratch& rs, cudaStream_t s, int* launches) {
+cudaError_t rows_dense_mark(int n_bound, const int* n2_dev, const RowScratch& rs, cudaStream_t s,
+                            int* launches) {
   cudaMemsetAsync(rs.ndense, 0, sizeof(int), s);
   cudaMemsetAsync(rs.dense_entries, 0, sizeof(unsigned long long), s);
-  const int max_dense = dense_capacity(n2, rs);
-  if (max_dense <= 0) return cudaGetLastError();
-  dense_mark_kernel<<<grid_blocks(n2, 256), 256, 0, s>>>(n2, rs.dsum, rs.gen, rs.did, rs.ndense,
-                                                         max_dense, rs.dense_entries);
+  dense_mark_kernel<<<grid_blocks(n_bound, 256), 256, 0, s>>>(
+      n2_dev, rs.dense_slots, rs.dsum, rs.gen, rs.did, rs.ndense, rs.dense_entries);
   ++*launches;
   return cudaGetLastError();
 }

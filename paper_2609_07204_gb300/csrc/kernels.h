@@ -289,7 +289,7 @@ struct RowScratch {
   int* kcnt;    // n: distinct moved labels of a singleton row
   int* off;     // n + 1: exclusive scan of len
   int* part;    // scan partials (n / 4096 + 2)
-  int* total;   // 1: sum of len (the contracted entry count)
+  int* total;   // 1: sum of len (the contracted entry count; in the device state)
   int* side_v;  // M: a singleton row's moved labels at the row's own offset
   int* vinfo;   // n: L[x], with the top bit set when x's group has several members
   unsigned long long* single_entries;  // entries of singleton groups' rows
@@ -306,7 +306,8 @@ struct RowScratch {
 };
 constexpr int kDenseChunk = 2048;  // accumulator slots per block of the dense kernels
 
-// cnt, gen (multi-member groups) and *single_entries.
+// cnt, gen (multi-member groups) and *single_entries.  n2 only sizes the
+// cleared arrays: any bound >= the relabelled vertex count will do.
 cudaError_t rows_classify(int n, int n2, const int64_t* rp, const int* L, const RowScratch& rs,
                           cudaStream_t s, int* launches);
 
@@ -316,7 +317,9 @@ int dense_capacity(int n2, const RowScratch& rs);
 // Groups whose member rows hold at least max(n2 / 16, 256) entries take a
 // dense accumulator of n2 slots (gen = 2) while accumulators are left
 // (min(n2, dense_slots / n2) of them); their entries go to *dense_entries.
-cudaError_t rows_dense_mark(int n2, const RowScratch& rs, cudaStream_t s, int* launches);
+// n2 is read from n2_dev on the device; n_bound >= n2 sizes the grid.
+cudaError_t rows_dense_mark(int n_bound, const int* n2_dev, const RowScratch& rs, cudaStream_t s,
+                            int* launches);
 
 // Dense groups: accumulate their entries (acc must be zero), count the
 // distinct labels into len.
