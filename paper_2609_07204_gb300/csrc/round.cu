@@ -674,18 +674,43 @@ __global__ void __launch_bounds__(kETThreads)
                     unsigned long long* __restrict__ best) {
   __shared__ TileRowsSmem tr;
   tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
-  const long long e0 = (long long)blockIdx.x * kET;
-  for (int i = 0; i < kETItems; ++i) {
-    const long long e = e0 + i * kETThreads + threadIdx.x;
-    bool valid = e < M;
-    int u = 0;
-    unsigned long long key = 0;
-    if (valid) {
-      u = tile_row_of(tr, rp, e);
-      key = ((unsigned long long)(unsigned)w[e] << 32) | (0xffffffffu - (unsigned)col[e]);
+  // run layout: this thread's kETItems consecutive entries; rows wholly
+  // inside the run publish their maximum directly, the first and the last
+  // row's are combined across the warp
+  const long long eb = (long long)blockIdx.x * kET + (long long)threadIdx.x * kETItems;
+  const int cnt = (int)max(0ll, min((long long)kETItems, M - eb));
+  int c[kETItems];
+  WT x[kETItems];
+  load_run<WT>(col, w, eb, cnt, c, x);
+  int first = 0, cur = 0;
+  unsigned long long first_max = 0, m = 0;
+  if (cnt > 0) {
+    first = cur = tile_row_of(tr, rp, eb);
+    long long rend = tile_rp(tr, rp, cur + 1);
+#pragma unroll
+    for (int k = 0; k < kETItems; ++k) {
+      if (k < cnt) {
+        const long long e = eb + k;
+        while (e >= rend) {  // leave row cur (skipping empty rows)
+          if (cur == first) first_max = m;
+          else if (m && ((cur ^ sweep) & 1) == 0) atomicMax(&best[cur], m);
+          m = 0;
+          ++cur;
+          rend = tile_rp(tr, rp, cur + 1);
+        }
+        const unsigned long long key =
+            ((unsigned long long)(unsigned)x[k] << 32) | (0xffffffffu - (unsigned)c[k]);
+        if (key > m) m = key;
+      }
     }
-    warp_segment_max(u, key, valid && (((u ^ sweep) & 1) == 0), best);
+    if (cur == first) {
+      first_max = m;
+      m = 0;
+    }
   }
+  warp_segment_max(first, first_max, cnt > 0 && ((first ^ sweep) & 1) == 0, best);
+  // (the last rows of the lanes whose run spans several rows are distinct)
+  warp_segment_max(cur, m, cnt > 0 && cur != first && ((cur ^ sweep) & 1) == 0, best);
 }
 
 __global__ void lp_first_finish_kernel(int n, const unsigned long long* __restrict__ best,
@@ -961,19 +986,46 @@ __global__ void __launch_bounds__(kETThreads)
                   const int* __restrict__ tile_row, int ntiles, long long* __restrict__ cut) {
   __shared__ TileRowsSmem tr;
   tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
-  const long long e0 = (long long)blockIdx.x * kET;
-  for (int i = 0; i < kETItems; ++i) {
-    const long long e = e0 + i * kETThreads + threadIdx.x;
-    const bool valid = e < M;
-    int u = 0, lu = 0;
-    long long val = 0;
-    if (valid) {
-      u = tile_row_of(tr, rp, e);
-      lu = lab[u];
-      if (lab[col[e]] != lu) val = (long long)w[e];
+  // run layout: this thread's kETItems consecutive entries
+  const long long eb = (long long)blockIdx.x * kET + (long long)threadIdx.x * kETItems;
+  const int cnt = (int)max(0ll, min((long long)kETItems, M - eb));
+  int c[kETItems];
+  WT x[kETItems];
+  load_run<WT>(col, w, eb, cnt, c, x);
+  int lv[kETItems];
+#pragma unroll
+  for (int k = 0; k < kETItems; ++k) lv[k] = k < cnt ? lab[c[k]] : 0;  // independent gathers
+  // walk the rows: rows wholly inside the run add their cut share directly;
+  // the first and the last row's shares are combined across the warp
+  int first = 0, cur = 0, lfirst = 0, lcur = 0;
+  long long first_acc = 0, acc = 0;
+  if (cnt > 0) {
+    first = cur = tile_row_of(tr, rp, eb);
+    lfirst = lcur = lab[cur];
+    long long rend = tile_rp(tr, rp, cur + 1);
+#pragma unroll
+    for (int k = 0; k < kETItems; ++k) {
+      if (k < cnt) {
+        const long long e = eb + k;
+        while (e >= rend) {  // leave row cur (skipping empty rows)
+          if (cur == first) first_acc = acc;
+          else if (acc) atomicAdd((unsigned long long*)&cut[lcur], (unsigned long long)acc);
+          acc = 0;
+          ++cur;
+          rend = tile_rp(tr, rp, cur + 1);
+          lcur = lab[cur];
+        }
+        if (lv[k] != lcur) acc += (long long)x[k];
+      }
     }
-    warp_segment_add<long long, long long>(u, lu, val, valid, cut);
+    if (cur == first) {
+      first_acc = acc;
+      acc = 0;
+    }
   }
+  warp_segment_add<long long, long long>(first, lfirst, first_acc, cnt > 0, cut);
+  // (the last rows of the lanes whose run spans several rows are distinct)
+  warp_segment_add<long long, long long>(cur, lcur, acc, cnt > 0 && cur != first, cut);
 }
 
 // Cluster sizes; lanes of a warp with the same label add once (large

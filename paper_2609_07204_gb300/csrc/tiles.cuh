@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -86,6 +88,51 @@ __device__ __forceinline__ void warp_segment_add(int seg, int target, T val, boo
   const int rn = __shfl_down_sync(FULL, r, 1);
   const bool last = lane == 31 || rn != r;
   if (valid && last && x != T(0)) atomic_add_w(&out[target], (O)x);
+}
+
+// Run layout of an entry tile: thread t owns the kETItems consecutive
+// entries e0 + kETItems * t ... (clipped to M), so that it finds its first
+// entry's row once and walks the rows forward instead of searching the row
+// of every entry.  tile_rp(s, rp, r) = rp[r] for rows r0 .. r1 + 1.
+__device__ __forceinline__ long long tile_rp(const TileRowsSmem& s, const int64_t* rp, int r) {
+  return s.use ? s.rp[r - s.r0] : (long long)rp[r];
+}
+
+// Loads a thread's run of cnt <= kETItems entries starting at eb: 16-byte
+// vector loads when the run is whole and the arrays are 16-byte aligned.
+template <typename WT>
+__device__ __forceinline__ void load_run(const int* __restrict__ col, const WT* __restrict__ w,
+                                         long long eb, int cnt, int (&c)[kETItems],
+                                         WT (&x)[kETItems]) {
+  static_assert(kETItems == 8, "run loads assume 8 entries per thread");
+  const bool vec = cnt == kETItems && ((reinterpret_cast<uintptr_t>(col) |
+                                         reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  if (vec) {
+    const int4* cp = reinterpret_cast<const int4*>(col + eb);
+    const int4 a = cp[0], b = cp[1];
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+    if (sizeof(WT) == 4) {
+      const int4* wp = reinterpret_cast<const int4*>(w + eb);
+      const int4 p = wp[0], q = wp[1];
+      x[0] = (WT)p.x; x[1] = (WT)p.y; x[2] = (WT)p.z; x[3] = (WT)p.w;
+      x[4] = (WT)q.x; x[5] = (WT)q.y; x[6] = (WT)q.z; x[7] = (WT)q.w;
+    } else {
+      const longlong2* wp = reinterpret_cast<const longlong2*>(w + eb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const longlong2 p = wp[k];
+        x[2 * k] = (WT)p.x;
+        x[2 * k + 1] = (WT)p.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kETItems; ++k) {
+      c[k] = k < cnt ? col[eb + k] : 0;
+      x[k] = k < cnt ? w[eb + k] : WT(0);
+    }
+  }
 }
 
 }  // namespace mc
