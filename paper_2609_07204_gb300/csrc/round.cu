@@ -257,25 +257,63 @@ __global__ void rp_search_kernel(const int* __restrict__ urow, const int* __rest
   }
 }
 
-// deg[u] = sum of w over row u (entry tiles, warp segmented sums).
+// deg[u] = sum of w over row u.  Run layout: each thread sums its 8
+// consecutive entries per row; rows wholly inside a run are written by it,
+// the first and last rows of the runs are combined across the warp.
 template <typename WT>
 __global__ void __launch_bounds__(kETThreads)
     degree_kernel(int n, long long M, const int64_t* __restrict__ rp, const WT* __restrict__ w,
                   const int* __restrict__ tile_row, int ntiles, WT* __restrict__ deg) {
   __shared__ TileRowsSmem tr;
   tile_rows_load(tr, rp, n, tile_row, ntiles, blockIdx.x);
-  const long long e0 = (long long)blockIdx.x * kET;
-  for (int i = 0; i < kETItems; ++i) {
-    const long long e = e0 + i * kETThreads + threadIdx.x;
-    const bool valid = e < M;
-    int u = 0;
-    long long val = 0;
-    if (valid) {
-      u = tile_row_of(tr, rp, e);
-      val = (long long)w[e];
+  const long long eb = (long long)blockIdx.x * kET + (long long)threadIdx.x * kETItems;
+  const int cnt = (int)max(0ll, min((long long)kETItems, M - eb));
+  WT x[kETItems];
+  if (cnt == kETItems && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+    if (sizeof(WT) == 4) {
+      const int4* wp = reinterpret_cast<const int4*>(w + eb);
+      const int4 p = wp[0], q = wp[1];
+      x[0] = (WT)p.x; x[1] = (WT)p.y; x[2] = (WT)p.z; x[3] = (WT)p.w;
+      x[4] = (WT)q.x; x[5] = (WT)q.y; x[6] = (WT)q.z; x[7] = (WT)q.w;
+    } else {
+      const longlong2* wp = reinterpret_cast<const longlong2*>(w + eb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const longlong2 p = wp[k];
+        x[2 * k] = (WT)p.x;
+        x[2 * k + 1] = (WT)p.y;
+      }
     }
-    warp_segment_add<long long, WT>(u, u, val, valid, deg);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kETItems; ++k) x[k] = k < cnt ? w[eb + k] : WT(0);
   }
+  int first = 0, cur = 0;
+  long long first_acc = 0, acc = 0;
+  if (cnt > 0) {
+    first = cur = tile_row_of(tr, rp, eb);
+    long long rend = tile_rp(tr, rp, cur + 1);
+#pragma unroll
+    for (int k = 0; k < kETItems; ++k) {
+      if (k < cnt) {
+        while (eb + k >= rend) {  // leave row cur (empty rows keep deg 0)
+          if (cur == first) first_acc = acc;
+          else deg[cur] = (WT)acc;  // the whole row lies in this run
+          acc = 0;
+          ++cur;
+          rend = tile_rp(tr, rp, cur + 1);
+        }
+        acc += (long long)x[k];
+      }
+    }
+    if (cur == first) {
+      first_acc = acc;
+      acc = 0;
+    }
+  }
+  warp_segment_add<long long, WT>(first, first, first_acc, cnt > 0, deg);
+  // (the last rows of the lanes whose run spans several rows are distinct)
+  warp_segment_add<long long, WT>(cur, cur, acc, cnt > 0 && cur != first, deg);
 }
 
 __global__ void rp_fill_kernel(int64_t* rp2, int n2) {
