@@ -196,7 +196,20 @@ def measure_batched(mc, n_graphs: int = 4096, alone: int = 256, reps: int = 3):
         graphs.append((s.n, s.row_ptr, s.col, s.w))
     vo, rp, col, w = mc.pack_graphs(graphs)
     B = mc.mincut_batch_from_csr(vo, rp, col, w)
-    mc.mincut_batch_solve(B, bitmap=False)
+    mc.mincut_batch_solve(B, bitmap=False)  # first solve: times the warp-solver thresholds
+    small_n, small_graphs = mc.mincut_batch_info(B)
+    paths = {}
+    for name, t in (("round_kernels_only", -1), ("one_warp_per_graph_only", 2048)):
+        o = mc.default_options(batch_small_n=t)
+        mc.mincut_batch_solve(B, o, bitmap=False)
+        tp = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mc.mincut_batch_solve(B, o)
+            torch.cuda.synchronize()
+            tp.append(time.perf_counter() - t0)
+        paths[name] = {"ms_per_batch": statistics.median(tp) * 1e3}
     ts = []
     launches = 0
     for _ in range(reps):
@@ -224,7 +237,10 @@ def measure_batched(mc, n_graphs: int = 4096, alone: int = 256, reps: int = 3):
             "solves_per_s": rate, "ms_per_batch": t_batch * 1e3, "rounds": st["rounds"],
             "one_at_a_time_solves_per_s": 1.0 / t_one,
             "speedup_vs_one_at_a_time": rate * t_one, "gpu_launches_per_batch": launches // reps,
-            "one_at_a_time_sample": alone}
+            "one_at_a_time_sample": alone,
+            "warp_solver": {"threshold_n": small_n, "graphs": small_graphs,
+                            "chosen_by": "timing candidate thresholds on the first solve"},
+            "paths": paths}
 
 
 def measure_variants(mc, g, val, reps: int = 3):

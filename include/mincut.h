@@ -93,6 +93,11 @@ typedef struct mincut_options {
                                 concurrent passes mark nothing, each a whole pass from its own
                                 start vertex with private arrays: 1 = the single pass of
                                 Algorithm 2; 0 = auto (one per SM, device memory permitting) */
+    int32_t batch_small_n;   /* mincut_batch_solve: graphs of at most this many vertices (and at
+                                most 2048) are solved one per warp, each running all its rounds
+                                alone; the others share the batch's round kernels.  0 = auto
+                                (chosen by timing candidate thresholds on the first solve of the
+                                batch, then kept); < 0 = every graph in the round kernels */
 } mincut_options;
 
 /* Statistics of a solve (all optional to read). */
@@ -215,6 +220,12 @@ int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
  * that does not hold the graph's first vertex. */
 int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_values,
                        uint64_t* side_bitmap, mincut_stats* stats);
+
+/* How the last mincut_batch_solve split the batch: *small_n = the vertex
+ * threshold of the one-warp-per-graph solver it used (the timed choice when
+ * opts->batch_small_n was 0; -1 before any solve), *small_graphs = the graphs
+ * it solved that way.  MINCUT_ERR_INVALID if g is not a batch. */
+int mincut_batch_info(const mincut_graph* g, int32_t* small_n, int64_t* small_graphs);
 
 /* Per-kernel-category timing collected by solves run with opts->profile = 1
  * (CUDA events recorded on the graph's stream around each launch).  Fills up

@@ -52,7 +52,8 @@ class MincutOptions(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("deterministic", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
                 ("profile", ctypes.c_int32), ("init_bound", ctypes.c_int32),
-                ("cf_visit", ctypes.c_int32), ("seq_passes", ctypes.c_int32)]
+                ("cf_visit", ctypes.c_int32), ("seq_passes", ctypes.c_int32),
+                ("batch_small_n", ctypes.c_int32)]
 
 
 class MincutStats(ctypes.Structure):
@@ -170,6 +171,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mincut_batch_solve.argtypes = [vp, ctypes.POINTER(MincutOptions), vp, vp,
                                        ctypes.POINTER(MincutStats)]
     lib.mincut_batch_solve.restype = ctypes.c_int
+    lib.mincut_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(i64)]
+    lib.mincut_batch_info.restype = ctypes.c_int
     lib.mincut_graph_footprint.argtypes = [i64, i64]
     lib.mincut_graph_footprint.restype = i64
     lib.mincut_release_cached.argtypes = [ctypes.c_int]
@@ -368,6 +371,15 @@ def mincut_batch_solve(g: Graph, opts: Optional[MincutOptions] = None, *, bitmap
                                 ctypes.byref(st))
     _check(rc)
     return vals, bm, st.as_dict()
+
+
+def mincut_batch_info(g: Graph) -> tuple[int, int]:
+    """(vertex threshold of the one-warp-per-graph solver used by the last
+    batch solve, number of graphs it solved)."""
+    t = ctypes.c_int32(0)
+    k = ctypes.c_int64(0)
+    _check(load_library().mincut_batch_info(g.handle, ctypes.byref(t), ctypes.byref(k)))
+    return int(t.value), int(k.value)
 
 
 def mincut_solve(g: Graph, opts: Optional[MincutOptions] = None, *, bitmap: bool = True,

@@ -198,7 +198,17 @@ struct mincut_graph {
   // packed batch (batch.G > 0)
   BatchState batch;
   std::vector<long long> voff0_h;
+  std::vector<int> batch_m;  // entries of each graph of a batch (canonical input)
   int max_graph_n = 0;
+  // graphs solved one per warp (batch_warp.cu)
+  int bw_threshold = -1;      // the list below holds the graphs with n <= this
+  int bw_auto = -1;           // threshold chosen by timing (batch_small_n = 0), -1: not yet
+  int* bw_list = nullptr;     // graph ids, most entries first
+  int bw_count = 0, bw_nmax = 0, bw_mmax = 0;
+  int* bw_cursor = nullptr;
+  int* bw_scratch = nullptr;
+  long long bw_scratch_words = 0;
+  int bw_slots = 0;
   unsigned long long* batch_levels = nullptr;
   long long* batch_vals = nullptr;
   long long spin_limit = 1ll << 22;
@@ -358,7 +368,9 @@ int sync_state(mincut_graph* g) {
   if (e & ERR_INPUT) return fail(MINCUT_ERR_INVALID, "index out of range or negative weight");
   if (e & ERR_ASYM) return fail(MINCUT_ERR_INVALID, "input CSR is not symmetric");
   if (e & ERR_OVERFLOW) return fail(MINCUT_ERR_OVERFLOW, "a device capacity was exceeded");
-  if (e & ERR_INTERNAL) return fail(MINCUT_ERR_INTERNAL, "internal consistency check failed");
+  if (e & ERR_INTERNAL)
+    return fail(MINCUT_ERR_INTERNAL, "internal consistency check failed (check %d)",
+                g->hst->internal_code);
   return MINCUT_OK;
 }
 
@@ -1256,9 +1268,57 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   return MINCUT_OK;
 }
 
+// The graphs of a batch with at most `threshold` vertices (and at most
+// kBwMaxN), most entries first, for the one-warp-per-graph solver; its
+// scratch (at most ~2 GB of slots).
+int bw_prepare(mincut_graph* g, int threshold) {
+  threshold = std::min(threshold, kBwMaxN);
+  if (threshold == g->bw_threshold) return MINCUT_OK;
+  const int G = g->batch.G;
+  std::vector<int> ids;
+  int nmax = 0, mmax = 0;
+  for (int i = 0; i < G; ++i) {
+    const int ng = (int)(g->voff0_h[i + 1] - g->voff0_h[i]);
+    if (ng > threshold) continue;
+    ids.push_back(i);
+    nmax = std::max(nmax, ng);
+    mmax = std::max(mmax, g->batch_m[i]);
+  }
+  std::stable_sort(ids.begin(), ids.end(),
+                   [&](int a, int b) { return g->batch_m[a] > g->batch_m[b]; });
+  g->bw_threshold = threshold;
+  g->bw_count = (int)ids.size();
+  g->bw_nmax = nmax;
+  g->bw_mmax = std::max(mmax, 1);
+  if (ids.empty()) return MINCUT_OK;
+  if (!g->bw_list) {
+    if (!galloc(g, &g->bw_list, G) || !galloc(g, &g->bw_cursor, 1))
+      return fail(MINCUT_ERR_OOM, "batch warp list");
+  }
+  CK(cudaMemcpyAsync(g->bw_list, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     g->stream));
+  // slots come in blocks of batch_warp_block_warps() (the kernel's block)
+  const int bw = batch_warp_block_warps();
+  const long long per = batch_warp_slot_words(nmax, g->bw_mmax);
+  const long long cap = std::max<long long>(bw, (2ll << 30) / 4 / per / bw * bw);
+  const long long need = ((long long)g->bw_count + bw - 1) / bw * bw;
+  const int slots = (int)std::min<long long>({(long long)batch_warp_slots(g->sms), cap, need});
+  const long long words = per * slots;
+  if (words > g->bw_scratch_words) {
+    if (g->bw_scratch) dev_free(g, g->bw_scratch);
+    g->bw_scratch = nullptr;
+    g->bw_scratch_words = 0;
+    if (!galloc(g, &g->bw_scratch, words)) return fail(MINCUT_ERR_OOM, "batch warp scratch");
+    g->bw_scratch_words = words;
+  }
+  g->bw_slots = slots;
+  CK(cudaStreamSynchronize(g->stream));  // ids may go out of scope
+  return MINCUT_OK;
+}
+
 template <typename WT>
 int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_values,
-                     uint64_t* side_bitmap, mincut_stats* stats) {
+                     uint64_t* side_bitmap, mincut_stats* stats, int small_n) {
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = g->stream;
   BatchState& b = g->batch;
@@ -1275,12 +1335,19 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
   iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
   ++g->launches;
   CK(cudaMemsetAsync(g->side0, 0, (size_t)g->n0, s));
+  // the small graphs are the warp solver's: the round kernels treat them as done
+  {
+    const int rc0 = bw_prepare(g, small_n);
+    if (rc0) return rc0;
+  }
+  if (g->bw_count > 0)
+    CK(batch_warp_mark(g->bw_list, g->bw_count, b.done_g, g->st, s, &g->launches));
   mincut_stats stl{};
   stl.n_input = g->n0;
   stl.m_input = g->M0 / 2;
   const int table = op.pass_table > 0 ? std::min(op.pass_table, g->max_table) : g->max_table;
   const int max_rounds = op.max_rounds > 0 ? op.max_rounds : g->max_graph_n + 8;
-  for (int round = 0; round < max_rounds; ++round) {
+  for (int round = 0; g->bw_count < G && round < max_rounds; ++round) {
     const int n = g->n;
     const long long M = g->M;
     const int64_t* rp = g->crp();
@@ -1334,6 +1401,12 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
     std::swap(b.voff, b.voff_next);
     CK(batch_gid(b.voff, G, n2, b.gid, s, &g->launches));
     if (g->hst->batch_done >= G) break;
+  }
+  if (g->bw_count > 0) {
+    ProfScope ps(P_BATCH_WARP, g->bw_count, s);
+    CK(batch_warp_solve(g->bw_list, g->bw_count, g->bw_cursor, b.voff0, g->rp0, g->col0,
+                        (const int*)g->w0, g->bw_scratch, g->bw_slots, g->bw_nmax, g->bw_mmax,
+                        op.pr_mask, op.pr_budget, b.lam_g, g->side0, g->st, s, &g->launches));
   }
   int rc = sync_state(g);
   if (rc) return rc;
@@ -1564,8 +1637,25 @@ int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
     if (rc == MINCUT_ERR_INVALID) fail(rc, "an edge joins two different graphs of the batch");
     return bail(rc);
   }
+  {  // entries per graph of the canonical input
+    std::vector<int64_t> rp_h((size_t)n + 1);
+    CK(cudaMemcpyAsync(rp_h.data(), g->rp0, (size_t)(n + 1) * sizeof(int64_t),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    g->batch_m.resize(G);
+    for (int i = 0; i < G; ++i)
+      g->batch_m[i] = (int)(rp_h[vertex_offsets[i + 1]] - rp_h[vertex_offsets[i]]);
+  }
   CK(cudaStreamSynchronize(s));
   *out = g;
+  return MINCUT_OK;
+}
+
+int mincut_batch_info(const mincut_graph* g, int32_t* small_n, int64_t* small_graphs) {
+  g_last_error.clear();
+  if (!g || g->batch.G <= 0) return fail(MINCUT_ERR_INVALID, "not a batch");
+  if (small_n) *small_n = g->bw_threshold;
+  if (small_graphs) *small_graphs = g->bw_threshold < 0 ? 0 : g->bw_count;
   return MINCUT_OK;
 }
 
@@ -1579,10 +1669,41 @@ int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut
   if (op.pass_table != 0 && (op.pass_table < 256 || op.pass_table > 2048 ||
                              (op.pass_table & (op.pass_table - 1))))
     return fail(MINCUT_ERR_INVALID, "pass_table must be a power of two in [256, 2048]");
+  int small_n = op.batch_small_n > 0 ? std::min(op.batch_small_n, kBwMaxN)
+                                      : (op.batch_small_n < 0 ? 0 : g->bw_auto);
+  if (small_n < 0) {
+    // autotuning: time the whole batch solve at each candidate threshold
+    // (the largest first, which also sizes the scratch), keep the fastest
+    const int cands[] = {kBwMaxN, 1024, 256, 64, 0};
+    std::vector<int64_t> tmp((size_t)g->batch.G);
+    double best_ms = 1e300;
+    int best = 0, last_count = -1;
+    for (int k = -1; k < 5; ++k) {
+      const int t = cands[k < 0 ? 0 : k];
+      if (k >= 0) {
+        int cnt = 0;
+        for (int i = 0; i < g->batch.G; ++i)
+          cnt += (g->voff0_h[i + 1] - g->voff0_h[i]) <= t ? 1 : 0;
+        if (cnt == last_count) continue;  // same graph split as the last candidate
+        last_count = cnt;
+      }
+      const auto t0 = std::chrono::steady_clock::now();
+      const int r = batch_solve_impl<int32_t>(g, op, tmp.data(), nullptr, nullptr, t);
+      if (r) return r;
+      const double ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (k >= 0 && ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    g->bw_auto = best;
+    small_n = best;
+  }
   int rc;
   {
     ProfGuard pg(g, op.profile != 0);
-    rc = batch_solve_impl<int32_t>(g, op, cut_values, side_bitmap, stats);
+    rc = batch_solve_impl<int32_t>(g, op, cut_values, side_bitmap, stats, small_n);
   }
   g->cur = -1;
   g->n = g->n0;

@@ -53,6 +53,7 @@ struct DevState {
   unsigned long long dense_entries;   // contraction: entries of dense groups' rows
   int ndense;                         // contraction: dense groups asked for this round
   int m_rows;                         // contraction: entries of the row-wise contracted graph
+  int internal_code;                  // which internal check failed (0: none), for the message
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -55,6 +55,26 @@ cudaError_t batch_collapse(int n, const BatchState& b, int* parent, cudaStream_t
                            int* launches);
 cudaError_t batch_new_offsets(int G, const BatchState& b, const int* rank, const DevState* st,
                               cudaStream_t s, int* launches);
+// ---- batch_warp.cu: graphs of up to kBwMaxN vertices, one warp each (the
+// whole of Algorithm 2 per graph).  list: the graph ids, largest first.
+constexpr int kBwMaxN = 2048;
+long long batch_warp_slot_words(int nmax, int mmax);  // ints of one warp's scratch slot
+int batch_warp_slots(int sms);                        // warps resident at once
+int batch_warp_block_warps();                          // warps (slots) per block
+// done_g = 1 for the listed graphs, st->batch_done += nlist (the round
+// kernels then leave them alone).
+cudaError_t batch_warp_mark(const int* list, int nlist, int* done_g, DevState* st,
+                            cudaStream_t s, int* launches);
+// Solves the listed graphs of the packed input (voff0, rp0, col0, w0; int32
+// weights, total below 2^31) into lam_g and side0.  scratch: slots slots (a
+// multiple of batch_warp_block_warps()) of
+// batch_warp_slot_words(nmax, mmax) ints; every listed graph has at most nmax
+// vertices and mmax entries.  cursor: one int of work-queue state.
+cudaError_t batch_warp_solve(const int* list, int nlist, int* cursor, const int* voff0,
+                             const int64_t* rp0, const int* col0, const int* w0, int* scratch,
+                             int slots, int nmax, int mmax, uint32_t pr_mask, long long pr_budget,
+                             unsigned long long* lam_g, uint8_t* side0, DevState* st,
+                             cudaStream_t s, int* launches);
 cudaError_t batch_bitmap(const uint8_t* side0, int n0, const BatchState& b, u64* bitmap,
                          cudaStream_t s, int* launches);
 cudaError_t batch_check_edges(int n, const int64_t* rp, const int* col, const int* gid,
@@ -71,7 +91,7 @@ void set_last_error(const char* msg);
 // stream (category, units processed).  Resolved after the stream synchronises.
 enum ProfCat {
   P_DEGREE, P_LP_SWEEP, P_LP_BOUND, P_PR, P_CF_PASSES, P_CF_SEQ, P_UF, P_EMIT,
-  P_SORT_HIST, P_SORT_PASS, P_BUILD, P_TILES, P_WITNESS, P_OTHER, P_ROWS, P_NCAT
+  P_SORT_HIST, P_SORT_PASS, P_BUILD, P_TILES, P_WITNESS, P_OTHER, P_ROWS, P_BATCH_WARP, P_NCAT
 };
 const char* prof_name(int cat);
 struct Profiler;

@@ -24,7 +24,7 @@ thread_local Profiler* tl_prof = nullptr;
 static const char* kNames[P_NCAT] = {"degree", "lp_sweep", "lp_bound", "pr_marks",
                                      "capforest_passes", "capforest_seq", "union_find", "emit",
                                      "sort_hist", "sort_pass", "build_csr", "tile_rows",
-                                     "witness", "other", "contract_rows"};
+                                     "witness", "other", "contract_rows", "batch_warp"};
 
 const char* prof_name(int cat) { return (cat >= 0 && cat < P_NCAT) ? kNames[cat] : "?"; }
 

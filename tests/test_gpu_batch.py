@@ -46,6 +46,10 @@ def test_batch_random_small_graphs():
         expect.append(oracle.stoer_wagner(n, *c)[0])
     _check_batch(graphs, expect)
     _check_batch(graphs, expect, mc.default_options(deterministic=1))
+    # every graph in the shared round kernels; every graph on its own warp;
+    # both at once
+    for small in (-1, 2048, 20):
+        _check_batch(graphs, expect, mc.default_options(batch_small_n=small))
 
 
 def test_batch_closed_forms_and_disconnected():
@@ -57,7 +61,8 @@ def test_batch_closed_forms_and_disconnected():
     for c, n, lam in cases:
         cc = oracle.canonicalize(n, *c)
         graphs.append((n, cc[0], cc[1], cc[2]))
-    _check_batch(graphs, [lam for _, _, lam in cases])
+    for small in (0, -1, 2048, 10):
+        _check_batch(graphs, [lam for _, _, lam in cases], mc.default_options(batch_small_n=small))
 
 
 def test_batch_workload_subset_vs_noi():
@@ -66,8 +71,27 @@ def test_batch_workload_subset_vs_noi():
         s = synth.batch_graph(4, i)
         graphs.append((s.n, s.row_ptr, s.col, s.w.astype(np.int64)))
         expect.append(oracle.noi(s.n, s.row_ptr, s.col, s.w)[0])
-    st = _check_batch(graphs, expect)
+    _check_batch(graphs, expect)  # threshold chosen by timing
+    st = _check_batch(graphs, expect, mc.default_options(batch_small_n=-1))
     assert st["rounds"] >= 1
+    st = _check_batch(graphs, expect, mc.default_options(batch_small_n=2048))
+    assert st["rounds"] == 0  # every graph solved by its own warp
+    _check_batch(graphs, expect, mc.default_options(batch_small_n=300))
+
+
+def test_batch_warp_path_weighted_and_pr_variants():
+    """The one-warp-per-graph solver on weighted graphs up to its size
+    limit, with and without the PR tests, against Stoer-Wagner."""
+    rng = np.random.default_rng(17)
+    graphs, expect = [], []
+    for i in range(24):
+        n = int(rng.integers(100, 700)) if i % 4 else 2048
+        s = synth.er_connected(n, int(n * rng.uniform(2.0, 7.0)), 1, 100, 300 + i)
+        c = (s.row_ptr, s.col, s.w.astype(np.int64))
+        graphs.append((n, *c))
+        expect.append(oracle.stoer_wagner(n, *c)[0])
+    for mask in (0xF, 0x3, 0x0):
+        _check_batch(graphs, expect, mc.default_options(batch_small_n=2048, pr_mask=mask))
 
 
 def test_batch_rejects_cross_graph_edge_and_tiny_graph():
