@@ -95,9 +95,10 @@ typedef struct mincut_options {
                                 Algorithm 2; 0 = auto (one per SM, device memory permitting) */
     int32_t batch_small_n;   /* mincut_batch_solve: graphs of at most this many vertices (and at
                                 most 2048) are solved one per warp, each running all its rounds
-                                alone; the others share the batch's round kernels.  0 = auto
-                                (chosen by timing candidate thresholds on the first solve of the
-                                batch, then kept); < 0 = every graph in the round kernels */
+                                alone (one CAPFOREST pass per round; of pr_mask only PR1/PR2);
+                                the others share the batch's round kernels.  0 = auto (chosen
+                                by timing candidate thresholds on the first solve of the batch,
+                                then kept); < 0 = every graph in the round kernels */
 } mincut_options;
 
 /* Statistics of a solve (all optional to read). */

@@ -2,11 +2,14 @@
 //
 // A warp takes graphs from a work queue (largest first) and runs the whole
 // of Algorithm 2 on each, its state in the warp's own scratch slot: per
-// round the degree bound (Sec. 2.1), the PR1-PR4 tests, one CAPFOREST pass
+// round the degree bound (Sec. 2.1), the PR1 / PR2 tests, one CAPFOREST pass
 // from vertex 0 (Algorithm 1 with one process: a maximum-adjacency order
 // with keys min(r(y), lambda-hat); marks where r(y) first reaches
 // lambda-hat; alpha lowers the bound with the visited prefix as witness),
-// the union-find of the marks and the contraction.  The contraction sums
+// the union-find of the marks and the contraction.  Of the PR tests only the
+// per-edge PR1 / PR2 run: on one warp the PR3 / PR4 intersections measured
+// several times the rest of a graph's solve, and the round's full pass marks
+// anyway.  The contraction sums
 // each contracted vertex's member rows into a dense accumulator of the new
 // vertex count (the per-vertex dense accumulation of Sec. 4, parallel
 // session (3)) and writes the row in label order, so the result is the same
@@ -84,43 +87,12 @@ __device__ BwSlot bw_slot(int* base, long long slot_words, int slot, int nmax, i
   return s;
 }
 
-// PR3 / PR4 for edge {u, v} (c = c(u, v), du = c(u), dv = c(v)): the
-// shorter row is walked and each neighbour binary-searched in the longer.
-__device__ bool bw_pr34(const int* __restrict__ rp, const int* __restrict__ col,
-                        const int* __restrict__ w, int u, int v, int c, int du, int dv,
-                        long long lam, uint32_t mask) {
-  const int bu = rp[u], eu = rp[u + 1], bv = rp[v], ev = rp[v + 1];
-  const bool a_is_u = eu - bu <= ev - bv;
-  const int ab = a_is_u ? bu : bv, ae = a_is_u ? eu : ev;
-  const int bb = a_is_u ? bv : bu, be = a_is_u ? ev : eu;
-  const int other = a_is_u ? v : u;
-  long long sum = c;
-  for (int i = ab; i < ae; ++i) {
-    const int x = col[i];
-    if (x == other) continue;
-    int lo = bb, hi = be;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (col[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    if (lo >= be || col[lo] != x) continue;
-    const int ca = w[i], cb = w[lo];  // c(a, x), c(b, x)
-    const int cux = a_is_u ? ca : cb, cvx = a_is_u ? cb : ca;
-    if ((mask & 4u) && (long long)du < 2ll * (c + cux) && (long long)dv < 2ll * (c + cvx))
-      return true;
-    sum += min(cux, cvx);
-    if ((mask & 8u) && sum >= lam) return true;
-  }
-  return false;
-}
-
 __global__ void __launch_bounds__(kBwWarps * 32)
     batch_warp_kernel(const int* __restrict__ list, int nlist, int* cursor,
                       const int* __restrict__ voff0, const int64_t* __restrict__ rp0,
                       const int* __restrict__ col0, const int* __restrict__ w0, int* scratch,
                       long long slot_words, int nmax, int mmax, uint32_t pr_mask,
-                      long long pr_budget, unsigned long long* lam_g, uint8_t* side0,
-                      DevState* st) {
+                      unsigned long long* lam_g, uint8_t* side0, DevState* st) {
   __shared__ int s_key[kBwWarps][kBwMaxN];  // r values in a pass, then the accumulator
   __shared__ unsigned s_l1[kBwWarps][kBwMaxN / 32];
   __shared__ unsigned s_l2[kBwWarps][kBwMaxN / 1024];
@@ -190,11 +162,8 @@ __global__ void __launch_bounds__(kBwWarps * 32)
             const int v = col[e];
             if (v <= u) continue;
             const int c = w[e], dv = S.deg[v];
-            bool f = ((pr_mask & 1u) && c >= lam) ||
-                     ((pr_mask & 2u) && ((long long)du < 2ll * c || (long long)dv < 2ll * c));
-            if (!f && (pr_mask & 12u) &&
-                (pr_budget < 0 || min(eu - bu, rp[v + 1] - rp[v]) <= pr_budget))
-              f = bw_pr34(rp, col, w, u, v, c, du, dv, lam, pr_mask);
+            const bool f = ((pr_mask & 1u) && c >= lam) ||
+                           ((pr_mask & 2u) && ((long long)du < 2ll * c || (long long)dv < 2ll * c));
             if (f && !uf_union(S.parent, u, v)) fail = fail ? fail : 2;
           }
         }
@@ -427,7 +396,7 @@ cudaError_t batch_warp_mark(const int* list, int nlist, int* done_g, DevState* s
 
 cudaError_t batch_warp_solve(const int* list, int nlist, int* cursor, const int* voff0,
                              const int64_t* rp0, const int* col0, const int* w0, int* scratch,
-                             int slots, int nmax, int mmax, uint32_t pr_mask, long long pr_budget,
+                             int slots, int nmax, int mmax, uint32_t pr_mask,
                              unsigned long long* lam_g, uint8_t* side0, DevState* st,
                              cudaStream_t s, int* launches) {
   if (nlist <= 0) return cudaSuccess;
@@ -437,7 +406,7 @@ cudaError_t batch_warp_solve(const int* list, int nlist, int* cursor, const int*
   const int blocks = slots / kBwWarps;
   batch_warp_kernel<<<blocks, kBwWarps * 32, 0, s>>>(
       list, nlist, cursor, voff0, rp0, col0, w0, scratch, batch_warp_slot_words(nmax, mmax), nmax,
-      mmax, pr_mask, pr_budget, lam_g, side0, st);
+      mmax, pr_mask, lam_g, side0, st);
   ++*launches;
   return cudaGetLastError();
 }

@@ -1404,9 +1404,11 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
   }
   if (g->bw_count > 0) {
     ProfScope ps(P_BATCH_WARP, g->bw_count, s);
+    // PR1 / PR2 only: on one warp the PR3 / PR4 intersections cost several
+    // times the rest of a graph's solve (the pass of each round marks anyway)
     CK(batch_warp_solve(g->bw_list, g->bw_count, g->bw_cursor, b.voff0, g->rp0, g->col0,
                         (const int*)g->w0, g->bw_scratch, g->bw_slots, g->bw_nmax, g->bw_mmax,
-                        op.pr_mask, op.pr_budget, b.lam_g, g->side0, g->st, s, &g->launches));
+                        op.pr_mask & 3u, b.lam_g, g->side0, g->st, s, &g->launches));
   }
   int rc = sync_state(g);
   if (rc) return rc;

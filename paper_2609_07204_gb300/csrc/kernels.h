@@ -56,7 +56,8 @@ cudaError_t batch_collapse(int n, const BatchState& b, int* parent, cudaStream_t
 cudaError_t batch_new_offsets(int G, const BatchState& b, const int* rank, const DevState* st,
                               cudaStream_t s, int* launches);
 // ---- batch_warp.cu: graphs of up to kBwMaxN vertices, one warp each (the
-// whole of Algorithm 2 per graph).  list: the graph ids, largest first.
+// whole of Algorithm 2 per graph, PR1 / PR2 of pr_mask).  list: the graph
+// ids, largest first.
 constexpr int kBwMaxN = 2048;
 long long batch_warp_slot_words(int nmax, int mmax);  // ints of one warp's scratch slot
 int batch_warp_slots(int sms);                        // warps resident at once
@@ -72,7 +73,7 @@ cudaError_t batch_warp_mark(const int* list, int nlist, int* done_g, DevState* s
 // vertices and mmax entries.  cursor: one int of work-queue state.
 cudaError_t batch_warp_solve(const int* list, int nlist, int* cursor, const int* voff0,
                              const int64_t* rp0, const int* col0, const int* w0, int* scratch,
-                             int slots, int nmax, int mmax, uint32_t pr_mask, long long pr_budget,
+                             int slots, int nmax, int mmax, uint32_t pr_mask,
                              unsigned long long* lam_g, uint8_t* side0, DevState* st,
                              cudaStream_t s, int* launches);
 cudaError_t batch_bitmap(const uint8_t* side0, int n0, const BatchState& b, u64* bitmap,
