@@ -14,6 +14,7 @@
 // mix.
 #include <algorithm>
 #include <chrono>
+#include <atomic>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -64,6 +65,9 @@ struct mincut_server {
   bool stopping = false;
   std::vector<std::thread> workers;
   mincut_server_stats st{};
+  // warp-solver threshold of packed solves when solve.batch_small_n = 0: timed
+  // on the first packed solve, then reused (0: not yet, -1: none)
+  std::atomic<int> bw_small_n{0};
 };
 
 namespace {
@@ -93,7 +97,8 @@ void solve_alone(const mincut_server_options& o, cudaStream_t s, const ReqPtr& r
   mincut_graph_destroy(g);
 }
 
-void solve_packed(const mincut_server_options& o, cudaStream_t s, std::vector<ReqPtr>& reqs) {
+void solve_packed(mincut_server* S, const mincut_server_options& o, cudaStream_t s,
+                  std::vector<ReqPtr>& reqs) {
   const size_t G = reqs.size();
   std::vector<int64_t> voff(G + 1, 0);
   int64_t entries = 0;
@@ -122,8 +127,15 @@ void solve_packed(const mincut_server_options& o, cudaStream_t s, std::vector<Re
   std::vector<uint64_t> bm;
   if (rc == MINCUT_OK) {
     if (o.want_bitmap) bm.assign((size_t)((voff[G] + 63) / 64), 0);
-    rc = mincut_batch_solve(g, &o.solve, vals.data(), o.want_bitmap ? bm.data() : nullptr,
-                            nullptr);
+    mincut_options so = o.solve;
+    const int tuned = S->bw_small_n.load();
+    if (so.batch_small_n == 0 && tuned != 0) so.batch_small_n = tuned;
+    rc = mincut_batch_solve(g, &so, vals.data(), o.want_bitmap ? bm.data() : nullptr, nullptr);
+    if (rc == MINCUT_OK && so.batch_small_n == 0) {
+      int32_t t = 0;
+      int64_t k = 0;
+      if (mincut_batch_info(g, &t, &k) == MINCUT_OK) S->bw_small_n.store(t > 0 ? t : -1);
+    }
     mincut_graph_destroy(g);
   }
   if (rc != MINCUT_OK) {  // isolate the failing request(s)
@@ -197,7 +209,7 @@ void worker_loop(mincut_server* S, int wid) {
     const double t = now_ms();
     for (auto& r : take) r->t_start = t;
     if (take.size() == 1) solve_alone(o, s, take[0]);
-    else solve_packed(o, s, take);
+    else solve_packed(S, o, s, take);
     finish(S, take);
   }
   cudaStreamDestroy(s);
