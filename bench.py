@@ -546,7 +546,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and serving measurements")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched measurement, printed as one JSON object "
+                         "(a short command to profile the batched kernels)")
     args = ap.parse_args()
+    if args.batched_only:
+        import torch
+
+        import paper_2609_07204_gb300 as mc
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        mc.load_library()
+        print(json.dumps({"batched": measure_batched(mc)}), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "gpu":
