@@ -32,6 +32,9 @@ namespace mc {
 namespace {
 
 constexpr int kBwWarps = 4;  // warps per block, each with its own graphs
+constexpr int kBwWarpSmemWords =
+    kBwMaxN + (kBwMaxN + 1) + kBwMaxN + kBwMaxN / 32 + kBwMaxN / 1024 + 32 + 1;
+constexpr size_t kBwSmemBytes = (size_t)kBwWarps * kBwWarpSmemWords * sizeof(int);
 
 __device__ __forceinline__ unsigned long long bw_warp_min(unsigned long long v) {
 #pragma unroll
@@ -51,7 +54,6 @@ struct BwSlot {
   int* rp[2];
   int* col[2];
   int* w[2];
-  int* deg;
   int* parent;
   int* lab;
   int* pos;
@@ -71,8 +73,6 @@ __device__ BwSlot bw_slot(int* base, long long slot_words, int slot, int nmax, i
     s.w[b] = p;
     p += mmax;
   }
-  s.deg = p;
-  p += nmax;
   s.parent = p;
   p += nmax;
   s.lab = p;
@@ -93,17 +93,19 @@ __global__ void __launch_bounds__(kBwWarps * 32)
                       const int* __restrict__ col0, const int* __restrict__ w0, int* scratch,
                       long long slot_words, int nmax, int mmax, uint32_t pr_mask,
                       unsigned long long* lam_g, uint8_t* side0, DevState* st) {
-  __shared__ int s_key[kBwWarps][kBwMaxN];  // r values in a pass, then the accumulator
-  __shared__ unsigned s_l1[kBwWarps][kBwMaxN / 32];
-  __shared__ unsigned s_l2[kBwWarps][kBwMaxN / 1024];
-  __shared__ int s_tl[kBwWarps][32];
-  __shared__ int s_tc[kBwWarps];
+  // per warp, in dynamic shared memory (kBwWarpSmemWords ints each): the
+  // keys (r values in a pass, then the accumulator), the current graph's row
+  // offsets and degrees, the two tree levels, the row label list and count
+  extern __shared__ int bw_smem[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const BwSlot S = bw_slot(scratch, slot_words, blockIdx.x * kBwWarps + wp, nmax, mmax);
-  int* key = s_key[wp];
-  unsigned* l1 = s_l1[wp];
-  unsigned* l2 = s_l2[wp];
-  int* tl = s_tl[wp];
+  int* key = bw_smem + (long long)wp * kBwWarpSmemWords;
+  int* srp = key + kBwMaxN;       // kBwMaxN + 1
+  int* sdeg = srp + kBwMaxN + 1;  // kBwMaxN
+  unsigned* l1 = reinterpret_cast<unsigned*>(sdeg + kBwMaxN);  // kBwMaxN / 32
+  unsigned* l2 = l1 + kBwMaxN / 32;                            // kBwMaxN / 1024
+  int* tl = reinterpret_cast<int*>(l2 + kBwMaxN / 1024);       // 32
+  int* tcount = tl + 32;                                       // 1
   int fail = 0;  // the first failed check: 1 rounds, 2 union-find, 3 / 4 tree descent
   for (;;) {
     int item = 0;
@@ -132,7 +134,10 @@ __global__ void __launch_bounds__(kBwWarps * 32)
         fail = fail ? fail : 1;
         break;
       }
-      const int* rp = S.rp[cur];
+      // the current graph's row offsets into shared memory
+      for (int i = lane; i <= n; i += 32) srp[i] = S.rp[cur][i];
+      __syncwarp();
+      const int* rp = srp;
       const int* col = S.col[cur];
       const int* w = S.w[cur];
       // ---- degree bound
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
       for (int v = lane; v < n; v += 32) {
         int d = 0;
         for (int e = rp[v]; e < rp[v + 1]; ++e) d += w[e];
-        S.deg[v] = d;
+        sdeg[v] = d;
         const unsigned long long k = ((unsigned long long)(unsigned)d << 32) | (unsigned)v;
         if (k < best) best = k;
       }
@@ -157,11 +162,11 @@ __global__ void __launch_bounds__(kBwWarps * 32)
       __syncwarp();
       if (pr_mask) {
         for (int u = lane; u < n; u += 32) {
-          const int bu = rp[u], eu = rp[u + 1], du = S.deg[u];
+          const int bu = rp[u], eu = rp[u + 1], du = sdeg[u];
           for (int e = bu; e < eu; ++e) {
             const int v = col[e];
             if (v <= u) continue;
-            const int c = w[e], dv = S.deg[v];
+            const int c = w[e], dv = sdeg[v];
             const bool f = ((pr_mask & 1u) && c >= lam) ||
                            ((pr_mask & 2u) && ((long long)du < 2ll * c || (long long)dv < 2ll * c));
             if (f && !uf_union(S.parent, u, v)) fail = fail ? fail : 2;
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
           rx = __shfl_sync(FULL, ry, wl);
         }
         const int ns = it + 1;
-        alpha += S.deg[x] - 2 * rx;
+        alpha += sdeg[x] - 2 * rx;
         if (ns < n && alpha < lam_p) {
           lam_p = alpha;
           best_len = ns;
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
       int* col2 = S.col[nb];
       int* w2 = S.w[nb];
       for (int i = lane; i < n2; i += 32) key[i] = 0;
-      if (lane == 0) s_tc[wp] = 0;
+      if (lane == 0) *tcount = 0;
       __syncwarp();
       int out = 0;
       for (int g = 0; g < n2; ++g) {
@@ -303,14 +308,14 @@ __global__ void __launch_bounds__(kBwWarps * 32)
             if (e < re) {
               const int lv = S.lab[col[e]];
               if (lv != g && atomicAdd(&key[lv], w[e]) == 0) {  // weights are positive
-                const int t = atomicAdd(&s_tc[wp], 1);
+                const int t = atomicAdd(&*tcount, 1);
                 if (t < 32) tl[t] = lv;
               }
             }
           }
         }
         __syncwarp();
-        const int tc = s_tc[wp];
+        const int tc = *tcount;
         if (tc <= 32) {
           // the few labels of the row, ranked among themselves
           const int my = lane < tc ? tl[lane] : INT_MAX;
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
         }
         if (lane == 0) {
           rp2[g] = out;
-          s_tc[wp] = 0;
+          *tcount = 0;
         }
         out += tc;
         __syncwarp();
@@ -370,16 +375,24 @@ __global__ void batch_mark_kernel(const int* __restrict__ list, int nlist, int* 
 }  // namespace
 
 long long batch_warp_slot_words(int nmax, int mmax) {
-  // two buffers of (rp, col, w), then deg, parent, lab, pos, cnt (+1), mem, map
-  return 2ll * ((long long)nmax + 1 + 2ll * mmax) + 7ll * nmax + 1;
+  // two buffers of (rp, col, w), then parent, lab, pos, cnt (+1), mem, map
+  return 2ll * ((long long)nmax + 1 + 2ll * mmax) + 6ll * nmax + 1;
 }
 
 int batch_warp_block_warps() { return kBwWarps; }
 
+bool bw_set_smem() {
+  static const bool ok = cudaFuncSetAttribute(batch_warp_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kBwSmemBytes) == cudaSuccess;
+  return ok;
+}
+
 int batch_warp_slots(int sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_warp_kernel, kBwWarps * 32, 0) !=
-          cudaSuccess ||
+  if (!bw_set_smem() ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_warp_kernel, kBwWarps * 32,
+                                                    kBwSmemBytes) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return std::max(1, sms) * per_sm * kBwWarps;
@@ -404,7 +417,8 @@ cudaError_t batch_warp_solve(const int* list, int nlist, int* cursor, const int*
   cudaMemsetAsync(cursor, 0, sizeof(int), s);
   if (slots < kBwWarps || slots % kBwWarps) return cudaErrorInvalidValue;
   const int blocks = slots / kBwWarps;
-  batch_warp_kernel<<<blocks, kBwWarps * 32, 0, s>>>(
+  if (!bw_set_smem()) return cudaErrorInvalidValue;
+  batch_warp_kernel<<<blocks, kBwWarps * 32, kBwSmemBytes, s>>>(
       list, nlist, cursor, voff0, rp0, col0, w0, scratch, batch_warp_slot_words(nmax, mmax), nmax,
       mmax, pr_mask, lam_g, side0, st);
   ++*launches;
