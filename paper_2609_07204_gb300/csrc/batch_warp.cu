@@ -31,9 +31,9 @@ namespace mc {
 
 namespace {
 
-constexpr int kBwWarps = 4;  // warps per block, each with its own graphs
-constexpr int kBwWarpSmemWords =
-    kBwMaxN + (kBwMaxN + 1) + kBwMaxN + kBwMaxN / 32 + kBwMaxN / 1024 + 32 + 1;
+constexpr int kBwWarps = 1;  // warps per block (each warp has its own graphs)
+constexpr int kBwWarpSmemWords = kBwMaxN + (kBwMaxN + 1) + kBwMaxN + (kBwMaxN + 1) + kBwMaxN +
+                                 kBwMaxN / 32 + kBwMaxN / 1024 + 32 + 1;
 constexpr size_t kBwSmemBytes = (size_t)kBwWarps * kBwWarpSmemWords * sizeof(int);
 
 __device__ __forceinline__ unsigned long long bw_warp_min(unsigned long long v) {
@@ -55,10 +55,7 @@ struct BwSlot {
   int* col[2];
   int* w[2];
   int* parent;
-  int* lab;
   int* pos;
-  int* cnt;
-  int* mem;
   int* map;
 };
 
@@ -75,13 +72,7 @@ __device__ BwSlot bw_slot(int* base, long long slot_words, int slot, int nmax, i
   }
   s.parent = p;
   p += nmax;
-  s.lab = p;
-  p += nmax;
   s.pos = p;
-  p += nmax;
-  s.cnt = p;
-  p += nmax + 1;
-  s.mem = p;
   p += nmax;
   s.map = p;
   return s;
@@ -95,14 +86,18 @@ __global__ void __launch_bounds__(kBwWarps * 32)
                       unsigned long long* lam_g, uint8_t* side0, DevState* st) {
   // per warp, in dynamic shared memory (kBwWarpSmemWords ints each): the
   // keys (r values in a pass, then the accumulator), the current graph's row
-  // offsets and degrees, the two tree levels, the row label list and count
+  // offsets, its degrees (then the labels), the group counts and members,
+  // the two tree levels, the row label list and count
   extern __shared__ int bw_smem[];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const BwSlot S = bw_slot(scratch, slot_words, blockIdx.x * kBwWarps + wp, nmax, mmax);
   int* key = bw_smem + (long long)wp * kBwWarpSmemWords;
   int* srp = key + kBwMaxN;       // kBwMaxN + 1
-  int* sdeg = srp + kBwMaxN + 1;  // kBwMaxN
-  unsigned* l1 = reinterpret_cast<unsigned*>(sdeg + kBwMaxN);  // kBwMaxN / 32
+  int* sdeg = srp + kBwMaxN + 1;  // kBwMaxN: degrees; labels once the pass is done
+  int* lab = sdeg;
+  int* scnt = sdeg + kBwMaxN;     // kBwMaxN + 1
+  int* smem_members = scnt + kBwMaxN + 1;  // kBwMaxN
+  unsigned* l1 = reinterpret_cast<unsigned*>(smem_members + kBwMaxN);  // kBwMaxN / 32
   unsigned* l2 = l1 + kBwMaxN / 32;                            // kBwMaxN / 1024
   int* tl = reinterpret_cast<int*>(l2 + kBwMaxN / 1024);       // 32
   int* tcount = tl + 32;                                       // 1
@@ -258,36 +253,36 @@ __global__ void __launch_bounds__(kBwWarps * 32)
         const int v = base + lane;
         const bool root = v < n && uf_find(S.parent, v) == v;
         const unsigned b = __ballot_sync(FULL, root);
-        if (root) S.lab[v] = n2 + __popc(b & lanemask_lt());
+        if (root) lab[v] = n2 + __popc(b & lanemask_lt());
         n2 += __popc(b);
       }
       __syncwarp();
       for (int v = lane; v < n; v += 32) {
         const int r = uf_find(S.parent, v);
-        if (r != v) S.lab[v] = S.lab[r];
+        if (r != v) lab[v] = lab[r];
       }
       __syncwarp();
       if (n2 == n) continue;  // no marks (the pass lowered the bound): again, lower bound
       // ---- members of each group (counting sort by label)
-      for (int g = lane; g <= n2; g += 32) S.cnt[g] = 0;
+      for (int g = lane; g <= n2; g += 32) scnt[g] = 0;
       __syncwarp();
-      for (int v = lane; v < n; v += 32) atomicAdd(&S.cnt[S.lab[v]], 1);
+      for (int v = lane; v < n; v += 32) atomicAdd(&scnt[lab[v]], 1);
       __syncwarp();
       int run = 0;  // exclusive scan of the counts
       for (int base = 0; base < n2; base += 32) {
         const int g = base + lane;
-        const int c = g < n2 ? S.cnt[g] : 0;
+        const int c = g < n2 ? scnt[g] : 0;
         int incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const int t = __shfl_up_sync(FULL, incl, o);
           if (lane >= o) incl += t;
         }
-        if (g < n2) S.cnt[g] = run + incl - c;
+        if (g < n2) scnt[g] = run + incl - c;
         run += __shfl_sync(FULL, incl, 31);
       }
       __syncwarp();
-      for (int v = lane; v < n; v += 32) S.mem[atomicAdd(&S.cnt[S.lab[v]], 1)] = v;
+      for (int v = lane; v < n; v += 32) smem_members[atomicAdd(&scnt[lab[v]], 1)] = v;
       __syncwarp();  // cnt[g] is now the end of group g's members
       // ---- contraction into the other buffer
       const int nb = cur ^ 1;
@@ -299,14 +294,14 @@ __global__ void __launch_bounds__(kBwWarps * 32)
       __syncwarp();
       int out = 0;
       for (int g = 0; g < n2; ++g) {
-        const int mb = g == 0 ? 0 : S.cnt[g - 1], me = S.cnt[g];
+        const int mb = g == 0 ? 0 : scnt[g - 1], me = scnt[g];
         for (int k = mb; k < me; ++k) {
-          const int m = S.mem[k];
+          const int m = smem_members[k];
           const int rb = rp[m], re = rp[m + 1];
           for (int base = rb; base < re; base += 32) {
             const int e = base + lane;
             if (e < re) {
-              const int lv = S.lab[col[e]];
+              const int lv = lab[col[e]];
               if (lv != g && atomicAdd(&key[lv], w[e]) == 0) {  // weights are positive
                 const int t = atomicAdd(&*tcount, 1);
                 if (t < 32) tl[t] = lv;
@@ -350,7 +345,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
         __syncwarp();
       }
       if (lane == 0) rp2[n2] = out;
-      for (int i = lane; i < n0; i += 32) S.map[i] = S.lab[S.map[i]];
+      for (int i = lane; i < n0; i += 32) S.map[i] = lab[S.map[i]];
       __syncwarp();
       cur = nb;
       n = n2;
@@ -375,8 +370,8 @@ __global__ void batch_mark_kernel(const int* __restrict__ list, int nlist, int* 
 }  // namespace
 
 long long batch_warp_slot_words(int nmax, int mmax) {
-  // two buffers of (rp, col, w), then parent, lab, pos, cnt (+1), mem, map
-  return 2ll * ((long long)nmax + 1 + 2ll * mmax) + 6ll * nmax + 1;
+  // two buffers of (rp, col, w), then parent, pos, map
+  return 2ll * ((long long)nmax + 1 + 2ll * mmax) + 3ll * nmax;
 }
 
 int batch_warp_block_warps() { return kBwWarps; }
