@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kBwWarps = 1;  // warps per block (each warp has its own graphs)
 constexpr int kBwWarpSmemWords = kBwMaxN + (kBwMaxN + 1) + kBwMaxN + (kBwMaxN + 1) + kBwMaxN +
-                                 kBwMaxN / 32 + kBwMaxN / 1024 + 32 + 1;
+                                 kBwMaxN + kBwMaxN / 32 + kBwMaxN / 1024 + 32 + 1;
 constexpr size_t kBwSmemBytes = (size_t)kBwWarps * kBwWarpSmemWords * sizeof(int);
 
 __device__ __forceinline__ unsigned long long bw_warp_min(unsigned long long v) {
@@ -54,7 +54,6 @@ struct BwSlot {
   int* rp[2];
   int* col[2];
   int* w[2];
-  int* parent;
   int* pos;
   int* map;
 };
@@ -70,8 +69,6 @@ __device__ BwSlot bw_slot(int* base, long long slot_words, int slot, int nmax, i
     s.w[b] = p;
     p += mmax;
   }
-  s.parent = p;
-  p += nmax;
   s.pos = p;
   p += nmax;
   s.map = p;
@@ -97,7 +94,8 @@ __global__ void __launch_bounds__(kBwWarps * 32)
   int* lab = sdeg;
   int* scnt = sdeg + kBwMaxN;     // kBwMaxN + 1
   int* smem_members = scnt + kBwMaxN + 1;  // kBwMaxN
-  unsigned* l1 = reinterpret_cast<unsigned*>(smem_members + kBwMaxN);  // kBwMaxN / 32
+  int* parent = smem_members + kBwMaxN;    // kBwMaxN: the round's union-find
+  unsigned* l1 = reinterpret_cast<unsigned*>(parent + kBwMaxN);  // kBwMaxN / 32
   unsigned* l2 = l1 + kBwMaxN / 32;                            // kBwMaxN / 1024
   int* tl = reinterpret_cast<int*>(l2 + kBwMaxN / 1024);       // 32
   int* tcount = tl + 32;                                       // 1
@@ -153,7 +151,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
       }
       if (n <= 2 || lam == 0) break;
       // ---- PR1-PR4, one lane per row, each edge once (u < v)
-      for (int v = lane; v < n; v += 32) S.parent[v] = v;
+      for (int v = lane; v < n; v += 32) parent[v] = v;
       __syncwarp();
       if (pr_mask) {
         for (int u = lane; u < n; u += 32) {
@@ -164,7 +162,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
             const int c = w[e], dv = sdeg[v];
             const bool f = ((pr_mask & 1u) && c >= lam) ||
                            ((pr_mask & 2u) && ((long long)du < 2ll * c || (long long)dv < 2ll * c));
-            if (f && !uf_union(S.parent, u, v)) fail = fail ? fail : 2;
+            if (f && !uf_union(parent, u, v)) fail = fail ? fail : 2;
           }
         }
       }
@@ -232,7 +230,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
             if (r0 >= 0) {  // rows hold distinct neighbours: one lane per y
               const int r1 = r0 + w[e];
               key[y] = r1;
-              if (r0 < lam_p && lam_p <= r1 && !uf_union(S.parent, x, y)) fail = fail ? fail : 2;
+              if (r0 < lam_p && lam_p <= r1 && !uf_union(parent, x, y)) fail = fail ? fail : 2;
               const unsigned k = bw_key(r1, lam_p);
               atomicMax(&l1[y >> 5], k);
               atomicMax(&l2[y >> 10], k);
@@ -251,14 +249,14 @@ __global__ void __launch_bounds__(kBwWarps * 32)
       int n2 = 0;
       for (int base = 0; base < n; base += 32) {
         const int v = base + lane;
-        const bool root = v < n && uf_find(S.parent, v) == v;
+        const bool root = v < n && uf_find(parent, v) == v;
         const unsigned b = __ballot_sync(FULL, root);
         if (root) lab[v] = n2 + __popc(b & lanemask_lt());
         n2 += __popc(b);
       }
       __syncwarp();
       for (int v = lane; v < n; v += 32) {
-        const int r = uf_find(S.parent, v);
+        const int r = uf_find(parent, v);
         if (r != v) lab[v] = lab[r];
       }
       __syncwarp();
@@ -370,8 +368,8 @@ __global__ void batch_mark_kernel(const int* __restrict__ list, int nlist, int* 
 }  // namespace
 
 long long batch_warp_slot_words(int nmax, int mmax) {
-  // two buffers of (rp, col, w), then parent, pos, map
-  return 2ll * ((long long)nmax + 1 + 2ll * mmax) + 3ll * nmax;
+  // two buffers of (rp, col, w), then pos, map
+  return 2ll * ((long long)nmax + 1 + 2ll * mmax) + 2ll * nmax;
 }
 
 int batch_warp_block_warps() { return kBwWarps; }
