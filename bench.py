@@ -16,9 +16,13 @@ until lambda is proven) on the graph already resident in HBM.
   roofline of the dominant kernel from the library's live CUDA-event profile
   cpu_baseline = the CPU oracle (sequential NOI) on the same workload
   batched = 4096 small graphs in one packed batch solve vs one at a time
+            (the split between the one-warp-per-graph solver and the shared
+            round kernels as the autotuner chose it, and both paths alone)
   serving = open-loop Poisson request stream through the continuous-batching
             server at 0.5x and 2x the sequential throughput: solves/s,
             p50/p99 latency
+  small_config = connected G(2000, 16000) single solve against the CPU
+            oracle's Stoer-Wagner and NOI
 
 --impl reference times the CPU oracle as the reference arm.  Multi-GPU runs
 (torchrun) are independent replicas: the solve does not shard.
@@ -268,6 +272,40 @@ def measure_variants(mc, g, val, reps: int = 3):
                      "lambda_source": st["lambda_source"]}
     G.destroy()
     return out
+
+
+def measure_small_config(mc, reps: int = 5):
+    """The small single-graph configuration: connected G(n=2000, m=16000),
+    weights in [1, 10], seed 1.  GPU solve (host wall time, median of reps
+    after a warm-up, graph resident) against the CPU oracle's Stoer-Wagner
+    and sequential NOI on one host core."""
+    import torch
+
+    import oracle
+    import synth
+    g = synth.workload_er2000()
+    G = mc.mincut_graph_from_csr(g.n, g.row_ptr, g.col, g.w)
+    mc.mincut_solve(G, bitmap=False)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v, _, st = mc.mincut_solve(G, bitmap=False)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    G.destroy()
+    c = (g.row_ptr, g.col, g.w.astype(np.int64))
+    t0 = time.perf_counter()
+    sw = oracle.stoer_wagner(g.n, *c)[0]
+    t_sw = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    noi = oracle.noi(g.n, *c)[0]
+    t_noi = time.perf_counter() - t0
+    assert v == sw == noi, (v, sw, noi)
+    t = statistics.median(ts)
+    return {"workload": workload_desc(g), "lambda": int(v), "ms": t * 1e3,
+            "edges_per_s": g.m / t, "rounds": st["rounds"],
+            "cpu_oracle": {"stoer_wagner_ms": t_sw * 1e3, "noi_ms": t_noi * 1e3, "cores": 1}}
 
 
 def measure_adversarial(mc, reps: int = 2):
@@ -527,6 +565,7 @@ def run_gpu(args, rank, world):
         line["batched"] = measure_batched(mc)
         line["serving"] = measure_serving(mc)
         line["variants"] = measure_variants(mc, g, val)
+        line["small_config"] = measure_small_config(mc)
         if not args.no_cpu_baseline:
             line["adversarial"] = measure_adversarial(mc)
     if not args.no_cpu_baseline:
