@@ -213,10 +213,11 @@ int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
                           uint32_t flags, void* cuda_stream, const mincut_allocator* alloc,
                           mincut_graph** out);
 
-/* Exact minimum cut of every graph of a batch (Algorithm 2 per graph; one
- * set of round kernels serves all graphs, each graph with its own bound,
- * stop test and witness; label propagation is not used).  cut_values: host
- * int64[num_graphs].  side_bitmap (nullable, host or device, ceil(n/64)
+/* Exact minimum cut of every graph of a batch (Algorithm 2 per graph; label
+ * propagation is not used).  Graphs of at most opts->batch_small_n vertices
+ * are solved one per warp in one persistent launch (a work queue, largest
+ * first); the others share one set of round kernels, each graph with its own
+ * bound, stop test and witness.  cut_values: host int64[num_graphs].  side_bitmap (nullable, host or device, ceil(n/64)
  * words): bit v = 1 iff vertex v is on the side of its graph's minimum cut
  * that does not hold the graph's first vertex. */
 int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_values,
