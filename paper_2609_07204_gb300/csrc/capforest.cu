@@ -480,28 +480,33 @@ __device__ __forceinline__ void seq_layout(const SeqTree& tl, int smem_from, int
   *r_out = r_in_smem ? reinterpret_cast<WT*>(smem + sbytes) : g_r;
 }
 
-// A small graph's CSR (row offsets, columns, weights, degrees) copied into
-// shared memory at byte offset `at`, so that the pass's row reads stay on
-// chip; the pointers are redirected to the copies.
+// A small graph's CSR copied into shared memory at byte offset `at` so that
+// the pass's reads stay on chip; the pointers are redirected to the copies.
+// Row offsets and degrees (read for the 32 candidates of every pop) come
+// first; columns and weights (read for the popped row) only when `full`.
 template <typename WT>
-__device__ void seq_csr_to_smem(unsigned char* smem, long long at, int n, long long M,
+__device__ void seq_csr_to_smem(unsigned char* smem, long long at, int n, long long M, int full,
                                 const int64_t*& rp, const int*& col, const WT*& w,
                                 const WT*& deg) {
   int64_t* srp = reinterpret_cast<int64_t*>(smem + at);
-  WT* sw = reinterpret_cast<WT*>(srp + (n + 1));
-  WT* sdeg = sw + M;
-  int* scol = reinterpret_cast<int*>(sdeg + n);
+  WT* sdeg = reinterpret_cast<WT*>(srp + (n + 1));
+  WT* sw = sdeg + n;
+  int* scol = reinterpret_cast<int*>(sw + M);
   for (long long i = threadIdx.x; i <= n; i += blockDim.x) srp[i] = rp[i];
-  for (long long i = threadIdx.x; i < M; i += blockDim.x) {
-    scol[i] = col[i];
-    sw[i] = w[i];
-  }
   for (long long i = threadIdx.x; i < n; i += blockDim.x) sdeg[i] = deg[i];
+  if (full) {
+    for (long long i = threadIdx.x; i < M; i += blockDim.x) {
+      scol[i] = col[i];
+      sw[i] = w[i];
+    }
+  }
   __syncthreads();
   rp = srp;
-  col = scol;
-  w = sw;
   deg = sdeg;
+  if (full) {
+    col = scol;
+    w = sw;
+  }
 }
 
 template <typename WT, typename KT>
@@ -510,7 +515,7 @@ __global__ void __launch_bounds__(512)
                   const WT* __restrict__ w, const WT* __restrict__ deg, int start, int* parent,
                   WT* g_r, KT* g_levels, int* __restrict__ order, int* __restrict__ marks_out,
                   long long marks_cap, int smem_from, int r_in_smem, long long csr_at,
-                  long long M, DevState* st) {
+                  int csr_full, long long M, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SeqTree tl = seq_tree(n);
   KT* lev[8];
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(512)
   const int* col_ = col;
   const WT* w_ = w;
   const WT* deg_ = deg;
-  if (csr_at >= 0) seq_csr_to_smem<WT>(smem, csr_at, n, M, rp_, col_, w_, deg_);
+  if (csr_at >= 0) seq_csr_to_smem<WT>(smem, csr_at, n, M, csr_full, rp_, col_, w_, deg_);
   long long best_alpha;
   int best_len, ns;
   unsigned long long my_marks;
@@ -627,7 +632,8 @@ __global__ void __launch_bounds__(512)
                         unsigned long long seed, int* parent, WT* g_r, KT* g_levels,
                         long long tree_words, int* __restrict__ order,
                         unsigned long long* __restrict__ pass_best, int* __restrict__ pass_len,
-                        int smem_from, int r_in_smem, long long csr_at, long long M,
+                        int smem_from, int r_in_smem, long long csr_at, int csr_full,
+                        long long M,
                         DevState* st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = blockIdx.x;
@@ -640,7 +646,7 @@ __global__ void __launch_bounds__(512)
   const int* col_ = col;
   const WT* w_ = w;
   const WT* deg_ = deg;
-  if (csr_at >= 0) seq_csr_to_smem<WT>(smem, csr_at, n, M, rp_, col_, w_, deg_);
+  if (csr_at >= 0) seq_csr_to_smem<WT>(smem, csr_at, n, M, csr_full, rp_, col_, w_, deg_);
   const int start = k == 0 ? 0 : (int)(mix64(seed ^ mix64((unsigned long long)k)) % (unsigned long long)n);
   long long best_alpha;
   int best_len, ns;
@@ -663,10 +669,29 @@ __global__ void __launch_bounds__(512)
 
 }  // namespace
 
-// Bytes of a CSR copy in shared memory (int64 offsets, weights, degrees,
-// int32 columns, in that order).
-size_t seq_csr_bytes(int n, long long M, size_t wt) {
-  return (size_t)(n + 1) * 8 + (size_t)M * wt + (size_t)n * wt + (size_t)M * 4;
+// Bytes of a CSR copy in shared memory (int64 offsets, degrees, then with
+// `full` the weights and int32 columns, in that order).
+size_t seq_csr_bytes(int n, long long M, size_t wt, bool full) {
+  return (size_t)(n + 1) * 8 + (size_t)n * wt + (full ? (size_t)M * (wt + 4) : 0);
+}
+
+// Where the CSR copy of a sequential pass goes: after `smem` bytes when r[]
+// is on chip, whole if it fits under `limit`, else offsets and degrees only.
+static void seq_csr_place(int n, long long M, size_t wt, int r_in_smem, size_t limit,
+                          size_t* smem, long long* csr_at, int* csr_full) {
+  *csr_at = -1;
+  *csr_full = 0;
+  if (!r_in_smem) return;
+  const size_t at = (*smem + 15) / 16 * 16;
+  for (int full = 1; full >= 0; --full) {
+    const size_t b = seq_csr_bytes(n, M, wt, full != 0);
+    if (at + b <= limit) {
+      *csr_at = (long long)at;
+      *csr_full = full;
+      *smem = at + b;
+      return;
+    }
+  }
 }
 
 template <typename WT>
@@ -738,11 +763,8 @@ cudaError_t capforest_sequential(int n, long long M, const int64_t* rp, const in
     smem = lev_bytes + (size_t)n * sizeof(WT);
   }
   long long csr_at = -1;
-  const size_t csr_bytes = seq_csr_bytes(n, M, sizeof(WT));
-  if (r_in_smem && (smem + 15) / 16 * 16 + csr_bytes <= limit) {
-    csr_at = (long long)((smem + 15) / 16 * 16);
-    smem = (size_t)csr_at + csr_bytes;
-  }
+  int csr_full = 0;
+  seq_csr_place(n, M, sizeof(WT), r_in_smem, limit, &smem, &csr_at, &csr_full);
   static bool attr[2] = {false, false};
   const int ai = sizeof(WT) == 8 ? 1 : 0;
   if (!attr[ai]) {
@@ -752,7 +774,8 @@ cudaError_t capforest_sequential(int n, long long M, const int64_t* rp, const in
   }
   cf_seq_kernel<WT, KT><<<1, 512, smem, s>>>(n, rp, col, w, deg, start, parent, r,
                                              reinterpret_cast<KT*>(tree), order, marks_out,
-                                             marks_cap, smem_from, r_in_smem, csr_at, M, st);
+                                             marks_cap, smem_from, r_in_smem, csr_at, csr_full,
+                                             M, st);
   ++*launches;
   return cudaGetLastError();
 }
@@ -784,11 +807,8 @@ cudaError_t capforest_sequential_multi(int n, long long M, const int64_t* rp, co
     smem = lev_bytes + (size_t)n * sizeof(WT);
   }
   long long csr_at = -1;
-  const size_t csr_bytes = seq_csr_bytes(n, M, sizeof(WT));
-  if (r_in_smem && (smem + 15) / 16 * 16 + csr_bytes <= limit) {
-    csr_at = (long long)((smem + 15) / 16 * 16);
-    smem = (size_t)csr_at + csr_bytes;
-  }
+  int csr_full = 0;
+  seq_csr_place(n, M, sizeof(WT), r_in_smem, limit, &smem, &csr_at, &csr_full);
   static bool attr[2] = {false, false};
   const int ai = sizeof(WT) == 8 ? 1 : 0;
   if (!attr[ai]) {
@@ -799,7 +819,7 @@ cudaError_t capforest_sequential_multi(int n, long long M, const int64_t* rp, co
   cf_seq_multi_kernel<WT, KT><<<passes, 512, smem, s>>>(
       n, rp, col, w, deg, seed, parent, r_pool, reinterpret_cast<KT*>(tree_pool),
       seq_tree_words(n) * (long long)(sizeof(unsigned long long) / sizeof(KT)), order_pool,
-      pass_best, pass_len, smem_from, r_in_smem, csr_at, M, st);
+      pass_best, pass_len, smem_from, r_in_smem, csr_at, csr_full, M, st);
   cf_multi_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, passes, st);
   *launches += 2;
   return cudaGetLastError();
