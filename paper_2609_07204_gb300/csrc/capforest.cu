@@ -323,7 +323,8 @@ template <typename WT, typename KT>
 __device__ void seq_pass_body(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
                               int vbase, const WT* __restrict__ w, const WT* __restrict__ deg,
                               int start, int* parent, KT** lev, const SeqTree& tl, volatile WT* r,
-                              int* __restrict__ order, int* __restrict__ marks_out,
+                              int* __restrict__ order, int* __restrict__ mark_src,
+                              int* __restrict__ marks_out,
                               long long marks_cap, long long lam0, long long* best_alpha_out,
                               int* best_len_out, int* ns_out, unsigned long long* marks_out_cnt,
                               bool* uf_fail_out) {
@@ -336,6 +337,8 @@ __device__ void seq_pass_body(int n, const int64_t* __restrict__ rp, const int* 
   for (int l = 1; l <= tl.levels; ++l)
     for (long long i = tid; i < tl.size[l]; i += blockDim.x) lev[l][i] = 0;
   for (long long i = tid; i < n; i += blockDim.x) r[i] = 0;
+  if (mark_src)
+    for (long long i = tid; i < n; i += blockDim.x) mark_src[i] = -1;
   if (tid == 0) {
     s_lam = lam0;
     s_done = 0;
@@ -436,7 +439,11 @@ __device__ void seq_pass_body(int n, const int64_t* __restrict__ rp, const int* 
       const long long r1 = r0 + c;
       r[y] = (WT)r1;
       if (r0 < lam && lam <= r1) {
-        if (!uf_union(parent, x + vbase, y + vbase)) uf_fail = true;
+        // r(y) crosses the bound once per pass (r grows, the bound only
+        // falls), so each y has at most one marking edge: recorded here,
+        // hooked after the pass, off the chain of pops
+        if (mark_src) mark_src[y] = x;
+        else if (!uf_union(parent, x + vbase, y + vbase)) uf_fail = true;
         ++my_marks;
         if (marks_out) {
           const unsigned long long k = atomicAdd(&s_nmarks, 1ull);
@@ -454,6 +461,12 @@ __device__ void seq_pass_body(int n, const int64_t* __restrict__ rp, const int* 
       }
     }
     __syncthreads();
+  }
+  if (mark_src) {
+    for (long long i = tid; i < n; i += blockDim.x) {
+      const int x = mark_src[i];
+      if (x >= 0 && !uf_union(parent, x + vbase, (int)i + vbase)) uf_fail = true;
+    }
   }
   *best_alpha_out = best_alpha;
   *best_len_out = best_len;
@@ -513,9 +526,9 @@ template <typename WT, typename KT>
 __global__ void __launch_bounds__(512)
     cf_seq_kernel(int n, const int64_t* __restrict__ rp, const int* __restrict__ col,
                   const WT* __restrict__ w, const WT* __restrict__ deg, int start, int* parent,
-                  WT* g_r, KT* g_levels, int* __restrict__ order, int* __restrict__ marks_out,
-                  long long marks_cap, int smem_from, int r_in_smem, long long csr_at,
-                  int csr_full, long long M, DevState* st) {
+                  WT* g_r, KT* g_levels, int* __restrict__ order, int* __restrict__ mark_src,
+                  int* __restrict__ marks_out, long long marks_cap, int smem_from,
+                  int r_in_smem, long long csr_at, int csr_full, long long M, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SeqTree tl = seq_tree(n);
   KT* lev[8];
@@ -530,7 +543,8 @@ __global__ void __launch_bounds__(512)
   int best_len, ns;
   unsigned long long my_marks;
   bool uf_fail;
-  seq_pass_body<WT, KT>(n, rp_, col_, 0, w_, deg_, start, parent, lev, tl, rr, order, marks_out,
+  seq_pass_body<WT, KT>(n, rp_, col_, 0, w_, deg_, start, parent, lev, tl, rr, order, mark_src,
+                        marks_out,
                         marks_cap, (long long)st->lambda, &best_alpha, &best_len, &ns, &my_marks,
                         &uf_fail);
   const int lane = threadIdx.x & 31;
@@ -575,8 +589,8 @@ __global__ void __launch_bounds__(512)
   bool uf_fail;
   const long long lam0 = (long long)*(volatile unsigned long long*)&bv.lam_g[g];
   seq_pass_body<WT, KT>(n, rp + vbase, col, vbase, w, deg + vbase, 0, parent, lev, tl, rr,
-                        order + vbase, nullptr, 0, lam0, &best_alpha, &best_len, &ns, &my_marks,
-                        &uf_fail);
+                        order + vbase, nullptr, nullptr, 0, lam0, &best_alpha, &best_len, &ns,
+                        &my_marks, &uf_fail);
   const int lane = threadIdx.x & 31;
   if (uf_fail) set_error(st, ERR_INTERNAL);
   my_marks = warp_sum(my_marks);
@@ -631,6 +645,7 @@ __global__ void __launch_bounds__(512)
                         const WT* __restrict__ w, const WT* __restrict__ deg,
                         unsigned long long seed, int* parent, WT* g_r, KT* g_levels,
                         long long tree_words, int* __restrict__ order,
+                        int* __restrict__ mark_pool,
                         unsigned long long* __restrict__ pass_best, int* __restrict__ pass_len,
                         int smem_from, int r_in_smem, long long csr_at, int csr_full,
                         long long M,
@@ -653,7 +668,7 @@ __global__ void __launch_bounds__(512)
   unsigned long long my_marks;
   bool uf_fail;
   seq_pass_body<WT, KT>(n, rp_, col_, 0, w_, deg_, start, parent, lev, tl, rr,
-                        order + (long long)k * n, nullptr, 0,
+                        order + (long long)k * n, mark_pool + (long long)k * n, nullptr, 0,
                         (long long)*(volatile unsigned long long*)&st->lambda, &best_alpha,
                         &best_len, &ns, &my_marks, &uf_fail);
   const int lane = threadIdx.x & 31;
@@ -739,10 +754,9 @@ long long seq_tree_words(int n) {
 template <typename WT>
 cudaError_t capforest_sequential(int n, long long M, const int64_t* rp, const int* col,
                                  const WT* w, const WT* deg, int start, int* parent, WT* r,
-                                 uint8_t* visited, unsigned long long* tree, int* order,
+                                 int* mark_src, unsigned long long* tree, int* order,
                                  int* marks_out, long long marks_cap, DevState* st,
                                  cudaStream_t s, int* launches) {
-  (void)visited;
   using KT = typename std::conditional<sizeof(WT) == 4, unsigned, unsigned long long>::type;
   const size_t limit = 200 * 1024;
   const SeqTree t = seq_tree(n);
@@ -773,7 +787,8 @@ cudaError_t capforest_sequential(int n, long long M, const int64_t* rp, const in
     attr[ai] = true;
   }
   cf_seq_kernel<WT, KT><<<1, 512, smem, s>>>(n, rp, col, w, deg, start, parent, r,
-                                             reinterpret_cast<KT*>(tree), order, marks_out,
+                                             reinterpret_cast<KT*>(tree), order, mark_src,
+                                             marks_out,
                                              marks_cap, smem_from, r_in_smem, csr_at, csr_full,
                                              M, st);
   ++*launches;
@@ -785,7 +800,8 @@ cudaError_t capforest_sequential_multi(int n, long long M, const int64_t* rp, co
                                        const WT* w, const WT* deg, int passes,
                                        unsigned long long seed,
                                        int* parent, WT* r_pool, unsigned long long* tree_pool,
-                                       int* order_pool, unsigned long long* pass_best,
+                                       int* order_pool, int* mark_pool,
+                                       unsigned long long* pass_best,
                                        int* pass_len, DevState* st, cudaStream_t s,
                                        int* launches) {
   using KT = typename std::conditional<sizeof(WT) == 4, unsigned, unsigned long long>::type;
@@ -819,7 +835,7 @@ cudaError_t capforest_sequential_multi(int n, long long M, const int64_t* rp, co
   cf_seq_multi_kernel<WT, KT><<<passes, 512, smem, s>>>(
       n, rp, col, w, deg, seed, parent, r_pool, reinterpret_cast<KT*>(tree_pool),
       seq_tree_words(n) * (long long)(sizeof(unsigned long long) / sizeof(KT)), order_pool,
-      pass_best, pass_len, smem_from, r_in_smem, csr_at, csr_full, M, st);
+      mark_pool, pass_best, pass_len, smem_from, r_in_smem, csr_at, csr_full, M, st);
   cf_multi_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, passes, st);
   *launches += 2;
   return cudaGetLastError();
@@ -861,13 +877,14 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
                                             int*, const BatchView*);                          \
   template cudaError_t capforest_sequential<WT>(int, long long, const int64_t*, const int*,     \
                                                 const WT*,                                     \
-                                                const WT*, int, int*, WT*, uint8_t*,          \
+                                                const WT*, int, int*, WT*, int*,              \
                                                 unsigned long long*, int*, int*, long long,   \
                                                 DevState*, cudaStream_t, int*);               \
   template cudaError_t capforest_sequential_multi<WT>(                                        \
       int, long long, const int64_t*, const int*, const WT*, const WT*, int,                   \
       unsigned long long, int*,                                                               \
-      WT*, unsigned long long*, int*, unsigned long long*, int*, DevState*, cudaStream_t, int*); \
+      WT*, unsigned long long*, int*, int*, unsigned long long*, int*, DevState*, cudaStream_t, \
+      int*);                                                                                  \
   template cudaError_t capforest_sequential_batch<WT>(                                        \
       int, const int64_t*, const int*, const WT*, const WT*, int*, WT*, unsigned long long*,   \
       const long long*, int*, int, int, const BatchView&, DevState*, cudaStream_t, int*);

@@ -179,7 +179,7 @@ struct mincut_graph {
   unsigned long long* pass_best = nullptr;
   int *pass_len = nullptr, *pass_counter = nullptr;
   void* seq_r = nullptr;
-  uint8_t* seq_vis = nullptr;
+  int* seq_mark = nullptr;  // the sequential pass's marks until the pass ends
   unsigned long long* seq_tree = nullptr;
   int* seq_order = nullptr;
   // several sequential passes at once (allocated at first use)
@@ -187,6 +187,7 @@ struct mincut_graph {
   void* seq_multi_r = nullptr;
   unsigned long long* seq_multi_tree = nullptr;
   int* seq_multi_order = nullptr;
+  int* seq_multi_mark = nullptr;
   // sort
   SortScratch sort{};
   // state
@@ -416,12 +417,13 @@ int ensure_seq_multi(mincut_graph* g, int want) {
   if (g->seq_multi_k > 0) return g->seq_multi_k;
   const size_t wsz = g->wt64 ? 8 : 4;
   const long long n = g->n0;
-  const long long per = n * (long long)(4 + wsz) + seq_tree_words((int)n) * 8;
+  const long long per = n * (long long)(8 + wsz) + seq_tree_words((int)n) * 8;
   const long long cap = std::max<long long>(1, (2ll << 30) / std::max<long long>(per, 1));
   const int k = (int)std::min<long long>(want, cap);
   if (!(g->seq_multi_r = dev_alloc(g, (size_t)k * n * wsz)) ||
       !galloc(g, &g->seq_multi_tree, (long long)k * seq_tree_words((int)n)) ||
-      !galloc(g, &g->seq_multi_order, (long long)k * n))
+      !galloc(g, &g->seq_multi_order, (long long)k * n) ||
+      !galloc(g, &g->seq_multi_mark, (long long)k * n))
     return 0;
   g->seq_multi_k = k;
   return k;
@@ -717,7 +719,8 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
         ProfScope ps(P_CF_SEQ, M, s);
         CK(capforest_sequential_multi<WT>(n, M, rp, col, w, deg, k, c.seed, g->parent,
                                           (WT*)g->seq_multi_r, g->seq_multi_tree,
-                                          g->seq_multi_order, g->pass_best, g->pass_len, g->st, s,
+                                          g->seq_multi_order, g->seq_multi_mark, g->pass_best,
+                                          g->pass_len, g->st, s,
                                           &g->launches));
       }
       rc = sync_state(g);
@@ -733,7 +736,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     const int start = (c.capforest == 2) ? c.cf_start : 0;
     {
       ProfScope ps(P_CF_SEQ, M, s);
-      CK(capforest_sequential<WT>(n, M, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_vis,
+      CK(capforest_sequential<WT>(n, M, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_mark,
                                   g->seq_tree, g->seq_order, marks_dev, cap, g->st, s,
                                   &g->launches));
     }
@@ -1210,7 +1213,7 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
        galloc(g, &g->visit_log, (long long)g->max_passes * g->max_table) &&
        galloc(g, &g->pass_best, g->max_passes) && galloc(g, &g->pass_len, g->max_passes) &&
        galloc(g, &g->pass_counter, 1) && (g->seq_r = dev_alloc(g, (size_t)n * wsz)) &&
-       galloc(g, &g->seq_vis, n) && galloc(g, &g->seq_tree, seq_tree_words(n)) &&
+       galloc(g, &g->seq_mark, n) && galloc(g, &g->seq_tree, seq_tree_words(n)) &&
        galloc(g, &g->seq_order, n) && galloc(g, &g->sort.hist, 8 * 256) &&
        galloc(g, &g->sort.goff, 8 * 256) &&
        galloc(g, &g->sort.lookback, sort_lookback_words(Mb));

@@ -259,14 +259,16 @@ cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT*
 size_t capforest_pass_smem(int table, int warps_per_block, size_t wt_size);
 
 // One sequential CAPFOREST pass over the whole graph from `start` (one block).
-// r[n], visited[n], tree[seq_tree_words(n)] are scratch (unused when the pass
-// fits in shared memory); order[n] receives the visit order; marks_out
-// (nullable) up to marks_cap pairs.  The best alpha goes to st->cf_val/cf_len
-// with st->cf_pass = -1; st->cf_nscanned counts the visited vertices.
+// r[n], tree[seq_tree_words(n)] are scratch (unused when the pass fits in
+// shared memory); order[n] receives the visit order; mark_src[n] (nullable)
+// holds each vertex's marking edge until the pass ends, when the marks are
+// hooked together (NULL: hooked as found); marks_out (nullable) up to
+// marks_cap pairs.  The best alpha goes to st->cf_val/cf_len with
+// st->cf_pass = -1; st->cf_nscanned counts the visited vertices.
 template <typename WT>
 cudaError_t capforest_sequential(int n, long long M, const int64_t* rp, const int* col,
                                  const WT* w, const WT* deg, int start, int* parent, WT* r,
-                                 uint8_t* visited, unsigned long long* tree, int* order,
+                                 int* mark_src, unsigned long long* tree, int* order,
                                  int* marks_out, long long marks_cap, DevState* st,
                                  cudaStream_t s, int* launches);
 long long seq_tree_words(int n);
@@ -279,7 +281,8 @@ long long seq_tree_words(int n);
 // `passes` sequential passes at once, pass k from its own start vertex (pass
 // 0 from vertex 0) with private keys and visit order: r_pool passes*n WT,
 // tree_pool passes*seq_tree_words(n) u64 (only the parts that do not fit in
-// shared memory are used), order_pool passes*n ints.  A pass that lowers the
+// shared memory are used), order_pool and mark_pool passes*n ints (mark_pool
+// as mark_src of capforest_sequential).  A pass that lowers the
 // bound lowers st->lambda; the best such pass k sets st->cf_val, cf_len and
 // cf_pass = -2 - k (its visit order is order_pool + k*n).
 template <typename WT>
@@ -287,9 +290,9 @@ cudaError_t capforest_sequential_multi(int n, long long M, const int64_t* rp, co
                                        const WT* w, const WT* deg, int passes,
                                        unsigned long long seed,
                                        int* parent, WT* r_pool, unsigned long long* tree_pool,
-                                       int* order_pool, unsigned long long* pass_best,
-                                       int* pass_len, DevState* st, cudaStream_t s,
-                                       int* launches);
+                                       int* order_pool, int* mark_pool,
+                                       unsigned long long* pass_best, int* pass_len,
+                                       DevState* st, cudaStream_t s, int* launches);
 
 template <typename WT>
 cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col, const WT* w,
