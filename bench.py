@@ -588,14 +588,20 @@ def main():
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched measurement, printed as one JSON object "
                          "(a short command to profile the batched kernels)")
+    ap.add_argument("--small-only", action="store_true",
+                    help="only the small single-graph measurement, printed as one JSON "
+                         "object (a short command to profile the sequential pass)")
     args = ap.parse_args()
-    if args.batched_only:
+    if args.batched_only or args.small_only:
         import torch
 
         import paper_2609_07204_gb300 as mc
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         mc.load_library()
-        print(json.dumps({"batched": measure_batched(mc)}), flush=True)
+        if args.batched_only:
+            print(json.dumps({"batched": measure_batched(mc)}), flush=True)
+        else:
+            print(json.dumps({"small_config": measure_small_config(mc)}), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
