@@ -1585,7 +1585,7 @@ int64_t mincut_graph_footprint(int64_t n, int64_t m_directed) {
   // 8-byte weights and sums double the weight terms; this bound assumes
   // 4-byte ones (total weight < 2^31) plus the label-propagation and the
   // row-wise contraction buffers
-  return (int64_t)(172 * n + 122 * m_directed + 4096 * P + (1 << 20));
+  return (int64_t)(176 * n + 122 * m_directed + 4096 * P + (1 << 20));
 }
 
 int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
