@@ -707,7 +707,13 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     CK(cudaMemcpyAsync(c.pr_flags_host, flags_dev, (size_t)M, cudaMemcpyDeviceToHost, s));
   long long marks = (long long)(g->hst->marks_pr + g->hst->marks_cf);
   o->marks_pr = (long long)g->hst->marks_pr;
-  bool need_seq = c.capforest == 2 || (c.capforest == 1 && marks == 0);
+  // the sequential pass when the round marked nothing (Algorithm 2), and on
+  // small graphs (n <= 8192, where a pass costs a few rounds' fixed cost at
+  // most) also when it marked so little (fewer edges than n / 64) that
+  // contracting would spend a whole round on almost no vertices; its marks
+  // only add
+  bool need_seq = c.capforest == 2 ||
+                  (c.capforest == 1 && (marks == 0 || (n <= 8192 && marks * 64 < n)));
   // several whole passes from different start vertices, each with private
   // arrays, when the concurrent passes found nothing (not in the modes that
   // report the single pass's order and marks)
