@@ -26,7 +26,9 @@
 //
 // capforest_sequential: one pass over the whole graph by one block (the
 // sequential CAPFOREST of Algorithm 2, used when the concurrent passes mark
-// nothing, and the deterministic mode).  Its queue is a 32-ary max tree over
+// nothing, and the deterministic mode).  A vertex's key crosses the bound
+// at most once in a pass, so its marking edge is recorded per vertex and
+// hooked after the pass, off the chain of pops.  Its queue is a 32-ary max tree over
 // per-vertex keys (key + 1, 0 = not queued); the descent takes the leftmost
 // maximum, i.e. the smallest vertex id among the largest keys.  Keys only
 // grow between pops (when alpha lowers lambda, every queued r(y) is at most
