@@ -9,18 +9,21 @@
 // the union-find of the marks and the contraction.  Of the PR tests only the
 // per-edge PR1 / PR2 run: on one warp the PR3 / PR4 intersections measured
 // several times the rest of a graph's solve, and the round's full pass marks
-// anyway.  The contraction sums
-// each contracted vertex's member rows into a dense accumulator of the new
-// vertex count (the per-vertex dense accumulation of Sec. 4, parallel
-// session (3)) and writes the row in label order, so the result is the same
-// canonical CSR as every other contraction.  A full pass on a connected
+// anyway.  The contraction sums each contracted vertex's member rows into a
+// dense accumulator of the new vertex count (the per-vertex dense
+// accumulation of Sec. 4, parallel session (3)) and writes the row in label
+// order, so the result is the same canonical CSR as every other
+// contraction.  A full pass on a connected
 // graph with lambda-hat > 0 marks at least one edge (its last vertex t has
 // r(t) = c(t) >= lambda-hat), so every round but one whose pass lowered the
 // bound shrinks the graph.
 //
-// Graphs of up to kBwMaxN vertices: the keys (r values) and, later, the
-// accumulator live in shared memory, the two-level max tree over the keys
-// too.  All values are int: a batch's total weight is below 2^31.
+// Graphs of up to kBwMaxN vertices: the keys (r values, later the
+// accumulator), the two-level max tree over them, the current row offsets,
+// the degrees (later the labels), the group lists and the union-find live in
+// the warp's shared memory; the columns, weights, visit positions and the
+// map to the input vertices in its global slot.  All values are int: a
+// batch's total weight is below 2^31.
 #include <algorithm>
 #include <climits>
 
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(kBwWarps * 32)
         for (int i = lane; i < n0; i += 32) side0[v0 + i] = S.map[i] == x ? 1 : 0;
       }
       if (n <= 2 || lam == 0) break;
-      // ---- PR1-PR4, one lane per row, each edge once (u < v)
+      // ---- PR1 / PR2, one lane per row, each edge once (u < v)
       for (int v = lane; v < n; v += 32) parent[v] = v;
       __syncwarp();
       if (pr_mask) {
