@@ -203,10 +203,12 @@ def test_from_csr_rejects_asymmetry_with_balanced_counts(case):
         # 0-1 present both ways; 0->2 is answered by 3->1 instead of 2->0
         rp, col, w = [0, 2, 3, 3, 4], [1, 2, 0, 1], [1, 1, 1, 1]
         n = 4
-    for pinned in (False, True):
+    for where in ("pageable", "pinned", "device"):
         args = [np.asarray(rp, np.int64), np.asarray(col, np.int32), np.asarray(w, np.int32)]
-        if pinned:
+        if where == "pinned":
             args = [torch.from_numpy(a).pin_memory().numpy() for a in args]
+        elif where == "device":
+            args = [torch.from_numpy(a).cuda() for a in args]
         with pytest.raises(mc.MincutError) as e:
             mc.mincut_graph_from_csr(n, *args)
         assert e.value.status == mc.MINCUT_ERR_INVALID
