@@ -897,6 +897,7 @@ int coarsening_bound(mincut_graph* g, const mincut_options& op, const RoundCfg& 
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
+  g->m_pending = false;
   iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, g->stream>>>(g->map0, g->n0);
   ++g->launches;
   int rc = set_lambda(g, lambda);
@@ -914,6 +915,7 @@ int solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_value,
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
+  g->m_pending = false;
   if (op.spin_limit > 0) g->spin_limit = op.spin_limit;
   CK(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
   int rc = set_lambda(g, kInf);
@@ -1273,6 +1275,7 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
   g->cur = -1;
   g->n = n;
   g->M = g->M0;
+  g->m_pending = false;
   *out = g;
   return MINCUT_OK;
 }
@@ -1336,6 +1339,7 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
+  g->m_pending = false;
   if (op.spin_limit > 0) g->spin_limit = op.spin_limit;
   CK(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
   CK(cudaMemcpyAsync(b.voff, b.voff0, (size_t)(G + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -1442,6 +1446,7 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
+  g->m_pending = false;
   return MINCUT_OK;
 }
 
@@ -1497,6 +1502,7 @@ int mincut_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_value
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
+  g->m_pending = false;
   return rc;
 }
 
@@ -1545,6 +1551,7 @@ int mincut_graph_reset(mincut_graph* g) {
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
+  g->m_pending = false;
   return MINCUT_OK;
 }
 
@@ -1719,6 +1726,7 @@ int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut
   g->cur = -1;
   g->n = g->n0;
   g->M = g->M0;
+  g->m_pending = false;
   return rc;
 }
 
