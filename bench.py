@@ -24,6 +24,9 @@ until lambda is proven) on the graph already resident in HBM.
   small_config = connected G(2000, 16000) single solve against the CPU
             oracle's Stoer-Wagner and NOI
 
+--workload picks the single-graph workload of the main line: rmat20 (the
+default above), rmat18, er2000 (the small configuration) or planted21 (two
+2^21-vertex 30-cores joined by 25 unit edges, ~85 M edges, lambda = 25).
 --impl reference times the CPU oracle as the reference arm.  Multi-GPU runs
 (torchrun) are independent replicas: the solve does not shard.
 """
