@@ -57,7 +57,8 @@ typedef enum {
 /* Device allocator used for all of a graph's device memory.  alloc returns a
  * device pointer of at least `bytes` (256-byte aligned) or NULL; free releases
  * it.  Both are called on the host thread that makes the library call, with
- * the graph's stream.  NULL allocator: cudaMallocAsync / cudaFreeAsync. */
+ * the graph's stream.  NULL allocator: stream-ordered allocations from a pool
+ * per device owned by the library (see mincut_release_cached). */
 typedef struct mincut_allocator {
     void* (*alloc)(size_t bytes, void* stream, void* ctx);
     void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
