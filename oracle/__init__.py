@@ -21,8 +21,9 @@ Functions and the passages of the paper they follow:
 * ``round_``            -- one deterministic contraction round (Algorithms 1-2)
 * ``noi``               -- the sequential exact algorithm (Algorithm 2, one process)
 
-Parity status: every function above is pinned by tests/test_oracle_*.py except
-the labels produced by ``lp`` (parity unpinned: no closed form fixes them; the
+Parity status: every function above is pinned by tests/test_oracle_*.py; the
+labels produced by ``lp`` only by hand-traced sweeps (tests/golden/lp_trace.json)
+and small rule checks, since no closed form fixes them on larger graphs (the
 bound derived from them is pinned as the cut value of an explicit set).
 """
 from __future__ import annotations

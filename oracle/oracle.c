@@ -24,9 +24,11 @@
  * as an independent check that shares no code with NOI).
  *
  * Parity pins: brute force, closed forms and library cross-checks in
- * tests/test_oracle_*.py.  The label-propagation labels themselves are
- * parity unpinned (no closed form fixes them); the LP *bound* is pinned as a
- * cut value of an explicit vertex set.
+ * tests/test_oracle_*.py.  The label-propagation labels are pinned by
+ * hand-traced sweeps (tests/golden/lp_trace.json: ties, the strictly-larger
+ * rule and the parity order) and small rule checks; beyond those no closed
+ * form fixes them.  The LP *bound* is pinned as a cut value of an explicit
+ * vertex set.
  */
 #include <stdint.h>
 #include <stdlib.h>

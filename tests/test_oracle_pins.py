@@ -472,6 +472,19 @@ def test_lp_sweep_rule_small():
     assert lab.tolist() == [1, 1, 1]  # 1 keeps 1 (own weight 6 > 0)
 
 
+def test_lp_golden_trace():
+    with open(os.path.join(GOLD, "lp_trace.json")) as f:
+        gd = json.load(f)
+    n = gd["n"]
+    rp, col, w = G.from_edges(n, [tuple(e) for e in gd["edges"]], gd["weights"])
+    for iters, labels in gd["expect_labels"].items():
+        assert oracle.lp(n, rp, col, w, int(iters)).tolist() == labels, iters
+    lab = oracle.lp(n, rp, col, w, 3)
+    val, _ = oracle.lp_bound(n, rp, col, w, lab)
+    assert val == gd["expect_bound"]
+    assert oracle.mincut_brute(n, rp, col, w)[0] == gd["mincut"]
+
+
 # ---------------------------------------------------------------- round oracle
 def test_round_preserves_lambda():
     rng = np.random.default_rng(23)
