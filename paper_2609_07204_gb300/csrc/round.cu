@@ -11,7 +11,11 @@
 //
 // Entry-parallel kernels work on tiles of kEntryTile consecutive CSR entries;
 // tile_rows() records the row of each tile's first entry so a block finds the
-// rows of its entries with a binary search in shared memory.
+// rows of its entries with a binary search in shared memory.  Strided tiles
+// (thread t takes entries t, t + 256, ...) keep a warp's atomics on
+// neighbouring addresses; the per-row reductions (degrees, the first LP
+// sweep, the cluster cut) take runs of 8 consecutive entries per thread
+// instead, searching a run's first row once and walking forward.
 #include <algorithm>
 
 #include "common.cuh"
