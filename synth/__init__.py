@@ -290,10 +290,12 @@ def workload_rmat_core(scale: int = 20, k: int = 10, seed: int = 2) -> Graph:
     return g
 
 
-def workload_planted(log_nb: int = 21, avg_deg: int = 40, kcore: int = 30, cross: int = 25,
+def workload_planted(log_nb: int = 21, avg_deg: int = 42, kcore: int = 30, cross: int = 25,
                      seed: int = 3) -> Graph:
     """Two G(2^log_nb, avg_deg/2 * 2^log_nb) blocks, each kcore-pruned, joined by
-    ``cross`` unit cross edges (lambda = cross when both blocks stay dense)."""
+    ``cross`` unit cross edges (lambda = cross when both blocks stay dense).
+    The 30-core of G(n, p) appears only above an average degree of about 40,
+    so at 40 a small block's core can vanish; 42 keeps most of each block."""
     nb = 1 << log_nb
     g = planted(nb, nb * avg_deg // 2, kcore, cross, 1, seed)
     g.meta["workload"] = f"planted_2x2^{log_nb}_deg{avg_deg}_{kcore}core_cross{cross}"
