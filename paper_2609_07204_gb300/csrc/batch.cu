@@ -25,7 +25,7 @@ int sms_b() {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
+    if (sms <= 0) sms = kDefaultSms;
   }
   return sms;
 }

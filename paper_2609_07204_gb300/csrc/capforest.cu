@@ -50,7 +50,7 @@ int num_sms_cf() {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
+    if (sms <= 0) sms = kDefaultSms;
   }
   return sms;
 }

@@ -128,7 +128,7 @@ struct mincut_graph {
   bool user_alloc = false;
   std::vector<Alloc> allocs;
   bool wt64 = false;
-  int sms = 148;
+  int sms = kDefaultSms;
   // canonical input
   int n0 = 0;
   long long M0 = 0, Mraw = 0;
@@ -1590,9 +1590,9 @@ int mincut_release_cached(int device) {
 
 int64_t mincut_graph_footprint(int64_t n, int64_t m_directed) {
   if (n < 0 || m_directed < 0) return -1;
-  int dev = 0, sms = 148;
+  int dev = 0, sms = kDefaultSms;
   cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = kDefaultSms;
   cudaGetLastError();
   const long long P = graph_max_passes(n, sms);
   // 8-byte weights and sums double the weight terms; this bound assumes

@@ -13,6 +13,8 @@ namespace mc {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWarp = 32;
+// SM count assumed when the device cannot be asked (GB300: two dies of 76)
+constexpr int kDefaultSms = 152;
 constexpr long long kInf = 0x7fffffffffffffffll;
 
 // Error bits written by kernels into DevState::error.

@@ -315,7 +315,7 @@ cudaError_t radix_sort_pairs(u64* k0, WT* v0, u64* k1, WT* v1, int N, int bits, 
   }
   cudaMemsetAsync(sc.hist, 0, 8 * 256 * sizeof(unsigned), s);
   cudaMemsetAsync(st->tile_counter, 0, sizeof(st->tile_counter), s);
-  int dev = 0, sms = 148;
+  int dev = 0, sms = kDefaultSms;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int hgrid = (int)std::min<long long>((maxN + 4095) / 4096, (long long)sms * 4);
