@@ -1,0 +1,78 @@
+"""Host-side arithmetic of bench.py, on fake inputs: the nvidia-smi clock
+record (median SM clock, throttle reasons) and the contraction GB/s of the
+roofline object (algorithmic bytes over CUDA-event time).  CPU only."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _line(sm, mx=2070, act="0x0000000000000000", hw="Not Active", hwt="Not Active",
+          swt="Not Active", cap="Not Active"):
+    return f"0, {sm}, {mx}, 900.5, {act}, {hw}, {hwt}, {swt}, {cap}"
+
+
+def test_clock_lines_median_and_reasons():
+    lines = [_line(1965), _line(2032, cap="Active"), _line(1980), "garbage", "",
+             _line("[N/A]"), _line(1700, hwt="Active")]
+    c = bench.parse_clock_lines(lines)
+    assert c["samples"] == 4
+    assert c["sm_mhz"] == pytest.approx((1965 + 1980) / 2)
+    assert c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_lines_empty():
+    assert bench.parse_clock_lines([]) is None
+    assert bench.parse_clock_lines(["a, b"]) is None
+
+
+def test_contraction_gbs_is_algorithmic_bytes_over_time():
+    prof = {
+        "contract_rows": {"ms": 2.0, "units": 10**9, "launches": 4},
+        "emit": {"ms": 1.0, "units": 10**8, "launches": 1},
+        "sort_pass": {"ms": 0.0, "units": 5, "launches": 0},  # not run: skipped
+        "pr_marks": {"ms": 9.0, "units": 10**9, "launches": 1},  # not contraction
+    }
+    out = bench.contraction_gbs(prof, 8000.0, "measured")
+    b_rows = 10**9 * bench.ALG_BYTES["contract_rows"]
+    b_emit = 10**8 * bench.ALG_BYTES["emit"]
+    assert out["contract_rows"]["gbs"] == pytest.approx(b_rows / 2e-3 / 1e9)
+    assert out["emit"]["gbs"] == pytest.approx(b_emit / 1e-3 / 1e9)
+    assert "sort_pass" not in out and "pr_marks" not in out
+    tot = (b_rows + b_emit) / 3e-3 / 1e9
+    assert out["total"]["gbs"] == pytest.approx(tot)
+    assert out["total"]["frac"] == pytest.approx(tot / 8000.0)
+    assert out["total"]["peak_kind"] == "measured"
+    assert bench.contraction_gbs({}, 8000.0, "measured") == {}
+
+
+def test_peaks_file_is_read():
+    peak, kind = bench.load_peaks()
+    assert peak > 0 and kind in ("measured", "fallback")
+
+
+def test_reference_arm_line_on_cpu():
+    """The reference arm (the CPU oracle's NOI) prints the contract's JSON
+    line; run here on the small G(2000, 16000) workload."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "er2000", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3
+    assert d["config"]["lambda"] == 23
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
