@@ -88,3 +88,48 @@ def test_product_path_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle.c" not in text and "liboracle" not in text, f
+
+
+def test_batch_rejects_bad_offsets_before_device_work(lib):
+    rp = np.array([0, 1, 2, 3, 4], np.int64)
+    col = np.array([1, 0, 3, 2], np.int32)
+    w = np.ones(4, np.int32)
+    for vo, what in (([1, 2, 4], "vertex_offsets[0]"), ([0, 1, 4], "fewer than 2"),
+                     ([0, 2, 2, 4], "fewer than 2")):
+        with pytest.raises(mc.MincutError) as e:
+            mc.mincut_batch_from_csr(np.array(vo, np.int64), rp, col, w)
+        assert e.value.status == mc.MINCUT_ERR_INVALID
+        assert what in mc.mincut_last_error()
+    out = ctypes.c_void_p(0)
+    vo = np.array([0], np.int64)
+    assert lib.mincut_batch_from_csr(0, vo.ctypes.data, rp.ctypes.data, col.ctypes.data,
+                                     w.ctypes.data, 0, None, None,
+                                     ctypes.byref(out)) == mc.MINCUT_ERR_INVALID
+    assert lib.mincut_batch_from_csr(1, None, None, None, None, 0, None, None,
+                                     ctypes.byref(out)) == mc.MINCUT_ERR_INVALID
+
+
+def test_server_rejects_bad_options_and_requests(lib):
+    for kw in ({"workers": 0}, {"workers": 65}, {"hbm_cap_bytes": 0}):
+        o = mc.server_default_options(**kw)
+        out = ctypes.c_void_p(0)
+        assert lib.mincut_server_create(ctypes.byref(o), ctypes.byref(out)) == mc.MINCUT_ERR_INVALID
+        assert not out.value
+    rid = ctypes.c_uint64(0)
+    rp = np.array([0, 1, 2], np.int64)
+    assert lib.mincut_server_submit(None, 2, rp.ctypes.data, None, None,
+                                    ctypes.byref(rid)) == mc.MINCUT_ERR_INVALID
+
+
+def test_footprint_estimate(lib):
+    """The admission estimate: -1 for negative sizes, monotone in both sizes,
+    and at least the input CSR and its two contracted copies."""
+    assert mc.mincut_graph_footprint(-1, 10) == -1
+    assert mc.mincut_graph_footprint(10, -1) == -1
+    prev = 0
+    for n, M in ((2, 2), (1000, 16000), (247_314, 29_031_216), (4 << 20, 170 << 20)):
+        f = mc.mincut_graph_footprint(n, M)
+        assert f > prev and f >= 3 * (8 * (n + 1) + 8 * M)
+        assert mc.mincut_graph_footprint(n + 1, M) > f
+        assert mc.mincut_graph_footprint(n, M + 1) > f
+        prev = f
