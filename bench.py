@@ -157,10 +157,11 @@ def parse_clock_lines(lines):
         if len(f) < 9:
             continue
         try:
-            sm.append(float(f[1]))
-            mx = float(f[2])
+            cur, top = float(f[1]), float(f[2])
         except ValueError:
             continue
+        sm.append(cur)
+        mx = top
         for nm, v in zip(names, f[5:9]):
             if v.lower().startswith("active"):
                 reasons.add(nm)

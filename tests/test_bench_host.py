@@ -18,7 +18,7 @@ def _line(sm, mx=2070, act="0x0000000000000000", hw="Not Active", hwt="Not Activ
 
 def test_clock_lines_median_and_reasons():
     lines = [_line(1965), _line(2032, cap="Active"), _line(1980), "garbage", "",
-             _line("[N/A]"), _line(1700, hwt="Active")]
+             _line("[N/A]"), _line(1990, mx="[N/A]"), _line(1700, hwt="Active")]
     c = bench.parse_clock_lines(lines)
     assert c["samples"] == 4
     assert c["sm_mhz"] == pytest.approx((1965 + 1980) / 2)
