@@ -133,3 +133,17 @@ def test_footprint_estimate(lib):
         assert mc.mincut_graph_footprint(n + 1, M) > f
         assert mc.mincut_graph_footprint(n, M + 1) > f
         prev = f
+
+
+def test_size_limits_rejected_before_device_work(lib):
+    out = ctypes.c_void_p(0)
+    one = np.zeros(4, np.int32)
+    rp = np.zeros(4, np.int64)
+    rc = lib.mincut_graph_from_csr(1 << 31, rp.ctypes.data, one.ctypes.data, one.ctypes.data,
+                                   mc.MINCUT_HOST_PTRS, None, None, ctypes.byref(out))
+    assert rc == mc.MINCUT_ERR_OVERFLOW and "2^31-2" in mc.mincut_last_error()
+    rp = np.array([0, 0, 1 << 31], np.int64)  # M = 2^31 entries
+    rc = lib.mincut_graph_from_csr(2, rp.ctypes.data, one.ctypes.data, one.ctypes.data,
+                                   mc.MINCUT_HOST_PTRS, None, None, ctypes.byref(out))
+    assert rc == mc.MINCUT_ERR_OVERFLOW and "2^31-1" in mc.mincut_last_error()
+    assert not out.value
