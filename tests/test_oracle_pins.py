@@ -500,6 +500,28 @@ def test_round_preserves_lambda():
         assert min(info["lambda"], lam2) == lam_true
 
 
+@pytest.mark.parametrize("case", ["A", "B", "C", "D", "E"])
+def test_round_golden_trace(case):
+    d = gold("round_two_triangles.json")
+    n = d["n"]
+    rp, col, w = G.from_edges(n, d["edges"], d["weights"])
+    c = d["cases"][case]
+    lam_in = INF if c["lambda_in"] is None else c["lambda_in"]
+    n2, rp2, col2, w2, info = oracle.round_(n, rp, col, w, lambda_in=lam_in, lp_iters=0,
+                                            pr_mask=c["pr_mask"], capforest=c["capforest"])
+    ex = c["expect"]
+    assert n2 == ex["n2"]
+    for k in ("lambda", "marks_pr", "marks_cf", "stopped"):
+        assert info[k] == ex[k], k
+    if ex.get("unchanged"):
+        assert rp2.tolist() == rp.tolist() and col2.tolist() == col.tolist()
+        assert w2.tolist() == w.tolist()
+    else:
+        assert rp2.tolist() == ex["rp2"] and col2.tolist() == ex["col2"]
+        assert w2.tolist() == ex["w2"]
+    assert oracle.mincut_brute(n, rp, col, w)[0] == d["mincut"]
+
+
 def test_round_iterated_reaches_lambda():
     g = synth.er_connected(300, 1500, 1, 10, 3)
     s, _ = oracle.stoer_wagner(g.n, g.row_ptr, g.col, g.w)
