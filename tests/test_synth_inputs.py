@@ -10,7 +10,6 @@ import pytest
 
 import synth
 
-nx = pytest.importorskip("networkx")
 
 
 def _edges(g):
@@ -21,6 +20,7 @@ def _edges(g):
 
 
 def _nx(g, weight_filter=None):
+    nx = pytest.importorskip("networkx")
     G = nx.Graph()
     G.add_nodes_from(range(g.n))
     for u, v, w in zip(*_edges(g)):
@@ -67,6 +67,7 @@ def test_er_exact_size_weights_and_determinism():
 
 
 def test_rmat_is_skewed_and_core_lcc_matches_networkx():
+    nx = pytest.importorskip("networkx")
     g = synth.rmat(12, 16, 0.57, 0.19, 0.19, 1, 1, 5)
     synth.check_csr(g)
     assert g.n == 4096 and np.all(g.w == 1)
@@ -117,6 +118,7 @@ def test_wheel_degrees_closed_form():
 
 
 def test_dblcyc_heavy_hamiltonian_and_light_half_cycles():
+    nx = pytest.importorskip("networkx")
     for n, heavy, light in ((10, 1000, 3), (22, 7, 2), (102, 50, 1)):
         h = n // 2
         g = synth.dblcyc(n, heavy, light, seed=n)
@@ -135,6 +137,7 @@ def test_dblcyc_heavy_hamiltonian_and_light_half_cycles():
 
 
 def test_cycle_plus_size_connectivity_and_weights():
+    nx = pytest.importorskip("networkx")
     for n, d in ((3, 10.0), (50, 3.0), (500, 6.0), (800, 11.5)):
         g = synth.cycle_plus(n, d, 1, 100, 9 + n)
         synth.check_csr(g)
@@ -166,6 +169,7 @@ def test_batched_workload_distribution():
 
 
 def test_serving_requests_connected_and_mixed():
+    nx = pytest.importorskip("networkx")
     kinds = set()
     for i in range(40):
         g = synth.serving_request(5, i, 100, 3000)
@@ -180,6 +184,7 @@ def test_serving_requests_connected_and_mixed():
 def test_workload_sizes_as_documented():
     """The single-solve workloads: G(2000, 16000) connected with weights in
     [1, 10]; the R-MAT scale-20 10-core with n = 247,314 and m = 14,515,608."""
+    nx = pytest.importorskip("networkx")
     c1 = synth.workload_er2000()
     synth.check_csr(c1)
     assert c1.n == 2000 and len(c1.col) == 32000
