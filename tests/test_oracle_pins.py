@@ -62,6 +62,41 @@ def test_complete_graph_large():
     assert s == q == 3 * (n - 1)
 
 
+def test_int32_max_weights_sum_in_int64():
+    """Weights at the int32 limit: every cut value exceeds 2^31 (K_n) or
+    2^32 and the oracle tiers still agree with the closed forms."""
+    W = (1 << 31) - 1
+    for n in (4, 7, 12):
+        b, s, q, *_ = mincut_all(n, G.complete(n, W))
+        assert s == q == (n - 1) * W
+        if b is not None:
+            assert b == (n - 1) * W
+    w = [W, W - 1, W - 2, W, W, W - 5]
+    b, s, q, *_ = mincut_all(6, G.cycle(6, w))
+    assert b == s == q == (W - 5) + (W - 2)
+
+
+def test_scale_invariance_at_large_weights():
+    """Multiplying every weight and the bound by k scales every cut by k and
+    changes no PR flag, CAPFOREST order or mark (all their tests compare
+    sums of weights); k = 2^24 pushes the sums past 2^32."""
+    rng = np.random.default_rng(29)
+    k = 1 << 24
+    for trial in range(40):
+        n = int(rng.integers(3, 10))
+        rp, col, w = G.random_graph(n, float(rng.uniform(0.3, 1.0)), rng, 1, 100)
+        wk = w.astype(np.int64) * k
+        lam = int(oracle.degrees(n, rp, col, w).min())
+        assert np.array_equal(oracle.pr_marks(n, rp, col, w, lam, 0xF, -1),
+                              oracle.pr_marks(n, rp, col, wk, lam * k, 0xF, -1))
+        a = oracle.capforest(n, rp, col, w, lam, 0)
+        b = oracle.capforest(n, rp, col, wk, lam * k, 0)
+        assert b["lambda"] == k * a["lambda"]
+        assert np.array_equal(a["order"], b["order"]) and np.array_equal(a["marks"], b["marks"])
+        assert oracle.noi(n, rp, col, wk)[0] == k * oracle.noi(n, rp, col, w)[0]
+        assert oracle.stoer_wagner(n, rp, col, wk)[0] == k * oracle.mincut_brute(n, rp, col, w)[0]
+
+
 def test_tree_is_min_edge():
     rng = np.random.default_rng(3)
     for n in [2, 5, 11, 16, 200]:
