@@ -97,6 +97,27 @@ def test_scale_invariance_at_large_weights():
         assert oracle.stoer_wagner(n, rp, col, wk)[0] == k * oracle.mincut_brute(n, rp, col, w)[0]
 
 
+def test_relabelling_invariance():
+    """lambda does not depend on vertex names: NOI and Stoer-Wagner on a
+    randomly relabelled copy agree with brute force on the original, and
+    the returned sides are cuts of that value in the relabelled graph."""
+    rng = np.random.default_rng(31)
+    for trial in range(60):
+        n = int(rng.integers(2, 14))
+        rp, col, w = G.random_graph(n, float(rng.uniform(0.2, 1.0)), rng, 1, 20)
+        lam = oracle.mincut_brute(n, rp, col, w)[0]
+        perm = rng.permutation(n)
+        src = np.repeat(np.arange(n), np.diff(rp))
+        keep = src < col
+        edges = list(zip(perm[src[keep]].tolist(), perm[col[keep]].tolist()))
+        g2 = G.from_edges(n, edges, w[keep].tolist())
+        q, side, _ = oracle.noi(n, *g2)
+        s2, sside = oracle.stoer_wagner(n, *g2)
+        assert q == s2 == lam
+        assert oracle.cut_weight(n, *g2, side) == lam
+        assert oracle.cut_weight(n, *g2, sside) == lam
+
+
 def test_tree_is_min_edge():
     rng = np.random.default_rng(3)
     for n in [2, 5, 11, 16, 200]:
