@@ -97,6 +97,24 @@ def contraction_gbs(prof, peak, peak_kind):
     return out
 
 
+def kernel_table(prof, steps, peak):
+    """Per kernel category of the live profile: launches, CUDA-event time
+    per step, share of the profiled time and, for the categories with an
+    algorithmic byte count, the achieved algorithmic GB/s and its fraction
+    of the HBM peak."""
+    total = sum(v["ms"] for v in prof.values())
+    out = {}
+    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]):
+        d = {"launches": v["launches"], "ms_per_step": v["ms"] / steps,
+             "share": v["ms"] / total if total else None}
+        if k in ALG_BYTES and v["ms"] > 0:
+            gbs = v["units"] * ALG_BYTES[k] / (v["ms"] / 1e3) / 1e9
+            d["alg_gbs"] = gbs
+            d["frac"] = gbs / peak
+        out[k] = d
+    return out
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -550,7 +568,6 @@ def run_gpu(args, rank, world):
                 "frac": ach / peak, "peak_kind": peak_kind,
                 "traffic": (tpu * d["units"] / d["launches"]) if tpu else None,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": d["ms"] / d["launches"]}
-    total_prof_ms = sum(v["ms"] for v in prof.values())
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_max,
@@ -566,9 +583,7 @@ def run_gpu(args, rank, world):
                 "ms_per_step": e_max},
         "gpu_launches": int(launches),
         "roofline": roof,
-        "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
-                        "share": v["ms"] / total_prof_ms if total_prof_ms else None}
-                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "kernels": kernel_table(prof, args.steps, peak),
         "contraction": contraction_gbs(prof, peak, peak_kind),
         "clocks": clk,
     }

@@ -76,3 +76,16 @@ def test_reference_arm_line_on_cpu():
     assert d["config"]["lambda"] == 23
     assert d["value"] > 0 and d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_kernel_table_shares_and_algorithmic_rates():
+    prof = {"pr_marks": {"ms": 6.0, "units": 3 * 10**9, "launches": 3},
+            "union_find": {"ms": 2.0, "units": 0, "launches": 12}}
+    t = bench.kernel_table(prof, 2, 8000.0)
+    assert list(t) == ["pr_marks", "union_find"]  # by time
+    assert t["pr_marks"]["ms_per_step"] == 3.0 and t["pr_marks"]["share"] == 0.75
+    gbs = 3 * 10**9 * bench.ALG_BYTES["pr_marks"] / 6e-3 / 1e9
+    assert t["pr_marks"]["alg_gbs"] == pytest.approx(gbs)
+    assert t["pr_marks"]["frac"] == pytest.approx(gbs / 8000.0)
+    assert "alg_gbs" not in t["union_find"]  # no algorithmic byte count
+    assert bench.kernel_table({}, 1, 8000.0) == {}
