@@ -147,3 +147,42 @@ def test_size_limits_rejected_before_device_work(lib):
                                    mc.MINCUT_HOST_PTRS, None, None, ctypes.byref(out))
     assert rc == mc.MINCUT_ERR_OVERFLOW and "2^31-1" in mc.mincut_last_error()
     assert not out.value
+
+
+def test_plain_c_program_links_and_calls_the_abi(lib, tmp_path):
+    """The header is plain C99 (no C++), and a C program linked against the
+    library calls it without a GPU: default options, status strings, the
+    n >= 2 rejection and the footprint estimate."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "mincut.h"
+int main(void) {
+    mincut_options o;
+    mincut_default_options(&o);
+    if (o.lp_iters != 2 || o.pr_mask != 0xF) return 1;
+    if (strcmp(mincut_status_string(-99), "unknown status") != 0) return 2;
+    int64_t rp[2] = {0, 0};
+    int32_t c[1] = {0}, w[1] = {0};
+    mincut_graph* g = NULL;
+    if (mincut_graph_from_csr(1, rp, c, w, MINCUT_HOST_PTRS, NULL, NULL, &g) != MINCUT_ERR_INVALID)
+        return 3;
+    if (g != NULL) return 4;
+    if (mincut_graph_footprint(-1, 0) != -1) return 5;
+    printf("ok\n");
+    return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(mc.LIB_PATH)
+    subprocess.check_call([gcc, "-std=c99", "-Wall", "-Werror", "-pedantic",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-lmincut", f"-Wl,-rpath,{libdir}"])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stderr[-500:])
