@@ -202,6 +202,14 @@ def make_workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def arithmetic_desc(g) -> str:
+    """The path's arithmetic for this workload: exact integers, with the sum
+    width the library picks from the total weight of the directed entries."""
+    wide = int(np.asarray(g.w, dtype=np.int64).sum()) > 0x7FFFFFFF
+    return ("int32 weights, exact integer sums (" + ("64-bit" if wide else "32-bit") +
+            " here; 32-bit when the total weight < 2^31, else 64-bit)")
+
+
 def workload_desc(g) -> str:
     return f"{g.meta.get('workload')} (n={g.n}, m={g.m}, seed={g.meta.get('seed')})"
 
@@ -571,7 +579,8 @@ def run_gpu(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_max,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": arithmetic_desc(g),
         "data": "synthetic",
         "config": {"workload": workload_desc(g), "lambda": val,
                    "rounds": statistics.median(rounds), "parallelism": "replicas",

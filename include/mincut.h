@@ -261,12 +261,19 @@ int mincut_profile_read(mincut_graph* g, mincut_profile_entry* out, int32_t cap,
  * edges summed, self-loops and zero weights dropped -- the same result as
  * mincut_contract_round with groups = labels when the labels are numbered
  * by increasing smallest member.
+ * Checked before any other work: row_ptr[0] = 0, row_ptr non-decreasing and
+ * row_ptr[n] = m_directed, labels in [0, n2), columns in [0, n), weights
+ * >= 0 (MINCUT_ERR_INVALID otherwise), and the sum of the M weights at most
+ * 2^31 - 1, so that every contracted weight fits int32
+ * (MINCUT_ERR_OVERFLOW otherwise).
  * Limits: n and M at most 262,144 (MINCUT_ERR_OVERFLOW beyond).  All
  * intermediate data lives in one fixed ~7.2 MB device array inside the
  * library, held by every GPU that loads it until the process exits; the
  * library allocates nothing on this path.  The first call on a device looks
  * up that array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Calls share the array, so calls that
+ * call before any stream capture.  The address is cached per device for the
+ * life of the process: do not use this entry point after cudaDeviceReset on
+ * that device.  Calls share the array, so calls that
  * overlap on the GPU race: serialise them.  Stream-ordered on cuda_stream;
  * returns after the work finished. */
 int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col,

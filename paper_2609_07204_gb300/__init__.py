@@ -459,18 +459,25 @@ def mincut_profile_read(g: Graph, reset: bool = False) -> dict:
 
 
 def mincut_contract_csr_noalloc(n: int, row_ptr, col, w, labels, n2: int, row_ptr_out, col_out,
-                                w_out, *, stream: Any = None) -> int:
+                                w_out, *, m_directed: Optional[int] = None,
+                                stream: Any = None) -> int:
     """Contract a device CSR (torch CUDA tensors) by labels without any device
     allocation inside the library; the caller supplies the output tensors
-    (row_ptr_out int64[n2+1], col_out/w_out int32 with capacity M).  Returns
-    the number of entries written.  See include/mincut.h for the limits."""
+    (row_ptr_out int64[n2+1], col_out/w_out int32 with capacity M).  M is
+    row_ptr[n] unless m_directed is given (the library rejects a mismatch).
+    Returns the number of entries written.  See include/mincut.h for the
+    limits."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream(row_ptr.device).cuda_stream
     if hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
+    if row_ptr.numel() < n + 1 or labels.numel() < n or row_ptr_out.numel() < n2 + 1:
+        raise ValueError("row_ptr needs n + 1, labels n and row_ptr_out n2 + 1 entries")
+    M = int(row_ptr[n].item()) if m_directed is None else int(m_directed)
+    if min(col.numel(), w.numel(), col_out.numel(), w_out.numel()) < M:
+        raise ValueError(f"col, w, col_out and w_out need capacity for M = {M} entries")
     m = ctypes.c_int64(0)
-    M = int(col.numel())
     _check(load_library().mincut_contract_csr_noalloc(
         n, row_ptr.data_ptr(), col.data_ptr(), w.data_ptr(), M, labels.data_ptr(), n2,
         row_ptr_out.data_ptr(), col_out.data_ptr(), w_out.data_ptr(), ctypes.byref(m),

@@ -56,6 +56,7 @@ struct DevState {
   int ndense;                         // contraction: dense groups asked for this round
   int m_rows;                         // contraction: entries of the row-wise contracted graph
   int internal_code;                  // which internal check failed (0: none), for the message
+  unsigned long long wsum;            // input check: sum of the directed entries' weights
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -15,6 +15,7 @@
 // that device current) and caches it.  Every call shares the one array:
 // calls whose work overlaps on the GPU (two streams, two threads) race and
 // must be serialised by the caller.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -57,11 +58,29 @@ int na_fail(int status, const char* msg) {
   return status;
 }
 
-__global__ void labels_check_kernel(const int32_t* __restrict__ lab, int n, int n2, DevState* st) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+// One pass over the caller's arrays before anything else reads them: row
+// offsets non-decreasing, labels in [0, n2), columns in [0, n), weights >= 0
+// (ERR_INPUT otherwise), and the sum of the weights into st->wsum.
+__global__ void input_check_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                   const int32_t* __restrict__ w, const int32_t* __restrict__ lab,
+                                   int n, long long M, int n2, DevState* st) {
+  unsigned long long sum = 0;
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long v = first; v < n; v += stride) {
     const int l = lab[v];
-    if (l < 0 || l >= n2) set_error(st, ERR_INPUT);
+    if (l < 0 || l >= n2 || rp[v] > rp[v + 1]) bad = true;
   }
+  for (long long e = first; e < M; e += stride) {
+    const int c = col[e];
+    const int x = w[e];
+    if (c < 0 || c >= n || x < 0) bad = true;
+    else sum += (unsigned long long)x;
+  }
+  sum = warp_sum(sum);
+  if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&st->wsum, sum);
+  if (bad) set_error(st, ERR_INPUT);
 }
 
 int bits_for_na(long long x) {
@@ -121,15 +140,39 @@ int mincut_contract_csr_noalloc(int64_t n, const int64_t* row_ptr, const int32_t
   const int ni = (int)n, n2i = (int)n2;
   const int vbits = bits_for_na(n2);
 
-  // the status block keeps the previous call's contents: clear it
+  // the row offsets' ends first (host reads): rp[0] = 0 and rp[n] = M
+  int64_t ends[2] = {-1, -1};
+  if (cudaMemcpyAsync(&ends[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&ends[1], row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return na_fail(MINCUT_ERR_CUDA, "reading row_ptr failed");
+  if (ends[0] != 0 || ends[1] != m_directed)
+    return na_fail(MINCUT_ERR_INVALID, "need row_ptr[0] = 0 and row_ptr[n] = m_directed");
+  // the status block keeps the previous call's contents: clear it, then
+  // check the whole input before any kernel relies on it
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess)
     return na_fail(MINCUT_ERR_CUDA, "cudaMemsetAsync failed");
-  labels_check_kernel<<<(ni + 255) / 256, 256, 0, s>>>(labels, ni, n2i, st);
+  {
+    const long long work = std::max<long long>(n, m_directed);
+    const int blocks = (int)std::min<long long>((work + 255) / 256, 1024);
+    input_check_kernel<<<blocks, 256, 0, s>>>(row_ptr, col, w, labels, ni, m_directed, n2i, st);
+  }
+  DevState h;
+  if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return na_fail(MINCUT_ERR_CUDA, "input check failed");
+  if (h.error & ERR_INPUT)
+    return na_fail(MINCUT_ERR_INVALID,
+                   "row_ptr decreasing, or column index, weight or label out of range");
+  if (h.wsum > 0x7fffffffull)
+    return na_fail(MINCUT_ERR_OVERFLOW,
+                   "total weight of the directed entries exceeds 2^31 - 1 (32-bit sums)");
   if (tile_rows(row_ptr, ni, m_directed, tiles, s, &launches) != cudaSuccess ||
       emit_pairs<int32_t>(ni, m_directed, row_ptr, col, w, labels, vbits, tiles, keys0, vals0,
                           st, 1, s, &launches) != cudaSuccess)
     return na_fail(MINCUT_ERR_CUDA, "launch failed (relabel)");
-  DevState h;
   if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return na_fail(MINCUT_ERR_CUDA, "relabel failed");

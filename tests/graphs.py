@@ -117,3 +117,17 @@ def to_nx(n, rp, col, w):
                 else:
                     G.add_edge(u, v, weight=int(w[e]))
     return G
+
+
+def csr_checksum(g) -> str:
+    """Order-dependent 64-bit checksum of a graph's (row_ptr, col, w), as hex:
+    ties a stored value to the exact generator output it was computed on."""
+    h = np.uint64(1469598103934665603)
+    with np.errstate(over="ignore"):
+        for a in (g.row_ptr.astype(np.uint64), g.col.astype(np.uint64), g.w.astype(np.uint64)):
+            idx = np.arange(1, a.size + 1, dtype=np.uint64)
+            h = np.uint64(h * np.uint64(1099511628211)) ^ np.uint64(
+                np.bitwise_xor.reduce(a * np.uint64(0x9E3779B97F4A7C15) +
+                                      idx * np.uint64(0xBF58476D1CE4E5B9)))
+            h = np.uint64(h + np.uint64(a.size))
+    return f"{int(h):016x}"

@@ -712,10 +712,17 @@ def test_solve_rmat20_core_full_size():
 
 @pytest.mark.slow
 def test_solve_planted21_full_size():
-    """Two 2^21-vertex blocks, 25 unit cross edges: lambda = 25 by
-    construction, and the block split is a minimum cut."""
+    """Two 2^21-vertex blocks, 25 unit cross edges (~85 M edges): the value
+    equals the oracle's NOI value stored in tests/golden/planted21_noi.json
+    (computed on this exact graph, identified by its CSR checksum) and the
+    returned side's cut weight equals the value."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "planted21_noi.json")) as f:
+        gold = json.load(f)
     s = synth.workload_planted(21, 42, 30, 25, 3)
+    assert (s.n, s.m) == (gold["n"], gold["m"])
+    assert G.csr_checksum(s) == gold["csr_checksum"]
     c = (s.row_ptr, s.col, s.w)
-    assert s.m > 80_000_000
-    st = _check_solve(s.n, c, mc.default_options(), expect=25)
+    st = _check_solve(s.n, c, mc.default_options(), expect=gold["lambda"])
     assert st["rounds"] >= 1

@@ -1,7 +1,10 @@
 """Serving loop (continuous batching): requests submitted together are
-admitted as workers and memory free up, small ones solved as packed batches,
-and every request's value equals its value solved alone (exact integers);
-each returned side has that cut weight."""
+admitted as workers and memory free up, small ones solved as packed batches.
+Every served value equals the oracle's Stoer-Wagner value of that request
+(the independent exact check of App. C) and its value solved alone (exact
+integers, tolerance 0); each returned side has that cut weight."""
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -26,6 +29,14 @@ def requests_small():
     return [synth.serving_request(5, i, 100, 3000) for i in range(96)]
 
 
+@pytest.fixture(scope="module")
+def oracle_values(requests_small):
+    # the oracle's C code runs with the GIL released: one request per thread
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        return list(ex.map(lambda g: oracle.stoer_wagner(g.n, g.row_ptr, g.col, g.w)[0],
+                           requests_small))
+
+
 def _alone(g):
     G = mc.mincut_graph_from_csr(g.n, g.row_ptr, g.col, g.w)
     v, _, _ = mc.mincut_solve(G)
@@ -33,7 +44,7 @@ def _alone(g):
     return v
 
 
-def test_server_results_equal_alone(requests_small):
+def test_server_results_equal_oracle_and_alone(requests_small, oracle_values):
     S = mc.Server(workers=4, pack_max_n=1500, pack_max_requests=32)
     ids = [S.submit(g.n, g.row_ptr, g.col, g.w) for g in requests_small]
     res = [S.wait(i) for i in ids]
@@ -42,7 +53,8 @@ def test_server_results_equal_alone(requests_small):
     assert st["completed"] == len(requests_small)
     assert st["packed_batches"] >= 1 and st["single_solves"] >= 1
     assert st["peak_inflight"] > 1
-    for g, (v, lat, bm) in zip(requests_small, res):
+    for g, want, (v, lat, bm) in zip(requests_small, oracle_values, res):
+        assert v == want
         assert v == _alone(g)
         side = mc.bitmap_to_side(bm, g.n)
         assert side[0] == 0 and 0 < side.sum() < g.n
@@ -50,7 +62,7 @@ def test_server_results_equal_alone(requests_small):
         assert lat >= 0
 
 
-def test_server_admission_cap_serialises(requests_small):
+def test_server_admission_cap_serialises(requests_small, oracle_values):
     sub = requests_small[:12]
     S = mc.Server(workers=4, hbm_cap_bytes=1, pack_max_requests=1)
     ids = [S.submit(g.n, g.row_ptr, g.col, g.w) for g in sub]
@@ -58,6 +70,7 @@ def test_server_admission_cap_serialises(requests_small):
     st = S.stats()
     S.close()
     assert st["peak_inflight"] == 1  # every request exceeds the cap: one at a time
+    assert vals == oracle_values[:12]
     assert vals == [_alone(g) for g in sub]
 
 
