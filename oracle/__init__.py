@@ -96,6 +96,9 @@ def _load():
     lib.orc_pr_marks.argtypes = [i32, _i64p, _i32p, _i64p, i64, u32, i64, _u8p]
     lib.orc_capforest.argtypes = [i32, _i64p, _i32p, _i64p, i64, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.orc_capforest.restype = i64
+    lib.orc_capforest_tie.argtypes = [i32, _i64p, _i32p, _i64p, i64, i32, i32, vp, vp, vp, vp,
+                                      vp, vp, vp]
+    lib.orc_capforest_tie.restype = i64
     lib.orc_lp.argtypes = [i32, _i64p, _i32p, _i64p, i32, _i32p]
     lib.orc_lp_bound.argtypes = [i32, _i64p, _i32p, _i64p, _i32p, vp]
     lib.orc_lp_bound.restype = i64
@@ -201,8 +204,10 @@ def pr_marks(n, rp, col, w, lam, mask=0xF, budget=-1):
     return fl[:M]
 
 
-def capforest(n, rp, col, w, lam, start=0):
-    """One CAPFOREST pass.  Returns dict(lambda, marks (k,2), order, q, best_len)."""
+def capforest(n, rp, col, w, lam, start=0, tie=0):
+    """One CAPFOREST pass.  Returns dict(lambda, marks (k,2), order, q, best_len).
+    tie 0: ties of highest priority to the smaller vertex id; tie 1: to the
+    first unvisited vertex of the last scanned row, else the smaller id."""
     rp, col, w = _csr(rp, col, w)
     M = int(rp[n])
     mu = np.zeros(M // 2 + 1, np.int32)
@@ -212,9 +217,9 @@ def capforest(n, rp, col, w, lam, start=0):
     ns = np.zeros(1, np.int32)
     q = np.zeros(max(M, 1), np.int64)
     bl = np.zeros(1, np.int32)
-    lam2 = int(_load().orc_capforest(n, rp, col, w, int(min(lam, INF)), start, _ptr(mu),
-                                     _ptr(mv), _ptr(nm), _ptr(order), _ptr(ns), _ptr(q),
-                                     _ptr(bl)))
+    lam2 = int(_load().orc_capforest_tie(n, rp, col, w, int(min(lam, INF)), start, int(tie),
+                                         _ptr(mu), _ptr(mv), _ptr(nm), _ptr(order), _ptr(ns),
+                                         _ptr(q), _ptr(bl)))
     k = int(nm[0])
     return {"lambda": lam2, "marks": np.stack([mu[:k], mv[:k]], axis=1),
             "order": order[:int(ns[0])].copy(), "q": q[:M].copy(), "best_len": int(bl[0])}

@@ -411,10 +411,20 @@ void orc_pr_marks(int32_t n, const int64_t* rp, const int32_t* col, const int64_
  * Note: when alpha lowers lambda, every queued y has r(y) = c(y, S) <= c(S,
  * V \ S) = alpha, so no stored key exceeds the new bound; re-capping the queue
  * at that moment would change nothing. */
-int64_t orc_capforest(int32_t n, const int64_t* rp, const int32_t* col, const int64_t* w,
-                      int64_t lambda, int32_t start, int32_t* mark_u, int32_t* mark_v,
-                      int64_t* nmarks, int32_t* order, int32_t* nscanned, int64_t* q_out,
-                      int32_t* best_len) {
+/* The same pass with a choice of tie rule among the vertices of highest
+ * priority (Sec. 2.1 leaves the order inside a bucket of the bounded priority
+ * queue open -- FIFO, LIFO, heap; any order keeps the pass a maximum-adjacency
+ * ordering and every mark sound):
+ *   tie = 0: the smaller vertex id;
+ *   tie = 1: neighbour first -- after x's row has been scanned, if some
+ *            unvisited y in x's row has the highest priority, the next vertex
+ *            is the first such y in x's row order; otherwise the smaller
+ *            vertex id among those of highest priority.
+ * Everything else is as described above. */
+int64_t orc_capforest_tie(int32_t n, const int64_t* rp, const int32_t* col, const int64_t* w,
+                          int64_t lambda, int32_t start, int32_t tie, int32_t* mark_u,
+                          int32_t* mark_v, int64_t* nmarks, int32_t* order, int32_t* nscanned,
+                          int64_t* q_out, int32_t* best_len) {
     int64_t* deg = (int64_t*)xmalloc((size_t)(n ? n : 1) * sizeof(int64_t));
     orc_degrees(n, rp, col, w, deg);
     int64_t* r = (int64_t*)xcalloc((size_t)(n ? n : 1), sizeof(int64_t));
@@ -426,14 +436,8 @@ int64_t orc_capforest(int32_t n, const int64_t* rp, const int32_t* col, const in
     heap_t h = {0};
     int64_t nm = 0, alpha = 0;
     int32_t ns = 0, blen = 0;
-    if (n > 0) {
-        key[start] = 0;
-        hpush(&h, 0, start);
-    }
-    while (h.n > 0) {
-        hent t = hpop(&h);
-        int32_t x = t.v;
-        if (visited[x] || t.key != key[x]) continue;
+    int32_t x = n > 0 ? start : -1;  /* the next vertex to visit */
+    while (x >= 0) {
         visited[x] = 1;
         if (order) order[ns] = x;
         ++ns;
@@ -454,6 +458,19 @@ int64_t orc_capforest(int32_t n, const int64_t* rp, const int32_t* col, const in
             key[y] = r[y] < lambda ? r[y] : lambda;
             hpush(&h, key[y], y);
         }
+        /* drop stale heap entries: the top is then the highest priority */
+        while (h.n > 0 && (visited[h.a[0].v] || h.a[0].key != key[h.a[0].v])) hpop(&h);
+        if (h.n == 0) break;
+        int64_t top = h.a[0].key;
+        int32_t next = -1;
+        if (tie == 1) {
+            for (int64_t e = rp[x]; e < rp[x + 1]; ++e) {
+                int32_t y = col[e];
+                if (!visited[y] && key[y] == top) { next = y; break; }
+            }
+        }
+        if (next < 0) next = hpop(&h).v;
+        x = next;
     }
     if (nmarks) *nmarks = nm;
     if (nscanned) *nscanned = ns;
@@ -461,6 +478,14 @@ int64_t orc_capforest(int32_t n, const int64_t* rp, const int32_t* col, const in
     free(h.a);
     free(deg); free(r); free(key); free(visited);
     return lambda;
+}
+
+int64_t orc_capforest(int32_t n, const int64_t* rp, const int32_t* col, const int64_t* w,
+                      int64_t lambda, int32_t start, int32_t* mark_u, int32_t* mark_v,
+                      int64_t* nmarks, int32_t* order, int32_t* nscanned, int64_t* q_out,
+                      int32_t* best_len) {
+    return orc_capforest_tie(n, rp, col, w, lambda, start, 0, mark_u, mark_v, nmarks, order,
+                             nscanned, q_out, best_len);
 }
 
 /* ------------------------------------------------ label propagation */

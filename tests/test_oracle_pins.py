@@ -589,3 +589,97 @@ def test_round_iterated_reaches_lambda():
         if info["stopped"]:
             break
     assert lam == s
+
+
+# ------------------------------------------- CAPFOREST, neighbour-first ties
+def test_capforest_neighbour_first_golden_trace():
+    d = gold("capforest_nbr_cycle.json")
+    rp, col, w = G.from_edges(d["n"], d["edges"], d["weights"])
+    r = oracle.capforest(d["n"], rp, col, w, d["lambda_in"], d["start"], tie=1)
+    ex = d["expect"]
+    assert r["lambda"] == ex["lambda_out"]
+    assert r["order"].tolist() == ex["order"]
+    assert r["marks"].tolist() == ex["marks"]
+    assert r["best_len"] == ex["best_len"]
+    for u in range(d["n"]):
+        for e in range(rp[u], rp[u + 1]):
+            v = int(col[e])
+            if r["q"][e] >= 0:
+                assert r["q"][e] == ex["q"][f"{min(u, v)}-{max(u, v)}"]
+    r0 = oracle.capforest(d["n"], rp, col, w, d["lambda_in"], d["start"], tie=0)
+    assert r0["order"].tolist() == d["smaller_id_rule"]["order"]
+    assert r0["marks"].tolist() == d["smaller_id_rule"]["marks"]
+    assert oracle.mincut_brute(d["n"], rp, col, w)[0] == d["mincut"]
+
+
+def test_capforest_neighbour_first_two_triangles():
+    # on the two triangles the neighbour-first rule visits in the same order
+    # as the smaller-id rule (each tie is won by a neighbour of smaller id)
+    d = gold("capforest_two_triangles.json")
+    rp, col, w = G.from_edges(d["n"], d["edges"], d["weights"])
+    r = oracle.capforest(d["n"], rp, col, w, d["lambda_in"], d["start"], tie=1)
+    assert r["order"].tolist() == d["expect"]["order"]
+    assert r["marks"].tolist() == d["expect"]["marks"]
+    assert r["lambda"] == d["expect"]["lambda_out"]
+
+
+def _replay_max_adjacency(n, rp, col, w, lam_in, order, start):
+    """Replays a visit order and checks that every visited vertex had the
+    highest bounded key Q = min(r, lambda) among the unvisited vertices
+    reached so far (lambda lowered by the cuts of proper prefixes); returns
+    the marks (x, y) with r(y) < lambda <= r(y) + c(x, y) in scan order."""
+    r = np.zeros(n, np.int64)
+    deg = oracle.degrees(n, rp, col, w)
+    seen = np.zeros(n, bool)
+    reached = np.zeros(n, bool)
+    reached[start] = True
+    lam, alpha, marks = lam_in, 0, []
+    for i, x in enumerate(order):
+        x = int(x)
+        cand = [v for v in range(n) if reached[v] and not seen[v]]
+        best = max(min(int(r[v]), lam) for v in cand)
+        assert min(int(r[x]), lam) == best and reached[x] and not seen[x]
+        seen[x] = True
+        alpha += int(deg[x]) - 2 * int(r[x])
+        if i + 1 < n and alpha < lam:
+            lam = alpha
+        for e in range(rp[x], rp[x + 1]):
+            y = int(col[e])
+            if seen[y]:
+                continue
+            if r[y] < lam <= r[y] + w[e]:
+                marks.append((x, y))
+            r[y] += w[e]
+            reached[y] = True
+    return lam, marks
+
+
+def test_capforest_neighbour_first_is_max_adjacency_and_sound():
+    """Random graphs: the neighbour-first order is a bounded maximum-adjacency
+    order (replayed independently), the marks are those of that order, each
+    mark (x, y) has lambda(G, x, y) >= the returned bound (brute force), the
+    bound's prefix is a cut of that weight, and contracting the marks keeps
+    min(bound, lambda(G')) = lambda(G)."""
+    rng = np.random.default_rng(23)
+    for trial in range(200):
+        n = int(rng.integers(2, 12))
+        g = G.random_graph(n, float(rng.uniform(0.2, 1.0)), rng, 1, int(rng.integers(1, 9)))
+        rp, col, w = g
+        lam_true, _ = oracle.mincut_brute(n, rp, col, w)
+        lam_in = int(oracle.degrees(n, rp, col, w).min())
+        start = int(rng.integers(0, n))
+        r = oracle.capforest(n, rp, col, w, lam_in, start, tie=1)
+        lam_r, marks_r = _replay_max_adjacency(n, rp, col, w, lam_in, r["order"], start)
+        assert lam_r == r["lambda"]
+        assert [tuple(m) for m in r["marks"].tolist()] == marks_r
+        assert lam_true <= r["lambda"] <= lam_in
+        for x, y in r["marks"]:
+            assert oracle.st_cut_brute(n, rp, col, w, int(x), int(y)) >= r["lambda"]
+        if r["best_len"]:
+            side = np.zeros(n, np.uint8)
+            side[r["order"][:r["best_len"]]] = 1
+            assert oracle.cut_weight(n, rp, col, w, side) == r["lambda"]
+        n2, L = oracle.labels_from_pairs(n, r["marks"][:, 0].copy(), r["marks"][:, 1].copy())
+        rp2, col2, w2 = oracle.contract(n, rp, col, w, L, n2)
+        lam2 = oracle.mincut_brute(n2, rp2, col2, w2)[0] if n2 >= 2 else INF
+        assert min(r["lambda"], lam2) == lam_true
