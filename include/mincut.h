@@ -100,6 +100,13 @@ typedef struct mincut_options {
                                 the others share the batch's round kernels.  0 = auto (chosen
                                 by timing candidate thresholds on the first solve of the batch,
                                 then kept); < 0 = every graph in the round kernels */
+    int32_t seq_kernel;      /* kernel of the whole-graph CAPFOREST passes: 0 (default) one
+                                warp per pass, the next vertex among those of highest priority
+                                taken from the last scanned row when it holds one (else the
+                                smaller id), keys in 1, 2 or 4 bytes as the bound requires, as
+                                many passes as keep their arrays within a share of L2 (or
+                                seq_passes); 1 one thread block per pass, ties to the smaller
+                                id.  Bounds of 2^32 - 1 and more always use 1. */
 } mincut_options;
 
 /* Statistics of a solve (all optional to read). */
@@ -124,8 +131,11 @@ typedef struct mincut_round_options {
     uint32_t pr_mask;
     int64_t pr_budget;
     int32_t capforest;       /* 0 none; 1 concurrent passes (+ sequential pass if no
-                                marks); 2 one sequential pass from cf_start; 3 as 1
-                                with visit sets private to each pass */
+                                marks); 2 one sequential pass from cf_start, ties to the
+                                smaller vertex id; 3 as 1 with visit sets private to each
+                                pass; 4 one sequential pass from cf_start driven by one warp,
+                                ties to the first vertex of the last scanned row that holds
+                                the highest priority, else the smaller id */
     int32_t cf_start;
     int32_t passes, pass_table, waves;
     uint64_t seed;
@@ -136,8 +146,9 @@ typedef struct mincut_round_options {
     const int32_t* pair_v;
     /* optional outputs (host pointers, sized for the round's input graph): */
     uint8_t* pr_flags_out;   /* [M] PR flags (bit0..3 = PR1..PR4) per directed entry */
-    int32_t* cf_order_out;   /* [n] visit order of the sequential pass (capforest == 2) */
-    int32_t* cf_marks_out;   /* [2*cf_marks_cap] marked pairs (x, y) of that pass */
+    int32_t* cf_order_out;   /* [n] visit order of the sequential pass (capforest 2 or 4) */
+    int32_t* cf_marks_out;   /* [2*cf_marks_cap] marked pairs (x, y) of that pass, in scan
+                                order */
     int64_t cf_marks_cap;
     int32_t* lp_labels_out;  /* [n] labels after the LP sweeps (when LP ran) */
 } mincut_round_options;

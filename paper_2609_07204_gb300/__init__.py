@@ -53,7 +53,7 @@ class MincutOptions(ctypes.Structure):
                 ("max_rounds", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
                 ("profile", ctypes.c_int32), ("init_bound", ctypes.c_int32),
                 ("cf_visit", ctypes.c_int32), ("seq_passes", ctypes.c_int32),
-                ("batch_small_n", ctypes.c_int32)]
+                ("batch_small_n", ctypes.c_int32), ("seq_kernel", ctypes.c_int32)]
 
 
 class MincutStats(ctypes.Structure):

@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmincut.so")
-SOURCES = ["sort.cu", "round.cu", "capforest.cu", "capi.cu", "prof.cu", "noalloc.cu", "batch.cu", "server.cu", "contract.cu", "ingest.cu", "batch_warp.cu"]
+SOURCES = ["sort.cu", "round.cu", "capforest.cu", "capi.cu", "prof.cu", "noalloc.cu", "batch.cu", "server.cu", "contract.cu", "ingest.cu", "batch_warp.cu", "capforest_warp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

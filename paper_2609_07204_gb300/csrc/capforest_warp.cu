@@ -1,0 +1,628 @@
+// capforest_warp.cu -- whole-graph CAPFOREST passes, each driven by one warp
+// (the sequential pass of Algorithm 2, run when a round's other marks do not
+// suffice; with several blocks, several such passes from different start
+// vertices at once, each with private keys and visit order).
+//
+// A pass is a bounded maximum-adjacency ordering (Sec. 2.1): repeatedly
+// visit the unvisited vertex x of highest priority Q(x) = min(r(x), lambda),
+// set alpha += c(x) - 2 r(x) (alpha = the cut of the visited set S) and
+// lower lambda to alpha while S != V, then scan x's row: for each unvisited
+// y, if r(y) < lambda <= r(y) + c(x, y) the edge {x, y} is contractible
+// (Algorithm 1's union condition), r(y) += c(x, y).
+//
+// Order among the vertices of highest priority (a free choice, Sec. 2.1):
+// neighbour first -- if some unvisited y of x's row now has the highest
+// priority, the next vertex is the first such y in row order; otherwise the
+// smallest vertex id among the highest.  The CPU oracle's tie = 1 mode
+// implements the same rule, so one pass is comparable entry by entry.
+//
+// Design (one dependent chain of visits per pass, so the chain is short):
+//  * one warp does everything: no block barrier on the path of a visit;
+//  * the queue is a max tree of priorities over the vertices (key =
+//    min(r, lambda) + 1, 0 = not queued): 128 leaves per level-1 node, 32
+//    children per node above, 32-bit nodes in shared memory up to 6.4 M
+//    vertices, so that a key update is one fire-and-forget atomicMax per
+//    level; the leaves are r[] itself, in global memory (L2-resident) or,
+//    for small graphs, in shared memory;
+//  * a single warp pays the full latency of every dependent instruction, so
+//    the chain of a visit is kept short: the row, then the gather of r, row
+//    bounds and degree of its neighbours (L2 prefetch hints were measured to
+//    gain nothing here); x's removal from the tree runs while that gather is
+//    in flight, and yields the highest key without x;
+//    if a neighbour's new key reaches it, that neighbour is next (no tree
+//    descent); only otherwise does the warp descend the tree and read one
+//    group of 128 leaves;
+//  * each vertex is marked at most once per pass (r(y) crosses lambda once),
+//    so marks are kept as mark[y] = x and hooked by a separate grid-wide
+//    kernel after the passes.
+#include <algorithm>
+#include <climits>
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mc {
+
+namespace {
+
+int num_sms_wp() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = kDefaultSms;
+  }
+  return sms;
+}
+
+__device__ __forceinline__ unsigned long long wp_mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// The queue: a max tree of priorities.  A level-1 node holds the largest key
+// of 128 consecutive vertices (key = min(r, lambda) + 1, 0 = not queued);
+// a node of level l + 1 the largest of 32 nodes of level l, up to a level of
+// 32 nodes.  Nodes are 32-bit, so a key update is one fire-and-forget
+// atomicMax per level; with 128 leaves per level-1 node the levels of 6.4 M
+// vertices fit in 200 KB of shared memory.
+constexpr int kLeafShift = 7;                // 128 leaves per level-1 node
+constexpr int kLeafFan = 1 << kLeafShift;
+constexpr int kMaxLev = 6;                   // levels 1..5: enough for 2^31 vertices
+
+struct WTree {
+  int levels;
+  long long size[8];  // nodes of level l, padded to a multiple of 32
+};
+
+__host__ __device__ inline WTree wtree(int n) {
+  WTree t{};
+  long long below = ((long long)n + kLeafFan - 1) / kLeafFan;
+  int l = 1;
+  for (;;) {
+    const long long sz = (below + 31) / 32 * 32;
+    t.size[l] = sz;
+    t.levels = l;
+    if (sz <= 32 || l == kMaxLev - 1) break;
+    below = sz / 32;
+    ++l;
+  }
+  return t;
+}
+
+__device__ __forceinline__ int lev_shift(int l) { return kLeafShift + 5 * (l - 1); }
+
+__device__ __forceinline__ unsigned key_of_wp(long long r, long long lam) {
+  return r > 0 ? (unsigned)((r < lam ? r : lam) + 1) : 0u;
+}
+
+struct WpArgs {
+  int n;
+  long long M;
+  const int64_t* rp;
+  const int* col;
+  const void* w;
+  const void* deg;
+  int start0;               // start vertex of pass 0
+  unsigned long long seed;  // start vertices of the other passes
+  void* r_pool;             // [passes * n] WT, zero (unused when r lives in shared memory)
+  unsigned char* lev_pool;  // tree levels below smem_from, lev_stride bytes per pass, zero
+  long long lev_stride;
+  int* order_pool;          // [passes * n] visit order
+  int* mark_pool;           // [passes * n] marking edge's far end, -1 = none
+  unsigned long long* pass_best;  // [passes] best alpha below the start bound (~0: none)
+  int* pass_len;            // [passes] its prefix length
+  DevState* st;
+  int smem_from;            // tree levels >= smem_from live in shared memory
+  int r_smem;               // r in shared memory
+  long long csr_at;         // byte offset of a shared-memory copy of the CSR (-1: none)
+  int csr_full;             // the copy holds columns and weights too
+};
+
+// x has left the queue and its level-1 node holds the new maximum of its
+// leaves: recompute the ancestors that change (a level whose node keeps its
+// value leaves everything above unchanged).
+__device__ __forceinline__ void tree_remove_up(unsigned* const* lev, int top, int x, int lane) {
+#pragma unroll
+  for (int l = 2; l < kMaxLev; ++l) {
+    if (l > top) break;
+    const int q = x >> lev_shift(l);
+    const unsigned old = *(volatile unsigned*)&lev[l][q];
+    const unsigned nv = __reduce_max_sync(FULL, *(volatile unsigned*)&lev[l - 1][q * 32 + lane]);
+    if (nv == old) break;
+    if (lane == 0) *(volatile unsigned*)&lev[l][q] = nv;
+    __syncwarp();
+  }
+}
+
+// r[] of a pass: in shared memory (RS) or in global memory, read and written
+// at L2 (ld/st .cg) -- one warp owns it, and weak accesses ordered by
+// __syncwarp let the loads of a visit issue without waiting for the previous
+// visit's stores, which volatile accesses would not.
+template <typename WT, bool RS>
+struct RArr {
+  WT* p;
+  __device__ __forceinline__ WT ld(long long i) const { return RS ? p[i] : __ldcg(p + i); }
+  __device__ __forceinline__ void st(long long i, WT v) const {
+    if (RS) p[i] = v;
+    else __stcg(p + i, v);
+  }
+};
+
+// Per-pass state of the driving warp (uniform across its lanes).  AT is the
+// arithmetic type: a graph with 32-bit weights has a total weight below 2^31,
+// so every r, degree, cut and bound of its passes fits 32 bits.
+template <typename AT>
+struct PassState {
+  int x, xb, xe;      // the vertex being visited and its row
+  AT rx, xd;          // its r at the visit and its degree
+  AT lam, alpha;
+  unsigned kt;        // highest key without x, before x's row updates
+  unsigned bk;        // highest key among x's updated neighbours ...
+  int by, bb, be;     // ... the first such neighbour and its row
+  AT br, bd;          // ... its r and degree
+};
+
+// One batch of NCH * 32 entries of x's row: all loads of the batch in flight
+// together, then (first batch only) x's removal from the tree while the
+// gathers are in flight, then the updates.
+template <int NCH, typename WT, bool RS>
+__device__ __forceinline__ void scan_batch(int e0, bool first, PassState<WT>& ps,
+                                           const int* __restrict__ col, const WT* __restrict__ w,
+                                           const int64_t* __restrict__ rp,
+                                           const WT* __restrict__ deg, const RArr<WT, RS> r,
+                                           unsigned* const* lev, int top,
+                                           volatile unsigned* vtop, const WT (&g4)[4],
+                                           int* __restrict__ mark, unsigned& nmarks,
+                                           bool packed) {
+  const int lane = threadIdx.x;
+  int y[NCH];
+  WT c[NCH];
+#pragma unroll
+  for (int u = 0; u < NCH; ++u) {
+    const int e = e0 + u * 32 + lane;
+    y[u] = -1;
+    c[u] = 0;
+    if (e < ps.xe) {
+      y[u] = col[e];
+      c[u] = w[e];
+    }
+  }
+  WT r0[NCH], yd[NCH];
+  int yb[NCH], ye[NCH];
+#pragma unroll
+  for (int u = 0; u < NCH; ++u) {
+    r0[u] = -1;
+    yb[u] = ye[u] = 0;
+    yd[u] = 0;
+    if (y[u] >= 0) {
+      r0[u] = r.ld(y[u]);
+      yb[u] = (int)rp[y[u]];
+      ye[u] = (int)rp[y[u] + 1];
+      yd[u] = deg[y[u]];
+    }
+  }
+  if (first) {
+    unsigned gk = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gk = max(gk, key_of_wp((long long)g4[j], (long long)ps.lam));
+    const unsigned node = __reduce_max_sync(FULL, gk);
+    if (lane == 0) *(volatile unsigned*)&lev[1][ps.x >> kLeafShift] = node;
+    __syncwarp();
+    tree_remove_up(lev, top, ps.x, lane);
+    ps.kt = __reduce_max_sync(FULL, vtop[lane]);
+  }
+  unsigned lbk = 0;
+  int lu = 0;
+#pragma unroll
+  for (int u = 0; u < NCH; ++u) {
+    if (r0[u] >= 0) {
+      const WT r1 = r0[u] + c[u];
+      r.st(y[u], r1);
+      if (r0[u] < ps.lam && ps.lam <= r1) {
+        mark[y[u]] = ps.x;
+        ++nmarks;
+      }
+      const unsigned k1 = (unsigned)(r1 < ps.lam ? r1 : ps.lam) + 1u;
+#pragma unroll
+      for (int l = 1; l < kMaxLev; ++l)
+        if (l <= top) atomicMax(&lev[l][y[u] >> lev_shift(l)], k1);
+      if (k1 > lbk) {  // strictly larger: the earlier entry keeps ties
+        lbk = k1;
+        lu = u;
+      }
+    }
+  }
+  // the batch's first entry with the highest key
+  unsigned km, pos;
+  if (packed) {  // key < 2^25: key and entry position in one reduction
+    const unsigned pk = lbk ? (lbk << 7) | (127u - (unsigned)(lu * 32 + lane)) : 0u;
+    const unsigned m = __reduce_max_sync(FULL, pk);
+    km = m >> 7;
+    pos = 127u - (m & 127u);
+  } else {
+    km = __reduce_max_sync(FULL, lbk);
+    pos = __reduce_min_sync(FULL, (lbk == km && km) ? (unsigned)(lu * 32 + lane) : ~0u);
+  }
+  if (km > ps.bk) {
+    const int wl = (int)(pos & 31);
+    int sy = y[0], sb = yb[0], se = ye[0];
+    WT sr = r0[0] + c[0], sd = yd[0];
+#pragma unroll
+    for (int u = 1; u < NCH; ++u)
+      if (lu == u) {
+        sy = y[u];
+        sb = yb[u];
+        se = ye[u];
+        sr = r0[u] + c[u];
+        sd = yd[u];
+      }
+    ps.bk = km;
+    ps.by = __shfl_sync(FULL, sy, wl);
+    ps.br = __shfl_sync(FULL, sr, wl);
+    ps.bb = __shfl_sync(FULL, sb, wl);
+    ps.be = __shfl_sync(FULL, se, wl);
+    ps.bd = __shfl_sync(FULL, sd, wl);
+  }
+}
+
+template <typename WT, bool RS>
+__global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x;
+  const int k = blockIdx.x;
+  const int n = a.n;
+  const WTree tl = wtree(n);
+  const int top = tl.levels;
+  unsigned* lev[kMaxLev];
+  long long soff = 0, goff = 0;
+  unsigned char* gbase = a.lev_pool + (long long)k * a.lev_stride;
+  lev[0] = nullptr;
+#pragma unroll
+  for (int l = kMaxLev - 1; l >= 1; --l) {
+    lev[l] = nullptr;
+    if (l <= top) {
+      if (l >= a.smem_from) {
+        lev[l] = reinterpret_cast<unsigned*>(smem + soff);
+        soff += tl.size[l] * 4;
+      } else {
+        lev[l] = reinterpret_cast<unsigned*>(gbase + goff);
+        goff += tl.size[l] * 4;
+      }
+    }
+  }
+  soff = (soff + 15) / 16 * 16;
+  const RArr<WT, RS> r{RS ? reinterpret_cast<WT*>(smem + soff)
+                          : reinterpret_cast<WT*>(a.r_pool) + (long long)k * n};
+#pragma unroll
+  for (int l = 1; l < kMaxLev; ++l)
+    if (l <= top && l >= a.smem_from)
+      for (long long i = lane; i < tl.size[l]; i += 32) lev[l][i] = 0;
+  if (RS)
+    for (long long i = lane; i < n; i += 32) r.st(i, 0);
+  const int64_t* rp = a.rp;
+  const int* col = a.col;
+  const WT* w = reinterpret_cast<const WT*>(a.w);
+  const WT* deg = reinterpret_cast<const WT*>(a.deg);
+  if (a.csr_at >= 0) {
+    int64_t* srp = reinterpret_cast<int64_t*>(smem + a.csr_at);
+    WT* sdeg = reinterpret_cast<WT*>(srp + (n + 1));
+    WT* sw = sdeg + n;
+    int* scol = reinterpret_cast<int*>(sw + a.M);
+    for (long long i = lane; i <= n; i += 32) srp[i] = rp[i];
+    for (long long i = lane; i < n; i += 32) sdeg[i] = deg[i];
+    if (a.csr_full) {
+      for (long long i = lane; i < a.M; i += 32) {
+        scol[i] = col[i];
+        sw[i] = w[i];
+      }
+      col = scol;
+      w = sw;
+    }
+    rp = srp;
+    deg = sdeg;
+  }
+  __syncwarp();
+  unsigned* topl = lev[1];
+#pragma unroll
+  for (int l = 2; l < kMaxLev; ++l)
+    if (l == top) topl = lev[l];
+  volatile unsigned* vtop = topl;
+
+  int* order = a.order_pool + (long long)k * n;
+  int* mark = a.mark_pool + (long long)k * n;
+  PassState<WT> ps;
+  ps.lam = (WT)*(volatile unsigned long long*)&a.st->lambda;
+  const bool packed = (unsigned long long)ps.lam < (1ull << 24);
+  ps.alpha = 0;
+  WT best_alpha = -1;
+  int best_len = 0, ns = 0;
+  unsigned nmarks = 0;
+  bool bad = false;
+  ps.x = k == 0 ? a.start0
+                : (int)(wp_mix64(a.seed ^ wp_mix64((unsigned long long)k)) % (unsigned long long)n);
+  ps.rx = 0;
+  ps.xd = deg[ps.x];
+  ps.xb = (int)rp[ps.x];
+  ps.xe = (int)rp[ps.x + 1];
+  for (int it = 0; it < n; ++it) {
+    // ---- visit x
+    if (lane == 0) {
+      r.st(ps.x, (WT)-1);
+      order[ns] = ps.x;
+    }
+    ++ns;
+    ps.alpha += ps.xd - 2 * ps.rx;
+    if (ns < n && ps.alpha < ps.lam) {
+      ps.lam = ps.alpha;
+      best_alpha = ps.alpha;
+      best_len = ns;
+    }
+    // x's group of 128 leaves (without x): loaded now, used once the first
+    // batch's gathers are in flight
+    const int gb = ps.x & ~(kLeafFan - 1);
+    WT g4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = gb + j * 32 + lane;
+      g4[j] = (v < n && v != ps.x) ? r.ld(v) : (WT)-1;
+    }
+    ps.kt = 0;
+    ps.bk = 0;
+    ps.by = -1;
+    ps.bb = ps.be = 0;
+    ps.br = ps.bd = 0;
+    const int len = ps.xe - ps.xb;
+    if (len <= 32) {
+      scan_batch<1, WT, RS>(ps.xb, true, ps, col, w, rp, deg, r, lev, top, vtop, g4, mark, nmarks,
+                        packed);
+    } else if (len <= 64) {
+      scan_batch<2, WT, RS>(ps.xb, true, ps, col, w, rp, deg, r, lev, top, vtop, g4, mark, nmarks,
+                        packed);
+    } else {
+      for (int e0 = ps.xb; e0 < ps.xe; e0 += 128)
+        scan_batch<4, WT, RS>(e0, e0 == ps.xb, ps, col, w, rp, deg, r, lev, top, vtop, g4, mark,
+                          nmarks, packed);
+    }
+    __syncwarp();  // this row's key updates are visible to the next reads
+    // ---- the next vertex: a neighbour holding the highest key, else the
+    // smallest vertex id among the highest
+    if (ps.bk > 0 && ps.bk >= ps.kt) {
+      ps.x = ps.by;
+      ps.rx = ps.br;
+      ps.xb = ps.bb;
+      ps.xe = ps.be;
+      ps.xd = ps.bd;
+      continue;
+    }
+    const unsigned kt = ps.kt;
+    if (kt == 0) break;  // nothing queued: every reachable vertex is visited
+    int idx = __ffs(__ballot_sync(FULL, vtop[lane] == kt)) - 1;
+#pragma unroll
+    for (int l = kMaxLev - 1; l >= 1; --l) {
+      if (l < top && !bad) {
+        const unsigned hb =
+            __ballot_sync(FULL, *(volatile unsigned*)&lev[l][idx * 32 + lane] == kt);
+        if (!hb) bad = true;
+        else idx = idx * 32 + (__ffs(hb) - 1);
+      }
+    }
+    if (bad) break;
+    WT rv[4], dv[4];
+    int bv[4], ev[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = idx * kLeafFan + j * 32 + lane;
+      rv[j] = -1;
+      bv[j] = ev[j] = 0;
+      dv[j] = 0;
+      if (v < n) {
+        rv[j] = r.ld(v);
+        bv[j] = (int)rp[v];
+        ev[j] = (int)rp[v + 1];
+        dv[j] = deg[v];
+      }
+    }
+    int found = -1;
+    WT srv = 0, sdv = 0;
+    int sbv = 0, sev = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned hb = __ballot_sync(FULL, key_of_wp((long long)rv[j], (long long)ps.lam) == kt);
+      if (found < 0 && hb) {
+        found = j * 32 + (__ffs(hb) - 1);
+        srv = rv[j];
+        sbv = bv[j];
+        sev = ev[j];
+        sdv = dv[j];
+      }
+    }
+    if (found < 0) {
+      bad = true;
+      break;
+    }
+    const int wl = found & 31;
+    ps.x = idx * kLeafFan + found;
+    ps.rx = __shfl_sync(FULL, srv, wl);
+    ps.xb = __shfl_sync(FULL, sbv, wl);
+    ps.xe = __shfl_sync(FULL, sev, wl);
+    ps.xd = __shfl_sync(FULL, sdv, wl);
+  }
+  nmarks = warp_sum(nmarks);
+  if (lane == 0) {
+    a.pass_best[k] = best_alpha >= 0 ? (unsigned long long)best_alpha : ~0ull;
+    a.pass_len[k] = best_len;
+    if (best_alpha >= 0) atomicMin(&a.st->lambda, (unsigned long long)best_alpha);
+    if (k == 0) a.st->cf_nscanned = ns;
+    if (nmarks) atomicAdd(&a.st->marks_cf, (unsigned long long)nmarks);
+    if (bad) {
+      set_error(a.st, ERR_INTERNAL);
+      atomicMax(&a.st->internal_code, 41);
+    }
+  }
+}
+
+// Hook every pass's marks: mark_pool[k * n + y] = x >= 0 joins x and y.
+__global__ void wp_hook_kernel(const int* __restrict__ mark_pool, long long total, int n,
+                               int* parent, DevState* st) {
+  bool fail = false;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = mark_pool[i];
+    if (x >= 0 && !uf_union(parent, x, (int)(i % n))) fail = true;
+  }
+  if (fail) set_error(st, ERR_INTERNAL);
+}
+
+// Best pass: the smallest alpha below the start bound (ties: smaller pass)
+// names the witness, cf_pass = -2 - k.
+__global__ void wp_best_kernel(const unsigned long long* __restrict__ pass_best,
+                               const int* __restrict__ pass_len, int passes, DevState* st) {
+  unsigned long long bv = ~0ull;
+  int bp = INT_MAX;
+  for (int p = threadIdx.x; p < passes; p += 32) {
+    const unsigned long long v = pass_best[p];
+    if (v < bv || (v == bv && p < bp)) {
+      bv = v;
+      bp = p;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v2 = __shfl_xor_sync(FULL, bv, o);
+    const int p2 = __shfl_xor_sync(FULL, bp, o);
+    if (v2 < bv || (v2 == bv && p2 < bp)) {
+      bv = v2;
+      bp = p2;
+    }
+  }
+  if (threadIdx.x == 0 && bv != ~0ull) {
+    st->cf_val = bv;
+    st->cf_pass = -2 - bp;
+    st->cf_len = pass_len[bp];
+  }
+}
+
+}  // namespace
+
+// 4 when a pass starting from bound lam fits the 32-bit keys, else 0.
+int warp_pass_key_bytes(long long lam) {
+  return (lam >= 0 && lam <= 0xfffffffell) ? 4 : 0;
+}
+
+long long warp_pass_lev_bytes(int n) {
+  const WTree t = wtree(n);
+  long long b = 0;
+  for (int l = 1; l <= t.levels; ++l) b += t.size[l] * 4;
+  return (b + 255) / 256 * 256;
+}
+
+// Global-memory bytes one pass reads repeatedly (its r[] and the tree
+// levels that stay in global memory): the L2 working set of a pass.
+long long warp_pass_hot_bytes(int n, size_t wt, long long lam) {
+  if (!warp_pass_key_bytes(lam)) return -1;
+  const WTree t = wtree(n);
+  long long lev = 0;
+  for (int l = 1; l <= t.levels; ++l) lev += t.size[l] * 4;
+  const long long rb = (long long)n * (long long)wt;
+  if (lev + rb <= (long long)kWarpPassSmem) return 0;
+  return rb + (lev <= (long long)kWarpPassSmem ? 0 : t.size[1] * 4);
+}
+
+template <typename WT>
+cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const int* col,
+                                  const WT* w, const WT* deg, int passes, int start0,
+                                  unsigned long long seed, long long lam, int* parent,
+                                  WT* r_pool, unsigned char* lev_pool, long long lev_stride,
+                                  int* order_pool, int* mark_pool, unsigned long long* pass_best,
+                                  int* pass_len, DevState* st, cudaStream_t s, int* launches) {
+  if (!warp_pass_key_bytes(lam) || passes < 1 || n < 1) return cudaErrorInvalidValue;
+  const WTree t = wtree(n);
+  // tree levels from the top down while they fit, then r[], then the CSR
+  const size_t limit = kWarpPassSmem;
+  size_t used = 0;
+  int smem_from = t.levels + 1;
+  for (int l = t.levels; l >= 1; --l) {
+    const size_t b = (size_t)t.size[l] * 4;
+    if (used + b > limit) break;
+    used += b;
+    smem_from = l;
+  }
+  long long gl = 0;  // bytes of the global levels of a pass
+  for (int l = 1; l < smem_from; ++l) gl += t.size[l] * 4;
+  if (gl > lev_stride) return cudaErrorInvalidValue;
+  size_t smem = (used + 15) / 16 * 16;
+  int r_smem = 0;
+  if (smem_from == 1 && smem + (size_t)n * sizeof(WT) <= limit) {
+    r_smem = 1;
+    smem += ((size_t)n * sizeof(WT) + 15) / 16 * 16;
+  }
+  long long csr_at = -1;
+  int csr_full = 0;
+  if (r_smem) {
+    for (int full = 1; full >= 0; --full) {
+      const size_t b = (size_t)(n + 1) * 8 + (size_t)n * sizeof(WT) +
+                       (full ? (size_t)M * (sizeof(WT) + 4) : 0);
+      if (smem + b <= limit) {
+        csr_at = (long long)smem;
+        csr_full = full;
+        smem += b;
+        break;
+      }
+    }
+  }
+  if (!r_smem) cudaMemsetAsync(r_pool, 0, (size_t)passes * n * sizeof(WT), s);
+  if (gl > 0) cudaMemsetAsync(lev_pool, 0, (size_t)passes * lev_stride, s);
+  cudaMemsetAsync(mark_pool, 0xff, (size_t)passes * n * sizeof(int), s);
+  WpArgs a{};
+  a.n = n;
+  a.M = M;
+  a.rp = rp;
+  a.col = col;
+  a.w = w;
+  a.deg = deg;
+  a.start0 = start0;
+  a.seed = seed;
+  a.r_pool = r_pool;
+  a.lev_pool = lev_pool;
+  a.lev_stride = lev_stride;
+  a.order_pool = order_pool;
+  a.mark_pool = mark_pool;
+  a.pass_best = pass_best;
+  a.pass_len = pass_len;
+  a.st = st;
+  a.smem_from = smem_from;
+  a.r_smem = r_smem;
+  a.csr_at = csr_at;
+  a.csr_full = csr_full;
+  static bool attr[2][2] = {};
+  const int wi = sizeof(WT) == 8 ? 1 : 0;
+  if (!attr[wi][r_smem]) {
+    cudaFuncSetAttribute(r_smem ? cf_warp_pass_kernel<WT, true> : cf_warp_pass_kernel<WT, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+    attr[wi][r_smem] = true;
+  }
+  if (r_smem) cf_warp_pass_kernel<WT, true><<<passes, 32, smem, s>>>(a);
+  else cf_warp_pass_kernel<WT, false><<<passes, 32, smem, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)passes * n;
+  const int hb = (int)std::min<long long>((total + 255) / 256, (long long)num_sms_wp() * 8);
+  wp_hook_kernel<<<std::max(hb, 1), 256, 0, s>>>(mark_pool, total, n, parent, st);
+  wp_best_kernel<<<1, 32, 0, s>>>(pass_best, pass_len, passes, st);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+#define MC_WP_INST(WT)                                                                        \
+  template cudaError_t capforest_warp_passes<WT>(                                             \
+      int, long long, const int64_t*, const int*, const WT*, const WT*, int, int,              \
+      unsigned long long, long long, int*, WT*, unsigned char*, long long, int*, int*,         \
+      unsigned long long*, int*, DevState*, cudaStream_t, int*);
+MC_WP_INST(int32_t)
+MC_WP_INST(int64_t)
+
+}  // namespace mc

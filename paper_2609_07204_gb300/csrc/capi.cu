@@ -414,12 +414,23 @@ int ensure_rows(mincut_graph* g) {
 // hold (at least 1 when the allocation succeeded, 0 on failure).
 int ensure_seq_multi(mincut_graph* g, int want) {
   if (g->seq_multi_k >= want) return want;
-  if (g->seq_multi_k > 0) return g->seq_multi_k;
   const size_t wsz = g->wt64 ? 8 : 4;
   const long long n = g->n0;
   const long long per = n * (long long)(8 + wsz) + seq_tree_words((int)n) * 8;
   const long long cap = std::max<long long>(1, (2ll << 30) / std::max<long long>(per, 1));
   const int k = (int)std::min<long long>(want, cap);
+  if (k <= g->seq_multi_k) return g->seq_multi_k;
+  if (g->seq_multi_k > 0) {  // grow: the previous buffers go back to the allocator
+    dev_free(g, g->seq_multi_r);
+    dev_free(g, g->seq_multi_tree);
+    dev_free(g, g->seq_multi_order);
+    dev_free(g, g->seq_multi_mark);
+    g->seq_multi_r = nullptr;
+    g->seq_multi_tree = nullptr;
+    g->seq_multi_order = nullptr;
+    g->seq_multi_mark = nullptr;
+    g->seq_multi_k = 0;
+  }
   if (!(g->seq_multi_r = dev_alloc(g, (size_t)k * n * wsz)) ||
       !galloc(g, &g->seq_multi_tree, (long long)k * seq_tree_words((int)n)) ||
       !galloc(g, &g->seq_multi_order, (long long)k * n) ||
@@ -589,8 +600,11 @@ struct RoundCfg {
   uint32_t pr_mask;
   long long pr_budget;
   int capforest;  // 0 none, 1 concurrent (+ sequential fallback), 2 sequential from cf_start
+                  // (block pass, smaller-id ties), 4 one warp-driven pass from cf_start
+                  // (neighbour-first ties)
   int cf_private = 0;  // concurrent passes with private visit sets
-  int seq_passes = 1;  // sequential passes when the concurrent ones mark nothing
+  int seq_passes = 1;  // sequential passes when the concurrent ones mark nothing (0: auto)
+  int seq_kernel = 0;  // 0: warp-driven passes; 1: block passes (smaller-id ties)
   bool coarsen = false;  // heuristic round: also join every label-propagation cluster
   int cf_start;
   int passes, table;
@@ -712,14 +726,78 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   // most) also when it marked so little (fewer edges than n / 64) that
   // contracting would spend a whole round on almost no vertices; its marks
   // only add
-  bool need_seq = c.capforest == 2 ||
+  bool need_seq = c.capforest == 2 || c.capforest == 4 ||
                   (c.capforest == 1 && (marks == 0 || (n <= 8192 && marks * 64 < n)));
+  // whole passes driven by one warp each (the default), when the bound fits
+  // their keys: one pass from cf_start in mode 4, else several from
+  // different start vertices with private arrays, as many as keep their hot
+  // arrays within a share of L2 (all SMs when they live in shared memory)
+  const long long lam_seq = (long long)g->hst->lambda;
+  if (need_seq && lam_seq > 0 && warp_pass_key_bytes(lam_seq) > 0 &&
+      (c.capforest == 4 || (c.capforest == 1 && c.seq_kernel == 0))) {
+    int want = 1;
+    if (c.capforest == 1) {
+      if (c.seq_passes > 0) {
+        want = c.seq_passes;
+      } else {
+        const long long hot = warp_pass_hot_bytes(n, sizeof(WT), lam_seq);
+        want = hot <= 0 ? g->sms : (int)std::max<long long>(1, kWarpPassL2Budget / hot);
+      }
+      want = std::max(1, std::min({want, g->sms, g->max_passes}));
+    }
+    const int k = ensure_seq_multi(g, want);
+    if (k < 1) return fail(MINCUT_ERR_OOM, "sequential pass buffers");
+    const int start = c.capforest == 4 ? c.cf_start : 0;
+    {
+      ProfScope ps(P_CF_SEQ, M, s);
+      CK(capforest_warp_passes<WT>(n, M, rp, col, w, deg, k, start, c.seed, lam_seq, g->parent,
+                                   (WT*)g->seq_multi_r,
+                                   reinterpret_cast<unsigned char*>(g->seq_multi_tree),
+                                   seq_tree_words((int)g->n0) * 8, g->seq_multi_order,
+                                   g->seq_multi_mark, g->pass_best, g->pass_len, g->st, s,
+                                   &g->launches));
+    }
+    rc = sync_state(g);
+    if (rc) return rc;
+    o->seq_pass = true;
+    o->cf_nscanned = g->hst->cf_nscanned;
+    o->cf_nmarks = (long long)g->hst->marks_cf;
+    if (c.capforest == 4 && (c.cf_order_host || c.cf_marks_host)) {
+      // pass 0's visit order, and its marks as (x, y) pairs in scan order:
+      // by x's visit position, then by y (rows are sorted by neighbour)
+      std::vector<int> ord((size_t)o->cf_nscanned), mk((size_t)n);
+      if (o->cf_nscanned > 0)
+        CK(cudaMemcpyAsync(ord.data(), g->seq_multi_order, ord.size() * sizeof(int),
+                           cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(mk.data(), g->seq_multi_mark, (size_t)n * sizeof(int),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (c.cf_order_host && !ord.empty())
+        memcpy(c.cf_order_host, ord.data(), ord.size() * sizeof(int));
+      if (c.cf_marks_host) {
+        std::vector<int> pos((size_t)n, INT32_MAX);
+        for (size_t i = 0; i < ord.size(); ++i) pos[(size_t)ord[i]] = (int)i;
+        std::vector<std::pair<long long, int>> pairs;
+        for (int y = 0; y < n; ++y)
+          if (mk[(size_t)y] >= 0)
+            pairs.push_back({(long long)pos[(size_t)mk[(size_t)y]] * n + y, mk[(size_t)y]});
+        std::sort(pairs.begin(), pairs.end());
+        const long long cap = std::min<long long>(c.cf_marks_cap, (long long)pairs.size());
+        for (long long i = 0; i < cap; ++i) {
+          c.cf_marks_host[2 * i] = pairs[(size_t)i].second;
+          c.cf_marks_host[2 * i + 1] = (int)(pairs[(size_t)i].first % n);
+        }
+      }
+    }
+    need_seq = false;
+  }
   // several whole passes from different start vertices, each with private
   // arrays, when the concurrent passes found nothing (not in the modes that
   // report the single pass's order and marks)
-  if (need_seq && (long long)g->hst->lambda > 0 && c.capforest == 1 && c.seq_passes > 1 &&
+  if (need_seq && (long long)g->hst->lambda > 0 && c.capforest == 1 && c.seq_passes != 1 &&
       !c.cf_marks_host && !c.cf_order_host) {
-    const int k = ensure_seq_multi(g, std::min({c.seq_passes, std::max(2, n / 2), g->max_passes}));
+    const int want = c.seq_passes > 0 ? c.seq_passes : g->sms;
+    const int k = ensure_seq_multi(g, std::min({want, std::max(2, n / 2), g->max_passes}));
     if (k > 1) {
       {
         ProfScope ps(P_CF_SEQ, M, s);
@@ -739,7 +817,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   if (need_seq && (long long)g->hst->lambda > 0) {
     const long long cap = c.cf_marks_host ? std::min(c.cf_marks_cap, M / 2 + 1) : 0;
     int* marks_dev = c.cf_marks_host ? reinterpret_cast<int*>(g->keys[1]) : nullptr;
-    const int start = (c.capforest == 2) ? c.cf_start : 0;
+    const int start = (c.capforest == 2 || c.capforest == 4) ? c.cf_start : 0;
     {
       ProfScope ps(P_CF_SEQ, M, s);
       CK(capforest_sequential<WT>(n, M, rp, col, w, deg, start, g->parent, (WT*)g->seq_r, g->seq_mark,
@@ -936,7 +1014,8 @@ int solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_value,
   c.table = op.pass_table > 0 ? op.pass_table : g->max_table;
   c.table = std::min(c.table, g->max_table);
   c.seed = op.seed;
-  c.seq_passes = op.seq_passes > 0 ? op.seq_passes : g->sms;
+  c.seq_passes = std::max(0, op.seq_passes);
+  c.seq_kernel = op.seq_kernel;
   const bool heuristic = op.init_bound == 1 && op.lp_iters > 0 && g->n0 >= op.lp_min_n;
   if (heuristic) {
     rc = coarsening_bound<WT>(g, op, c, &lambda, &stl);
@@ -1015,7 +1094,7 @@ int contract_round_impl(mincut_graph* g, const mincut_round_options* ro,
   c.capforest = ro->capforest == 3 ? 1 : ro->capforest;
   c.cf_private = ro->capforest == 3 ? 1 : 0;
   c.cf_start = ro->cf_start;
-  if (c.capforest == 2 && (c.cf_start < 0 || c.cf_start >= n))
+  if ((c.capforest == 2 || c.capforest == 4) && (c.cf_start < 0 || c.cf_start >= n))
     return fail(MINCUT_ERR_INVALID, "cf_start out of range");
   c.table = ro->pass_table > 0 ? std::min(ro->pass_table, g->max_table) : g->max_table;
   c.passes = ro->passes > 0 ? ro->passes : std::max(32, std::min(g->max_passes, n / 4));
@@ -1513,7 +1592,7 @@ int mincut_contract_round(mincut_graph* g, const mincut_round_options* ro,
   if (ro->pass_table != 0 && (ro->pass_table < 256 || ro->pass_table > 2048 ||
                               (ro->pass_table & (ro->pass_table - 1))))
     return fail(MINCUT_ERR_INVALID, "pass_table must be a power of two in [256, 2048]");
-  if (ro->capforest < 0 || ro->capforest > 3) return fail(MINCUT_ERR_INVALID, "capforest mode");
+  if (ro->capforest < 0 || ro->capforest > 4) return fail(MINCUT_ERR_INVALID, "capforest mode");
   return g->wt64 ? contract_round_impl<int64_t>(g, ro, res) : contract_round_impl<int32_t>(g, ro, res);
 }
 

@@ -302,6 +302,34 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
                                        const BatchView& bv, DevState* st, cudaStream_t s,
                                        int* launches);
 
+// ------------------------------------------------------ capforest_warp.cu
+// Whole-graph CAPFOREST passes driven by one warp each (block k = pass k,
+// pass 0 from start0, pass k > 0 from a seeded vertex), with private keys and
+// visit order and the neighbour-first tie rule (see the file).  Keys are
+// min(r, lambda) + 1 in 32 bits; warp_pass_key_bytes(lam) == 0 means lam
+// (the bound at launch, which the device state also holds) is too large for
+// these passes.  Scratch per pass: r_pool n WT,
+// lev_pool lev_stride >= warp_pass_lev_bytes(n) bytes, order_pool and
+// mark_pool n ints.  Marks are hooked in parent after the passes; the best
+// alpha goes to st->lambda and, naming its pass (cf_pass = -2 - k, visit
+// order order_pool + k * n), to st->cf_val / cf_len; st->cf_nscanned gets
+// pass 0's visited count.
+constexpr size_t kWarpPassSmem = 200 * 1024;
+// global bytes the simultaneous warp passes of a round may keep hot in L2
+constexpr long long kWarpPassL2Budget = 80ll << 20;
+int warp_pass_key_bytes(long long lam);
+long long warp_pass_lev_bytes(int n);
+// bytes of global memory a pass keeps reading (r and tree levels that do not
+// fit in shared memory); -1 if lam is too large
+long long warp_pass_hot_bytes(int n, size_t wt, long long lam);
+template <typename WT>
+cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const int* col,
+                                  const WT* w, const WT* deg, int passes, int start0,
+                                  unsigned long long seed, long long lam, int* parent,
+                                  WT* r_pool, unsigned char* lev_pool, long long lev_stride,
+                                  int* order_pool, int* mark_pool, unsigned long long* pass_best,
+                                  int* pass_len, DevState* st, cudaStream_t s, int* launches);
+
 // ------------------------------------------------------------- contract.cu
 // Row-wise contraction when most groups are single vertices: singleton rows
 // are rebuilt in place, the rows of multi-member groups (and singleton rows

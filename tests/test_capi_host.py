@@ -34,7 +34,7 @@ def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(mc.MincutStats) == 64
     o = mc.default_options()
     assert (o.lp_iters, o.lp_min_n, o.lp_every_round, o.pr_mask, o.pr_budget) == (2, 10000, 0, 0xF, 16)
-    assert (o.init_bound, o.cf_visit, o.seq_passes, o.batch_small_n) == (0, 0, 0, 0)
+    assert (o.init_bound, o.cf_visit, o.seq_passes, o.batch_small_n, o.seq_kernel) == (0, 0, 0, 0, 0)
     ro = mc.default_round_options()
     assert ro.lambda_in == mc.INT64_MAX and ro.capforest == 1
 

@@ -421,14 +421,15 @@ def test_pr_flags_bit_exact_hub_rows(budget, big):
 
 
 # ------------------------------------------------ deterministic CAPFOREST pass
-def _det_round(n, c, lam_in=INF, start=0, lp_iters=0, lp_min_n=10000, pr_mask=0xF):
+def _det_round(n, c, lam_in=INF, start=0, lp_iters=0, lp_min_n=10000, pr_mask=0xF,
+               capforest=2):
     g = make(n, c[0], c[1], c[2])
     M = int(c[0][-1])
     order = np.zeros(n, np.int32)
     marks = np.zeros(2 * (M // 2 + 1), np.int32)
     ro = mc.default_round_options()
     ro.lambda_in = lam_in
-    ro.capforest = 2
+    ro.capforest = capforest
     ro.cf_start = start
     ro.lp_iters = lp_iters
     ro.lp_min_n = lp_min_n
