@@ -1,11 +1,12 @@
 """Benchmark of the exact minimum-cut solve (one JSON line on rank 0).
 
-Default workload: R-MAT scale 20, edge factor 16, (a, b, c) = (.57, .19, .19),
-unit weights, reduced to its 10-core and largest connected component
-(seed 2): n = 247,314, m = 14,515,608.  A step is one full exact solve
-(every contraction-round kernel: degree bound, label-propagation bound,
-PR1-PR4, CAPFOREST passes, union-find, relabel/sort/segment-sum contraction,
-until lambda is proven) on the graph already resident in HBM.
+Default workload (the largest single-GPU configuration): the planted cut --
+two G(2^21, average degree 42) blocks, each reduced to its 30-core, joined by
+25 unit cross edges, ids permuted (seed 3): n = 4,071,044, m = 84,682,111,
+lambda = 25.  A step is one full exact solve (every contraction-round kernel:
+degree bound, label-propagation bound, PR1-PR4, CAPFOREST passes, union-find,
+relabel/sort/segment-sum contraction, until lambda is proven) on the graph
+already resident in HBM.
 
   value  = input edges m / device time of one solve (CUDA events on the
            graph's stream), whole job (sum over ranks / max time)
@@ -14,21 +15,22 @@ until lambda is proven) on the graph already resident in HBM.
            validation, canonicalisation), the solve and the D2H read of the
            value and the side bitmap
   roofline of the dominant kernel from the library's live CUDA-event profile
-  cpu_baseline = the CPU oracle (sequential NOI) on the same workload
+  cpu_baseline = the CPU oracle (sequential NOI) on a bounded sample of the
+           workload: the same construction at 2^17 vertices per block
+  rmat20 = the R-MAT scale-20 10-core (n = 247,314, m = 14,515,608) measured
+           the same way, with its own roofline
   batched = 4096 small graphs in one packed batch solve vs one at a time
-            (the split between the one-warp-per-graph solver and the shared
-            round kernels as the autotuner chose it, and both paths alone)
   serving = open-loop Poisson request stream through the continuous-batching
             server at 0.5x and 2x the sequential throughput: solves/s,
             p50/p99 latency
   small_config = connected G(2000, 16000) single solve against the CPU
             oracle's Stoer-Wagner and NOI
 
---workload picks the single-graph workload of the main line: rmat20 (the
-default above), rmat18, er2000 (the small configuration) or planted21 (two
-2^21-vertex 30-cores joined by 25 unit edges, ~85 M edges, lambda = 25).
---impl reference times the CPU oracle as the reference arm.  Multi-GPU runs
-(torchrun) are independent replicas: the solve does not shard.
+--workload picks the single-graph workload of the main line: planted21 (the
+default above), rmat20, rmat18 or er2000 (the small configuration).
+--impl reference times the CPU oracle as the reference arm (on the bounded
+sample for planted21).  Multi-GPU runs (torchrun) are independent replicas:
+the solve does not shard.
 """
 from __future__ import annotations
 
@@ -76,6 +78,20 @@ TRAFFIC_PER_UNIT = {
 
 
 CONTRACTION = ("contract_rows", "emit", "sort_hist", "sort_pass", "build_csr")
+
+# Kernel categories bound by one dependent chain of memory accesses rather
+# than by bandwidth: their HBM fraction is reported, with this note.
+LATENCY_BOUND = {
+    "capforest_seq": "latency-bound: one chain of dependent visits per pass (each visit a row "
+                     "load and a gather of its neighbours' keys); the HBM fraction is tiny by "
+                     "construction",
+    "capforest_passes": "latency-bound: one chain of dependent pops per warp",
+}
+
+# Timed steps and end-to-end steps of each main-line workload by default
+# (a planted-cut solve takes seconds; keep the timed work near a minute).
+DEFAULT_STEPS = {"planted21": 3}
+E2E_STEPS = {"planted21": 2}
 
 
 def contraction_gbs(prof, peak, peak_kind):
@@ -199,7 +215,20 @@ def make_workload(name: str):
         return synth.workload_er2000()
     if name == "planted21":
         return synth.workload_planted(21, 42, 30, 25, 3)
+    if name == "planted17":
+        return synth.workload_planted(17, 42, 30, 25, 3)
     raise SystemExit(f"unknown workload {name}")
+
+
+# The bounded CPU sample of each workload: the same construction at a size
+# the single-core oracle solves in seconds (the full planted cut takes the
+# oracle's NOI about two minutes on one core).
+CPU_SAMPLE = {"planted21": "planted17"}
+FULL_DESC = {"planted21": "planted_2x2^21_deg42_30core_cross25 (n=4071044, m=84682111, seed=3)"}
+FULL_ORACLE_NOTE = {
+    "planted21": "oracle NOI on the full workload: 130.9 s on one x86 core "
+                 "(tests/golden/planted21_noi.json, lambda = 25)",
+}
 
 
 def arithmetic_desc(g) -> str:
@@ -214,15 +243,25 @@ def workload_desc(g) -> str:
     return f"{g.meta.get('workload')} (n={g.n}, m={g.m}, seed={g.meta.get('seed')})"
 
 
-def cpu_oracle_time(g, budget_s: float = 30.0):
-    """Time the CPU oracle (sequential NOI) on the workload: one full solve if
-    it fits the budget, else on the largest R-MAT core sample that does."""
+def cpu_oracle_time(name, g, budget_s: float = 30.0):
+    """Time the CPU oracle (sequential NOI, one core) on the workload, or on
+    its bounded sample (CPU_SAMPLE) for workloads too large for a few seconds
+    of CPU; returns the baseline object and the value the oracle found on the
+    graph it ran on (the workload's own lambda when it ran on the workload)."""
     import oracle
+    sample = CPU_SAMPLE.get(name)
+    gs = make_workload(sample) if sample else g
     t0 = time.perf_counter()
-    lam, _, _ = oracle.noi(g.n, g.row_ptr, g.col, g.w)
+    lam, _, _ = oracle.noi(gs.n, gs.row_ptr, gs.col, gs.w)
     dt = time.perf_counter() - t0
-    return {"value": g.m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"one sequential NOI solve of the full workload ({dt:.2f} s, lambda={lam})"}, lam
+    what = (f"one sequential NOI solve of {workload_desc(gs)}, the same construction as the "
+            f"workload at a size one core solves in seconds ({dt:.2f} s, lambda={lam})"
+            if sample else f"one sequential NOI solve of the full workload ({dt:.2f} s, "
+            f"lambda={lam})")
+    out = {"value": gs.m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": what}
+    if name in FULL_ORACLE_NOTE:
+        out["full_workload"] = FULL_ORACLE_NOTE[name]
+    return out, (None if sample else lam)
 
 
 def measure_batched(mc, n_graphs: int = 4096, alone: int = 256, reps: int = 3):
@@ -284,7 +323,7 @@ def measure_batched(mc, n_graphs: int = 4096, alone: int = 256, reps: int = 3):
             "paths": paths}
 
 
-def measure_variants(mc, g, val, reps: int = 3):
+def measure_variants(mc, g, val=None, reps: int = 3):
     """The paper's variants on the same workload: concurrent CAPFOREST passes
     with private visit arrays, the shared/private settings alternated over
     the first rounds, and the coarsening heuristic for the first bound.
@@ -304,6 +343,8 @@ def measure_variants(mc, g, val, reps: int = 3):
             torch.cuda.synchronize()
             ts.append((time.perf_counter() - t0) * 1e3)
             rounds = st["rounds"]
+            if val is None:
+                val = v
             assert v == val, (name, v, val)
         out[name] = {"ms": statistics.median(ts), "rounds": rounds,
                      "lambda_source": st["lambda_source"]}
@@ -464,63 +505,66 @@ def job_rate(world, units_per_rank, ms_max):
 
 
 def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle's sequential NOI (one host core) on the
+    main line's workload -- on its bounded sample (CPU_SAMPLE) where the full
+    workload takes the oracle minutes -- for the same metric and unit."""
     if rank != 0:
         return
     import oracle
-    g = make_workload(args.workload)
+    name = args.workload
+    sample = CPU_SAMPLE.get(name)
+    g = make_workload(sample or name)
+    steps = args.steps if args.steps > 0 else DEFAULT_STEPS.get(name, 5)
     for _ in range(args.warmup):
         pass  # the oracle has no warm state; warm-up steps are not repeated solves
     times = []
     lam = None
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         lam, _, _ = oracle.noi(g.n, g.row_ptr, g.col, g.w)
         times.append(time.perf_counter() - t0)
     t = statistics.mean(times)
     v = g.m / t
+    what = (f"{steps} sequential NOI solves of {workload_desc(g)}, the bounded sample of "
+            f"{name} (same construction, one core)" if sample else
+            f"{steps} sequential NOI solves of the full workload")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": workload_desc(g), "lambda": lam,
+            "config": {"workload": FULL_DESC.get(name, name) if sample else workload_desc(g),
+                       "sample": workload_desc(g) if sample else None, "lambda": lam,
                        "parallelism": "single host thread"},
             "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} sequential NOI solves of the full workload"},
+                             "sample": what},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    if name in FULL_ORACLE_NOTE:
+        line["cpu_baseline"]["full_workload"] = FULL_ORACLE_NOTE[name]
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, rank, world):
+def measure_single(mc, g, steps, warmup, dev, stream, e2e_steps):
+    """One single-graph workload: warm-up solves, then `steps` timed solves on
+    the resident graph (CUDA events on the graph's stream, a 256 MB buffer
+    written between steps to flush L2, nvidia-smi clocks sampled during the
+    timed region), the live per-kernel profile of the timed solves, and the
+    end-to-end time through the public API from pinned host arrays."""
     import torch
-
-    import paper_2609_07204_gb300 as mc
-    dev = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream()
-    g = make_workload(args.workload)
-    M = g.M
     G = mc.mincut_graph_from_csr(g.n, g.row_ptr, g.col, g.w, stream=stream.cuda_stream)
     opts = mc.default_options(profile=1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=f"cuda:{dev}")
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         val, _, _ = mc.mincut_solve(G, opts, bitmap=False)
     mc.mincut_profile_read(G, reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     clocks = ClockSampler(dev)
     launches = 0
     rounds = []
-    barrier()
     torch.cuda.synchronize()
     clocks.start()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.fill_(i)  # write 256 MB (> L2) between steps, outside the timed events
         with torch.cuda.stream(stream):
             stream.wait_stream(torch.cuda.current_stream())
@@ -530,18 +574,16 @@ def run_gpu(args, rank, world):
         launches += st["kernel_launches"]
         rounds.append(st["rounds"])
     torch.cuda.synchronize()
-    barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     prof = mc.mincut_profile_read(G, reset=True)
-    ms = statistics.mean(step_ms)
-
-    # ---- end-to-end through the public API with host buffers
+    G.destroy()
+    # ---- end to end through the public API with host buffers
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
     col_h = torch.from_numpy(g.col).pin_memory()
     w_h = torch.from_numpy(g.w).pin_memory()
     e2e_ms = []
-    for i in range(args.steps + 1):
+    for i in range(e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G2 = mc.mincut_graph_from_csr(g.n, rp_h.numpy(), col_h.numpy(), w_h.numpy(),
@@ -552,60 +594,105 @@ def run_gpu(args, rank, world):
         if i > 0:  # first call warms the allocator pool
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
         assert v2 == val
-    e2e = statistics.mean(e2e_ms)
-    G.destroy()
+    return {"val": val, "ms": statistics.mean(step_ms), "step_ms": step_ms,
+            "e2e_ms": statistics.mean(e2e_ms), "prof": prof, "launches": launches,
+            "rounds": statistics.median(rounds), "clocks": clk,
+            "h2d": int(g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes),
+            "d2h": int(8 * ((g.n + 63) // 64) + 8)}
 
-    # ---- reduce over ranks (replicas)
-    t_max, e_max = ms, e2e
+
+def roofline_of(prof, peak, peak_kind):
+    """Roofline object of the dominant kernel category (longest CUDA-event
+    time among those with an algorithmic byte count): algorithmic bytes per
+    launch over its average launch time, against the measured HBM peak."""
+    kern = {k: v for k, v in prof.items() if k in ALG_BYTES and v["launches"] > 0}
+    if not kern:
+        return None
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    alg_bytes = d["units"] * ALG_BYTES[dom] / d["launches"]
+    avg_s = d["ms"] / d["launches"] / 1e3
+    ach = alg_bytes / avg_s / 1e9
+    tpu = TRAFFIC_PER_UNIT.get(dom)
+    out = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+           "frac": ach / peak, "peak_kind": peak_kind,
+           "traffic": (tpu * d["units"] / d["launches"]) if tpu else None,
+           "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": d["ms"] / d["launches"]}
+    if dom in LATENCY_BOUND:
+        out["note"] = LATENCY_BOUND[dom]
+    return out
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    import paper_2609_07204_gb300 as mc
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    g = make_workload(args.workload)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    barrier()
+    steps = args.steps if args.steps > 0 else DEFAULT_STEPS.get(args.workload, 5)
+    e2e_steps = max(1, min(steps, E2E_STEPS.get(args.workload, steps)))
+    r = measure_single(mc, g, steps, args.warmup, dev, stream, e2e_steps)
+    barrier()
+    t_max, e_max = r["ms"], r["e2e_ms"]
     if world > 1:
-        t_max, e_max = reduce_max_over_ranks([ms, e2e], f"cuda:{dev}")
+        t_max, e_max = reduce_max_over_ranks([r["ms"], r["e2e_ms"]], f"cuda:{dev}")
     if rank != 0:
         return
+    val = r["val"]
     value = job_rate(world, g.m, t_max)
     peak, peak_kind = load_peaks()
-    kern = {k: v for k, v in prof.items() if k in ALG_BYTES}
-    dom = max(kern, key=lambda k: kern[k]["ms"]) if kern else None
-    roof = None
-    if dom:
-        d = kern[dom]
-        alg_bytes = d["units"] * ALG_BYTES[dom] / d["launches"]
-        avg_s = d["ms"] / d["launches"] / 1e3
-        ach = alg_bytes / avg_s / 1e9
-        tpu = TRAFFIC_PER_UNIT.get(dom)
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": peak_kind,
-                "traffic": (tpu * d["units"] / d["launches"]) if tpu else None,
-                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": d["ms"] / d["launches"]}
+    prof = r["prof"]
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_max,
+        "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": t_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": arithmetic_desc(g),
         "data": "synthetic",
         "config": {"workload": workload_desc(g), "lambda": val,
-                   "rounds": statistics.median(rounds), "parallelism": "replicas",
+                   "rounds": r["rounds"], "parallelism": "replicas",
                    "l2": "256 MB buffer written between steps, outside the timed events; "
-                         "input CSR 234 MB > L2"},
+                         f"input CSR {(g.col.nbytes + g.w.nbytes) >> 20} MB > L2"},
         "e2e": {"value": job_rate(world, g.m, e_max), "unit": "edges/s",
-                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes),
-                "d2h_bytes_per_step": int(8 * ((g.n + 63) // 64) + 8),
-                "ms_per_step": e_max},
-        "gpu_launches": int(launches),
-        "roofline": roof,
-        "kernels": kernel_table(prof, args.steps, peak),
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
+                "ms_per_step": e_max, "steps": e2e_steps},
+        "gpu_launches": int(r["launches"]),
+        "roofline": roofline_of(prof, peak, peak_kind),
+        "kernels": kernel_table(prof, steps, peak),
         "contraction": contraction_gbs(prof, peak, peak_kind),
-        "clocks": clk,
+        "clocks": r["clocks"],
     }
+    if not args.no_extra and args.workload != "rmat20":
+        g2 = make_workload("rmat20")
+        r2 = measure_single(mc, g2, 5, 3, dev, stream, 3)
+        line["rmat20"] = {
+            "workload": workload_desc(g2), "lambda": r2["val"],
+            "value": g2.m / (r2["ms"] / 1e3), "unit": "edges/s", "ms_per_step": r2["ms"],
+            "steps": 5, "rounds": r2["rounds"],
+            "e2e": {"value": g2.m / (r2["e2e_ms"] / 1e3), "ms_per_step": r2["e2e_ms"],
+                    "h2d_bytes_per_step": r2["h2d"], "d2h_bytes_per_step": r2["d2h"]},
+            "roofline": roofline_of(r2["prof"], peak, peak_kind),
+            "kernels": kernel_table(r2["prof"], 5, peak),
+            "contraction": contraction_gbs(r2["prof"], peak, peak_kind),
+            "clocks": r2["clocks"]}
     if not args.no_extra:
         line["batched"] = measure_batched(mc)
         line["serving"] = measure_serving(mc)
-        line["variants"] = measure_variants(mc, g, val)
+        line["variants"] = measure_variants(mc, make_workload("rmat20"))
         line["small_config"] = measure_small_config(mc)
         if not args.no_cpu_baseline:
             line["adversarial"] = measure_adversarial(mc)
     if not args.no_cpu_baseline:
-        cb, lam = cpu_oracle_time(g)
-        assert lam == val, (lam, val)
+        cb, lam = cpu_oracle_time(args.workload, g)
+        assert lam is None or lam == val, (lam, val)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
 
@@ -613,10 +700,11 @@ def run_gpu(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (0: 3 for planted21, 5 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--workload", default="planted21")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and serving measurements")
