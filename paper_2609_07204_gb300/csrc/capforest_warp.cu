@@ -109,7 +109,8 @@ struct WpArgs {
   const void* deg;
   int start0;               // start vertex of pass 0
   unsigned long long seed;  // start vertices of the other passes
-  void* r_pool;             // [passes * n] WT, zero (unused when r lives in shared memory)
+  void* r_pool;             // [passes * n] (r, row start) pairs of WT (set by wp_init_kernel;
+                            // unused when they live in shared memory)
   unsigned char* lev_pool;  // tree levels below smem_from, lev_stride bytes per pass, zero
   long long lev_stride;
   int* order_pool;          // [passes * n] visit order
@@ -139,90 +140,70 @@ __device__ __forceinline__ void tree_remove_up(unsigned* const* lev, int top, in
   }
 }
 
-// r[] of a pass: in shared memory (RS) or in global memory, read and written
-// at L2 (ld/st .cg) -- one warp owns it, and weak accesses ordered by
-// __syncwarp let the loads of a visit issue without waiting for the previous
-// visit's stores, which volatile accesses would not.
+// Per-vertex state of a pass, one vector word per vertex so that a
+// neighbour's gather is a single load: r (the connection to the visited set;
+// -1 once visited) and the vertex's row start.  8 bytes for 32-bit weights,
+// 16 for 64-bit.  In shared memory (RS) or in global memory, read and written
+// at L2 (ld/st .cg): one warp owns it, and weak accesses ordered by
+// __syncwarp let a visit's loads issue without waiting for the previous
+// visit's stores.
+template <typename WT>
+struct RRT;
+template <>
+struct RRT<int32_t> {
+  using V = int2;
+};
+template <>
+struct RRT<int64_t> {
+  using V = longlong2;
+};
+
 template <typename WT, bool RS>
 struct RArr {
-  WT* p;
-  __device__ __forceinline__ WT ld(long long i) const { return RS ? p[i] : __ldcg(p + i); }
-  __device__ __forceinline__ void st(long long i, WT v) const {
-    if (RS) p[i] = v;
-    else __stcg(p + i, v);
+  using V = typename RRT<WT>::V;
+  V* p;
+  __device__ __forceinline__ V ld(long long i) const { return RS ? p[i] : __ldcg(p + i); }
+  __device__ __forceinline__ WT ld_r(long long i) const {
+    return RS ? p[i].x : __ldcg(reinterpret_cast<const WT*>(p + i));
+  }
+  __device__ __forceinline__ void st_r(long long i, WT v) const {
+    if (RS) p[i].x = v;
+    else __stcg(reinterpret_cast<WT*>(p + i), v);
   }
 };
 
-// Per-pass state of the driving warp (uniform across its lanes).  AT is the
-// arithmetic type: a graph with 32-bit weights has a total weight below 2^31,
-// so every r, degree, cut and bound of its passes fits 32 bits.
-template <typename AT>
+// Per-pass state of the driving warp (uniform across its lanes).  A graph
+// with 32-bit weights has a total weight below 2^31, so every r, degree, cut
+// and bound of its passes fits the weight type WT.
+template <typename WT>
 struct PassState {
   int x, xb, xe;      // the vertex being visited and its row
-  AT rx, xd;          // its r at the visit and its degree
-  AT lam, alpha;
+  WT rx, xd;          // its r at the visit and its degree
+  WT lam, alpha;
   unsigned kt;        // highest key without x, before x's row updates
   unsigned bk;        // highest key among x's updated neighbours ...
-  int by, bb, be;     // ... the first such neighbour and its row
-  AT br, bd;          // ... its r and degree
+  int by, bb;         // ... the first such neighbour and its row start
+  WT br;              // ... its r
 };
 
-// One batch of NCH * 32 entries of x's row: all loads of the batch in flight
-// together, then (first batch only) x's removal from the tree while the
-// gathers are in flight, then the updates.
+// Updates of one chunk set of x's row: entries y[u] (-1: none) with weights
+// c[u] and gathered state (r0[u], yb[u]): r, marks, tree, and the first entry
+// with the highest new key.
 template <int NCH, typename WT, bool RS>
-__device__ __forceinline__ void scan_batch(int e0, bool first, PassState<WT>& ps,
-                                           const int* __restrict__ col, const WT* __restrict__ w,
-                                           const int64_t* __restrict__ rp,
-                                           const WT* __restrict__ deg, const RArr<WT, RS> r,
-                                           unsigned* const* lev, int top,
-                                           volatile unsigned* vtop, const WT (&g4)[4],
-                                           int* __restrict__ mark, unsigned& nmarks,
-                                           bool packed) {
+__device__ __forceinline__ void apply_batch(PassState<WT>& ps, const int (&y)[NCH],
+                                            const WT (&c)[NCH], const WT (&r0)[NCH],
+                                            const int (&yb)[NCH], const RArr<WT, RS> rr,
+                                            unsigned* const* lev, int top,
+                                            int* __restrict__ mark, unsigned& nmarks,
+                                            bool packed) {
   const int lane = threadIdx.x;
-  int y[NCH];
-  WT c[NCH];
-#pragma unroll
-  for (int u = 0; u < NCH; ++u) {
-    const int e = e0 + u * 32 + lane;
-    y[u] = -1;
-    c[u] = 0;
-    if (e < ps.xe) {
-      y[u] = col[e];
-      c[u] = w[e];
-    }
-  }
-  WT r0[NCH], yd[NCH];
-  int yb[NCH], ye[NCH];
-#pragma unroll
-  for (int u = 0; u < NCH; ++u) {
-    r0[u] = -1;
-    yb[u] = ye[u] = 0;
-    yd[u] = 0;
-    if (y[u] >= 0) {
-      r0[u] = r.ld(y[u]);
-      yb[u] = (int)rp[y[u]];
-      ye[u] = (int)rp[y[u] + 1];
-      yd[u] = deg[y[u]];
-    }
-  }
-  if (first) {
-    unsigned gk = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) gk = max(gk, key_of_wp((long long)g4[j], (long long)ps.lam));
-    const unsigned node = __reduce_max_sync(FULL, gk);
-    if (lane == 0) *(volatile unsigned*)&lev[1][ps.x >> kLeafShift] = node;
-    __syncwarp();
-    tree_remove_up(lev, top, ps.x, lane);
-    ps.kt = __reduce_max_sync(FULL, vtop[lane]);
-  }
   unsigned lbk = 0;
   int lu = 0;
 #pragma unroll
   for (int u = 0; u < NCH; ++u) {
-    if (r0[u] >= 0) {
+    if (y[u] >= 0 && r0[u] >= 0) {
       const WT r1 = r0[u] + c[u];
-      r.st(y[u], r1);
+      rr.st_r(y[u], r1);
       if (r0[u] < ps.lam && ps.lam <= r1) {
         mark[y[u]] = ps.x;
         ++nmarks;
@@ -237,7 +218,6 @@ __device__ __forceinline__ void scan_batch(int e0, bool first, PassState<WT>& ps
       }
     }
   }
-  // the batch's first entry with the highest key
   unsigned km, pos;
   if (packed) {  // key < 2^25: key and entry position in one reduction
     const unsigned pk = lbk ? (lbk << 7) | (127u - (unsigned)(lu * 32 + lane)) : 0u;
@@ -250,29 +230,42 @@ __device__ __forceinline__ void scan_batch(int e0, bool first, PassState<WT>& ps
   }
   if (km > ps.bk) {
     const int wl = (int)(pos & 31);
-    int sy = y[0], sb = yb[0], se = ye[0];
-    WT sr = r0[0] + c[0], sd = yd[0];
+    int sy = y[0], sb = yb[0];
+    WT sr = r0[0] + c[0];
 #pragma unroll
     for (int u = 1; u < NCH; ++u)
       if (lu == u) {
         sy = y[u];
         sb = yb[u];
-        se = ye[u];
         sr = r0[u] + c[u];
-        sd = yd[u];
       }
     ps.bk = km;
     ps.by = __shfl_sync(FULL, sy, wl);
     ps.br = __shfl_sync(FULL, sr, wl);
     ps.bb = __shfl_sync(FULL, sb, wl);
-    ps.be = __shfl_sync(FULL, se, wl);
-    ps.bd = __shfl_sync(FULL, sd, wl);
+  }
+}
+
+// Gather of NCH chunks: r and row start of each valid entry's vertex.
+template <int NCH, typename WT, bool RS>
+__device__ __forceinline__ void gather_batch(const int (&y)[NCH], WT (&r0)[NCH], int (&yb)[NCH],
+                                             const RArr<WT, RS> rr) {
+#pragma unroll
+  for (int u = 0; u < NCH; ++u) {
+    r0[u] = -1;
+    yb[u] = 0;
+    if (y[u] >= 0) {
+      const typename RRT<WT>::V v = rr.ld(y[u]);
+      r0[u] = (WT)v.x;
+      yb[u] = (int)v.y;
+    }
   }
 }
 
 template <typename WT, bool RS>
 __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  using V = typename RRT<WT>::V;
   const int lane = threadIdx.x;
   const int k = blockIdx.x;
   const int n = a.n;
@@ -296,18 +289,23 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     }
   }
   soff = (soff + 15) / 16 * 16;
-  const RArr<WT, RS> r{RS ? reinterpret_cast<WT*>(smem + soff)
-                          : reinterpret_cast<WT*>(a.r_pool) + (long long)k * n};
+  const RArr<WT, RS> rr{RS ? reinterpret_cast<V*>(smem + soff)
+                           : reinterpret_cast<V*>(a.r_pool) + (long long)k * n};
 #pragma unroll
   for (int l = 1; l < kMaxLev; ++l)
     if (l <= top && l >= a.smem_from)
       for (long long i = lane; i < tl.size[l]; i += 32) lev[l][i] = 0;
-  if (RS)
-    for (long long i = lane; i < n; i += 32) r.st(i, 0);
   const int64_t* rp = a.rp;
   const int* col = a.col;
   const WT* w = reinterpret_cast<const WT*>(a.w);
   const WT* deg = reinterpret_cast<const WT*>(a.deg);
+  if (RS)  // global r_pool entries are set by wp_init_kernel
+    for (long long i = lane; i < n; i += 32) {
+      V v;
+      v.x = 0;
+      v.y = (WT)rp[i];
+      rr.p[i] = v;
+    }
   if (a.csr_at >= 0) {
     int64_t* srp = reinterpret_cast<int64_t*>(smem + a.csr_at);
     WT* sdeg = reinterpret_cast<WT*>(srp + (n + 1));
@@ -333,6 +331,7 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     if (l == top) topl = lev[l];
   volatile unsigned* vtop = topl;
 
+  const int M = (int)a.M;
   int* order = a.order_pool + (long long)k * n;
   int* mark = a.mark_pool + (long long)k * n;
   PassState<WT> ps;
@@ -346,13 +345,34 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
   ps.x = k == 0 ? a.start0
                 : (int)(wp_mix64(a.seed ^ wp_mix64((unsigned long long)k)) % (unsigned long long)n);
   ps.rx = 0;
-  ps.xd = deg[ps.x];
   ps.xb = (int)rp[ps.x];
-  ps.xe = (int)rp[ps.x + 1];
   for (int it = 0; it < n; ++it) {
-    // ---- visit x
+    // ---- visit x: its first 64 row entries, row end and degree in one round
+    // trip (the row start came with x's gather)
+    int y[2];
+    WT c[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = ps.xb + u * 32 + lane;
+      y[u] = -1;
+      c[u] = 0;
+      if (e < M) {
+        y[u] = col[e];
+        c[u] = w[e];
+      }
+    }
+    ps.xe = (int)rp[ps.x + 1];
+    ps.xd = deg[ps.x];
+    // x's group of 128 leaves without x, for x's removal from the tree
+    const int gb = ps.x & ~(kLeafFan - 1);
+    WT g4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = gb + j * 32 + lane;
+      g4[j] = (v < n && v != ps.x) ? rr.ld_r(v) : (WT)-1;
+    }
     if (lane == 0) {
-      r.st(ps.x, (WT)-1);
+      rr.st_r(ps.x, (WT)-1);
       order[ns] = ps.x;
     }
     ++ns;
@@ -362,41 +382,54 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
       best_alpha = ps.alpha;
       best_len = ns;
     }
-    // x's group of 128 leaves (without x): loaded now, used once the first
-    // batch's gathers are in flight
-    const int gb = ps.x & ~(kLeafFan - 1);
-    WT g4[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int v = gb + j * 32 + lane;
-      g4[j] = (v < n && v != ps.x) ? r.ld(v) : (WT)-1;
+    for (int u = 0; u < 2; ++u)
+      if (ps.xb + u * 32 + lane >= ps.xe) y[u] = -1;
+    WT r0[2];
+    int yb[2];
+    gather_batch<2, WT, RS>(y, r0, yb, rr);
+    // x leaves the queue (while the gather is in flight): its level-1 node
+    // and the ancestors that change; then the highest key without x
+    {
+      unsigned gk = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) gk = max(gk, key_of_wp((long long)g4[j], (long long)ps.lam));
+      const unsigned node = __reduce_max_sync(FULL, gk);
+      if (lane == 0) *(volatile unsigned*)&lev[1][ps.x >> kLeafShift] = node;
+      __syncwarp();
+      tree_remove_up(lev, top, ps.x, lane);
+      ps.kt = __reduce_max_sync(FULL, vtop[lane]);
     }
-    ps.kt = 0;
     ps.bk = 0;
     ps.by = -1;
-    ps.bb = ps.be = 0;
-    ps.br = ps.bd = 0;
-    const int len = ps.xe - ps.xb;
-    if (len <= 32) {
-      scan_batch<1, WT, RS>(ps.xb, true, ps, col, w, rp, deg, r, lev, top, vtop, g4, mark, nmarks,
-                        packed);
-    } else if (len <= 64) {
-      scan_batch<2, WT, RS>(ps.xb, true, ps, col, w, rp, deg, r, lev, top, vtop, g4, mark, nmarks,
-                        packed);
-    } else {
-      for (int e0 = ps.xb; e0 < ps.xe; e0 += 128)
-        scan_batch<4, WT, RS>(e0, e0 == ps.xb, ps, col, w, rp, deg, r, lev, top, vtop, g4, mark,
-                          nmarks, packed);
+    ps.bb = 0;
+    ps.br = 0;
+    apply_batch<2, WT, RS>(ps, y, c, r0, yb, rr, lev, top, mark, nmarks, packed);
+    // the rest of a long row, 128 entries per batch
+    for (int e0 = ps.xb + 64; e0 < ps.xe; e0 += 128) {
+      int y4[4];
+      WT c4[4], r4[4];
+      int b4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * 32 + lane;
+        y4[u] = -1;
+        c4[u] = 0;
+        if (e < ps.xe) {
+          y4[u] = col[e];
+          c4[u] = w[e];
+        }
+      }
+      gather_batch<4, WT, RS>(y4, r4, b4, rr);
+      apply_batch<4, WT, RS>(ps, y4, c4, r4, b4, rr, lev, top, mark, nmarks, packed);
     }
-    __syncwarp();  // this row's key updates are visible to the next reads
+    __syncwarp();  // this row's updates are visible to the next reads
     // ---- the next vertex: a neighbour holding the highest key, else the
     // smallest vertex id among the highest
     if (ps.bk > 0 && ps.bk >= ps.kt) {
       ps.x = ps.by;
       ps.rx = ps.br;
       ps.xb = ps.bb;
-      ps.xe = ps.be;
-      ps.xd = ps.bd;
       continue;
     }
     const unsigned kt = ps.kt;
@@ -412,24 +445,22 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
       }
     }
     if (bad) break;
-    WT rv[4], dv[4];
-    int bv[4], ev[4];
+    WT rv[4];
+    int bv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int v = idx * kLeafFan + j * 32 + lane;
       rv[j] = -1;
-      bv[j] = ev[j] = 0;
-      dv[j] = 0;
+      bv[j] = 0;
       if (v < n) {
-        rv[j] = r.ld(v);
-        bv[j] = (int)rp[v];
-        ev[j] = (int)rp[v + 1];
-        dv[j] = deg[v];
+        const V q = rr.ld(v);
+        rv[j] = (WT)q.x;
+        bv[j] = (int)q.y;
       }
     }
     int found = -1;
-    WT srv = 0, sdv = 0;
-    int sbv = 0, sev = 0;
+    WT srv = 0;
+    int sbv = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const unsigned hb = __ballot_sync(FULL, key_of_wp((long long)rv[j], (long long)ps.lam) == kt);
@@ -437,8 +468,6 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
         found = j * 32 + (__ffs(hb) - 1);
         srv = rv[j];
         sbv = bv[j];
-        sev = ev[j];
-        sdv = dv[j];
       }
     }
     if (found < 0) {
@@ -449,8 +478,6 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     ps.x = idx * kLeafFan + found;
     ps.rx = __shfl_sync(FULL, srv, wl);
     ps.xb = __shfl_sync(FULL, sbv, wl);
-    ps.xe = __shfl_sync(FULL, sev, wl);
-    ps.xd = __shfl_sync(FULL, sdv, wl);
   }
   nmarks = warp_sum(nmarks);
   if (lane == 0) {
@@ -463,6 +490,20 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
       set_error(a.st, ERR_INTERNAL);
       atomicMax(&a.st->internal_code, 41);
     }
+  }
+}
+
+// Global per-vertex state of every pass: r = 0, row start from rp.
+template <typename WT>
+__global__ void wp_init_kernel(typename RRT<WT>::V* __restrict__ pool, int passes, int n,
+                               const int64_t* __restrict__ rp) {
+  const long long total = (long long)passes * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    typename RRT<WT>::V v;
+    v.x = 0;
+    v.y = (WT)rp[i % n];
+    pool[i] = v;
   }
 }
 
@@ -527,7 +568,7 @@ long long warp_pass_hot_bytes(int n, size_t wt, long long lam) {
   const WTree t = wtree(n);
   long long lev = 0;
   for (int l = 1; l <= t.levels; ++l) lev += t.size[l] * 4;
-  const long long rb = (long long)n * (long long)wt;
+  const long long rb = (long long)n * 2 * (long long)wt;
   if (lev + rb <= (long long)kWarpPassSmem) return 0;
   return rb + (lev <= (long long)kWarpPassSmem ? 0 : t.size[1] * 4);
 }
@@ -556,9 +597,9 @@ cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const i
   if (gl > lev_stride) return cudaErrorInvalidValue;
   size_t smem = (used + 15) / 16 * 16;
   int r_smem = 0;
-  if (smem_from == 1 && smem + (size_t)n * sizeof(WT) <= limit) {
+  if (smem_from == 1 && smem + (size_t)n * 2 * sizeof(WT) <= limit) {
     r_smem = 1;
-    smem += ((size_t)n * sizeof(WT) + 15) / 16 * 16;
+    smem += ((size_t)n * 2 * sizeof(WT) + 15) / 16 * 16;
   }
   long long csr_at = -1;
   int csr_full = 0;
@@ -574,7 +615,13 @@ cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const i
       }
     }
   }
-  if (!r_smem) cudaMemsetAsync(r_pool, 0, (size_t)passes * n * sizeof(WT), s);
+  if (!r_smem) {
+    const long long total = (long long)passes * n;
+    const int ib = (int)std::min<long long>((total + 255) / 256, (long long)num_sms_wp() * 8);
+    wp_init_kernel<WT><<<std::max(ib, 1), 256, 0, s>>>(
+        reinterpret_cast<typename RRT<WT>::V*>(r_pool), passes, n, rp);
+    ++*launches;
+  }
   if (gl > 0) cudaMemsetAsync(lev_pool, 0, (size_t)passes * lev_stride, s);
   cudaMemsetAsync(mark_pool, 0xff, (size_t)passes * n * sizeof(int), s);
   WpArgs a{};

@@ -416,7 +416,7 @@ int ensure_seq_multi(mincut_graph* g, int want) {
   if (g->seq_multi_k >= want) return want;
   const size_t wsz = g->wt64 ? 8 : 4;
   const long long n = g->n0;
-  const long long per = n * (long long)(8 + wsz) + seq_tree_words((int)n) * 8;
+  const long long per = n * (long long)(8 + 2 * wsz) + seq_tree_words((int)n) * 8;
   const long long cap = std::max<long long>(1, (2ll << 30) / std::max<long long>(per, 1));
   const int k = (int)std::min<long long>(want, cap);
   if (k <= g->seq_multi_k) return g->seq_multi_k;
@@ -431,7 +431,7 @@ int ensure_seq_multi(mincut_graph* g, int want) {
     g->seq_multi_mark = nullptr;
     g->seq_multi_k = 0;
   }
-  if (!(g->seq_multi_r = dev_alloc(g, (size_t)k * n * wsz)) ||
+  if (!(g->seq_multi_r = dev_alloc(g, (size_t)k * n * 2 * wsz)) ||
       !galloc(g, &g->seq_multi_tree, (long long)k * seq_tree_words((int)n)) ||
       !galloc(g, &g->seq_multi_order, (long long)k * n) ||
       !galloc(g, &g->seq_multi_mark, (long long)k * n))
@@ -740,8 +740,13 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
       if (c.seq_passes > 0) {
         want = c.seq_passes;
       } else {
+        // passes are independent chains on separate SMs: more of them cost
+        // little time and mark more edges, so large graphs collapse in one
+        // such round (measured on the planted cut: 4 passes leave one round
+        // of whole passes, 2 leave two); the L2 share only raises the count
         const long long hot = warp_pass_hot_bytes(n, sizeof(WT), lam_seq);
-        want = hot <= 0 ? g->sms : (int)std::max<long long>(1, kWarpPassL2Budget / hot);
+        want = hot <= 0 ? g->sms
+                        : (int)std::max<long long>(kWarpPassMin, kWarpPassL2Budget / hot);
       }
       want = std::max(1, std::min({want, g->sms, g->max_passes}));
     }

@@ -308,7 +308,7 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
 // visit order and the neighbour-first tie rule (see the file).  Keys are
 // min(r, lambda) + 1 in 32 bits; warp_pass_key_bytes(lam) == 0 means lam
 // (the bound at launch, which the device state also holds) is too large for
-// these passes.  Scratch per pass: r_pool n WT,
+// these passes.  Scratch per pass: r_pool 2n WT,
 // lev_pool lev_stride >= warp_pass_lev_bytes(n) bytes, order_pool and
 // mark_pool n ints.  Marks are hooked in parent after the passes; the best
 // alpha goes to st->lambda and, naming its pass (cf_pass = -2 - k, visit
@@ -317,6 +317,8 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
 constexpr size_t kWarpPassSmem = 200 * 1024;
 // global bytes the simultaneous warp passes of a round may keep hot in L2
 constexpr long long kWarpPassL2Budget = 80ll << 20;
+// passes a round runs at least (device memory and SMs permitting)
+constexpr int kWarpPassMin = 8;
 int warp_pass_key_bytes(long long lam);
 long long warp_pass_lev_bytes(int n);
 // bytes of global memory a pass keeps reading (r and tree levels that do not
