@@ -27,7 +27,9 @@ already resident in HBM.
             oracle's Stoer-Wagner and NOI
 
 --workload picks the single-graph workload of the main line: planted21 (the
-default above), rmat20, rmat18 or er2000 (the small configuration).
+default above), planted18 / planted17 (the same construction at 2^18 / 2^17
+vertices per block, for profiling), rmat20, rmat18 or er2000 (the small
+configuration).
 --impl reference times the CPU oracle as the reference arm (on the bounded
 sample for planted21).  Multi-GPU runs (torchrun) are independent replicas:
 the solve does not shard.
@@ -217,6 +219,8 @@ def make_workload(name: str):
         return synth.workload_planted(21, 42, 30, 25, 3)
     if name == "planted17":
         return synth.workload_planted(17, 42, 30, 25, 3)
+    if name == "planted18":
+        return synth.workload_planted(18, 42, 30, 25, 3)
     raise SystemExit(f"unknown workload {name}")
 
 
