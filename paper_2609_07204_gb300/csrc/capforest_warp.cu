@@ -246,6 +246,78 @@ __device__ __forceinline__ void apply_batch(PassState<WT>& ps, const int (&y)[NC
   }
 }
 
+// The first entry with the highest new key among NCH chunks (no side
+// effects; commit_batch then applies the same updates).
+template <int NCH, typename WT>
+__device__ __forceinline__ void best_batch(PassState<WT>& ps, const int (&y)[NCH],
+                                           const WT (&c)[NCH], const WT (&r0)[NCH],
+                                           const int (&yb)[NCH], bool packed) {
+  const int lane = threadIdx.x;
+  unsigned lbk = 0;
+  int lu = 0;
+#pragma unroll
+  for (int u = 0; u < NCH; ++u) {
+    if (y[u] >= 0 && r0[u] >= 0) {
+      const WT r1 = r0[u] + c[u];
+      const unsigned k1 = (unsigned)(r1 < ps.lam ? r1 : ps.lam) + 1u;
+      if (k1 > lbk) {
+        lbk = k1;
+        lu = u;
+      }
+    }
+  }
+  unsigned km, pos;
+  if (packed) {
+    const unsigned pk = lbk ? (lbk << 7) | (127u - (unsigned)(lu * 32 + lane)) : 0u;
+    const unsigned m = __reduce_max_sync(FULL, pk);
+    km = m >> 7;
+    pos = 127u - (m & 127u);
+  } else {
+    km = __reduce_max_sync(FULL, lbk);
+    pos = __reduce_min_sync(FULL, (lbk == km && km) ? (unsigned)(lu * 32 + lane) : ~0u);
+  }
+  if (km > ps.bk) {
+    const int wl = (int)(pos & 31);
+    int sy = y[0], sb = yb[0];
+    WT sr = r0[0] + c[0];
+#pragma unroll
+    for (int u = 1; u < NCH; ++u)
+      if (lu == u) {
+        sy = y[u];
+        sb = yb[u];
+        sr = r0[u] + c[u];
+      }
+    ps.bk = km;
+    ps.by = __shfl_sync(FULL, sy, wl);
+    ps.br = __shfl_sync(FULL, sr, wl);
+    ps.bb = __shfl_sync(FULL, sb, wl);
+  }
+}
+
+// The updates of NCH chunks: r, marks and the tree.
+template <int NCH, typename WT, bool RS>
+__device__ __forceinline__ void commit_batch(const PassState<WT>& ps, const int (&y)[NCH],
+                                             const WT (&c)[NCH], const WT (&r0)[NCH],
+                                             const RArr<WT, RS> rr, unsigned* const* lev,
+                                             int top, int* __restrict__ mark,
+                                             unsigned& nmarks) {
+#pragma unroll
+  for (int u = 0; u < NCH; ++u) {
+    if (y[u] >= 0 && r0[u] >= 0) {
+      const WT r1 = r0[u] + c[u];
+      rr.st_r(y[u], r1);
+      if (r0[u] < ps.lam && ps.lam <= r1) {
+        mark[y[u]] = ps.x;
+        ++nmarks;
+      }
+      const unsigned k1 = (unsigned)(r1 < ps.lam ? r1 : ps.lam) + 1u;
+#pragma unroll
+      for (int l = 1; l < kMaxLev; ++l)
+        if (l <= top) atomicMax(&lev[l][y[u] >> lev_shift(l)], k1);
+    }
+  }
+}
+
 // Gather of NCH chunks: r and row start of each valid entry's vertex.
 template <int NCH, typename WT, bool RS>
 __device__ __forceinline__ void gather_batch(const int (&y)[NCH], WT (&r0)[NCH], int (&yb)[NCH],
@@ -346,23 +418,39 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
                 : (int)(wp_mix64(a.seed ^ wp_mix64((unsigned long long)k)) % (unsigned long long)n);
   ps.rx = 0;
   ps.xb = (int)rp[ps.x];
+  // the next vertex's first 64 row entries, row end and degree, loaded
+  // ahead when the next vertex was known before x's updates were committed
+  bool pre = false;
+  int ny[2] = {-1, -1};
+  WT nc[2] = {0, 0};
+  int nxe = 0;
+  WT nxd = 0;
   for (int it = 0; it < n; ++it) {
     // ---- visit x: its first 64 row entries, row end and degree in one round
     // trip (the row start came with x's gather)
     int y[2];
     WT c[2];
+    if (pre) {
+      y[0] = ny[0];
+      y[1] = ny[1];
+      c[0] = nc[0];
+      c[1] = nc[1];
+      ps.xe = nxe;
+      ps.xd = nxd;
+    } else {
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e = ps.xb + u * 32 + lane;
-      y[u] = -1;
-      c[u] = 0;
-      if (e < M) {
-        y[u] = col[e];
-        c[u] = w[e];
+      for (int u = 0; u < 2; ++u) {
+        const int e = ps.xb + u * 32 + lane;
+        y[u] = -1;
+        c[u] = 0;
+        if (e < M) {
+          y[u] = col[e];
+          c[u] = w[e];
+        }
       }
+      ps.xe = (int)rp[ps.x + 1];
+      ps.xd = deg[ps.x];
     }
-    ps.xe = (int)rp[ps.x + 1];
-    ps.xd = deg[ps.x];
     // x's group of 128 leaves without x, for x's removal from the tree
     const int gb = ps.x & ~(kLeafFan - 1);
     WT g4[4];
@@ -404,7 +492,36 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     ps.by = -1;
     ps.bb = 0;
     ps.br = 0;
-    apply_batch<2, WT, RS>(ps, y, c, r0, yb, rr, lev, top, mark, nmarks, packed);
+    best_batch<2, WT>(ps, y, c, r0, yb, packed);
+    // a row of at most 64 entries whose best neighbour holds the highest key:
+    // that neighbour is next, and its row loads go out before this row's
+    // updates are committed
+    const bool single = ps.xe - ps.xb <= 64;
+    const bool fast = single && ps.bk > 0 && ps.bk >= ps.kt;
+    if (fast) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = ps.bb + u * 32 + lane;
+        ny[u] = -1;
+        nc[u] = 0;
+        if (e < M) {
+          ny[u] = col[e];
+          nc[u] = w[e];
+        }
+      }
+      nxe = (int)rp[ps.by + 1];
+      nxd = deg[ps.by];
+    }
+    commit_batch<2, WT, RS>(ps, y, c, r0, rr, lev, top, mark, nmarks);
+    if (fast) {
+      __syncwarp();  // this row's updates are visible to the next reads
+      ps.x = ps.by;
+      ps.rx = ps.br;
+      ps.xb = ps.bb;
+      pre = true;
+      continue;
+    }
+    pre = false;
     // the rest of a long row, 128 entries per batch
     for (int e0 = ps.xb + 64; e0 < ps.xe; e0 += 128) {
       int y4[4];

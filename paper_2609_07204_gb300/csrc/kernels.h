@@ -318,7 +318,7 @@ constexpr size_t kWarpPassSmem = 200 * 1024;
 // global bytes the simultaneous warp passes of a round may keep hot in L2
 constexpr long long kWarpPassL2Budget = 80ll << 20;
 // passes a round runs at least (device memory and SMs permitting)
-constexpr int kWarpPassMin = 8;
+constexpr int kWarpPassMin = 4;
 int warp_pass_key_bytes(long long lam);
 long long warp_pass_lev_bytes(int n);
 // bytes of global memory a pass keeps reading (r and tree levels that do not
