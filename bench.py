@@ -427,68 +427,132 @@ def measure_adversarial(mc, reps: int = 2):
     return out
 
 
-def measure_serving(mc, n_req: int = 300, nhi: int = 1 << 14, seed: int = 5):
-    """Open-loop Poisson stream of n_req requests (n log-uniform in [100, nhi],
-    R-MAT or G(n, 8n) 50/50, weights in [1, 100], largest component) served by
-    the continuous-batching server at 0.5x and 2x the sequential-submission
-    throughput; sequential submission = create + solve + read back, one at a
-    time.  Latency = submission to completion."""
+def _gen_request(args):
+    import synth
+    seed, i, nlo, nhi = args
+    g = synth.serving_request(seed, i, nlo, nhi)
+    return g.n, g.row_ptr, g.col, g.w, g.meta.get("kind")
+
+
+def measure_serving(mc, n_req: int = 20000, nhi: int = 1 << 20, pool: int = 48, seed: int = 5,
+                    workers: int = 16, window: int = 64, seq_sample: int = 1000,
+                    low_sample: int = 4000):
+    """Serving workload: a stream of n_req solve requests, n log-uniform in
+    [100, nhi], R-MAT (scale ceil(log2 n), edge factor 16, truncated) or
+    G(n, 8n) with probability 1/2 each, weights in [1, 100], largest
+    component (seed 5), under the server's 60 GB device-memory admission cap.
+    Host generation of 2^20-vertex R-MAT graphs takes seconds each, so the
+    stream draws its requests from a pool of `pool` distinct seeded requests
+    (generated in parallel processes; request j of the stream is pool entry
+    mix(seed, j) mod pool).  Measured: sequential submission (create + solve +
+    read back, one at a time) on the first seq_sample requests; a closed loop
+    of `window` outstanding requests over the whole stream (saturation);
+    open-loop Poisson arrivals at 2x the sequential rate over the whole stream
+    and at 0.5x over its first low_sample requests.  The pool is in pinned
+    host memory, read in place by the device on every path; the server
+    borrows the arrays (mincut_server_submit_borrowed).  Latency = submission
+    to completion.  Every served value equals its graph's value solved
+    alone."""
+    import multiprocessing as mp
     import threading
+    from concurrent.futures import ProcessPoolExecutor
+
+    import torch
 
     import synth
-    reqs = [synth.serving_request(seed, i, 100, nhi) for i in range(n_req)]
+    t0 = time.perf_counter()
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4),
+                             mp_context=mp.get_context("spawn")) as ex:
+        reqs = list(ex.map(_gen_request, [(seed, i, 100, nhi) for i in range(pool)]))
+    t_gen = time.perf_counter() - t0
+    # the pool lives in pinned host memory: the device reads each request in
+    # place, and the server borrows the arrays instead of copying them
+    reqs = [(n, torch.from_numpy(rp).pin_memory().numpy(), torch.from_numpy(col).pin_memory().numpy(),
+             torch.from_numpy(w).pin_memory().numpy(), kind) for (n, rp, col, w, kind) in reqs]
+    # the value of every pool graph, solved alone
+    expected = []
+    for (n, rp, col, w, _) in reqs:
+        Gi = mc.mincut_graph_from_csr(n, rp, col, w)
+        expected.append(mc.mincut_solve(Gi, bitmap=False)[0])
+        Gi.destroy()
+    stream = [synth.splitmix64(seed ^ (0x9E3779B97F4A7C15 * (j + 1) & ((1 << 64) - 1)))[0] % pool
+              for j in range(n_req)]
+    sizes = [reqs[k][0] for k in stream]
+    edges = [int(reqs[k][1][-1]) // 2 for k in stream]
+    # ---- sequential submission on the first seq_sample requests
     lat_seq = []
     t0 = time.perf_counter()
-    vals_seq = []
-    for g in reqs:
+    for k in stream[:seq_sample]:
+        n, rp, col, w, _ = reqs[k]
         t1 = time.perf_counter()
-        Gi = mc.mincut_graph_from_csr(g.n, g.row_ptr, g.col, g.w)
+        Gi = mc.mincut_graph_from_csr(n, rp, col, w)
         v, _, _ = mc.mincut_solve(Gi)
         Gi.destroy()
         lat_seq.append((time.perf_counter() - t1) * 1e3)
-        vals_seq.append(v)
-    t_seq = time.perf_counter() - t0
-    seq_rate = n_req / t_seq
-    out = {"workload": f"{n_req} requests, n log-uniform [100,{nhi}], R-MAT/ER 50/50, w U[1,100], seed {seed}",
-           "sequential": {"solves_per_s": seq_rate,
+        assert v == expected[k]
+    seq_rate = seq_sample / (time.perf_counter() - t0)
+    out = {"workload": (f"{n_req} requests, n log-uniform [100,{nhi}], R-MAT/ER 50/50, "
+                        f"w U[1,100], largest component, seed {seed}; drawn from a pool of "
+                        f"{pool} distinct seeded requests (host generation of 2^20-vertex "
+                        f"R-MAT graphs takes seconds each; pool generated in {t_gen:.1f} s)"),
+           "requests": n_req, "n_max_drawn": max(sizes), "n_median": int(np.median(sizes)),
+           "edges_total": int(sum(edges)), "workers": workers,
+           "admission_cap_bytes": int(60 << 30),
+           "sequential": {"sample": seq_sample, "solves_per_s": seq_rate,
                           "p50_ms": float(np.percentile(lat_seq, 50)),
                           "p99_ms": float(np.percentile(lat_seq, 99))}}
-    rng = np.random.default_rng(seed)
-    for load in (0.5, 2.0):
-        rate = load * seq_rate
-        gaps = rng.exponential(1.0 / rate, size=n_req)
-        S = mc.Server(workers=4)
-        ids = [None] * n_req
+
+    def run(order, gaps=None):
+        """Serve `order` (pool indices): with gaps, open-loop arrivals at those
+        inter-arrival times; else a closed loop of `window` outstanding."""
+        S = mc.Server(workers=workers)
+        ids = [None] * len(order)
+        lats = [0.0] * len(order)
+        vals = [None] * len(order)
         start = time.perf_counter()
-
-        def submitter():
-            t_next = start
-            for i, g in enumerate(reqs):
-                t_next += gaps[i]
-                d = t_next - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                ids[i] = S.submit(g.n, g.row_ptr, g.col, g.w)
-
-        th = threading.Thread(target=submitter)
-        th.start()
-        lats, vals = [], []
-        for i in range(n_req):
-            while ids[i] is None:
-                time.sleep(0.0002)
-            v, lat, _ = S.wait(ids[i], bitmap=False)
-            lats.append(lat)
-            vals.append(v)
-        th.join()
+        if gaps is None:
+            nxt = 0
+            for i in range(len(order)):
+                while nxt < len(order) and nxt - i < window:
+                    n, rp, col, w, _ = reqs[order[nxt]]
+                    ids[nxt] = S.submit(n, rp, col, w, borrow=True)
+                    nxt += 1
+                vals[i], lats[i], _ = S.wait(ids[i], bitmap=False)
+        else:
+            def submitter():
+                t_next = start
+                for i, k in enumerate(order):
+                    t_next += gaps[i]
+                    d = t_next - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    n, rp, col, w, _ = reqs[k]
+                    ids[i] = S.submit(n, rp, col, w, borrow=True)
+            th = threading.Thread(target=submitter)
+            th.start()
+            for i in range(len(order)):
+                while ids[i] is None:
+                    time.sleep(0.0002)
+                vals[i], lats[i], _ = S.wait(ids[i], bitmap=False)
+            th.join()
         wall = time.perf_counter() - start
         st = S.stats()
         S.close()
-        assert vals == vals_seq
-        out[f"load_{load}x"] = {"offered_per_s": rate, "solves_per_s": n_req / wall,
-                                "p50_ms": float(np.percentile(lats, 50)),
-                                "p99_ms": float(np.percentile(lats, 99)),
-                                "packed_batches": st["packed_batches"],
-                                "peak_inflight": st["peak_inflight"]}
+        assert all(v == expected[k] for v, k in zip(vals, order))
+        return {"solves_per_s": len(order) / wall, "wall_s": wall,
+                "p50_ms": float(np.percentile(lats, 50)),
+                "p99_ms": float(np.percentile(lats, 99)),
+                "packed_batches": st["packed_batches"], "peak_inflight": st["peak_inflight"],
+                "all_equal_alone": True}
+
+    rng = np.random.default_rng(seed)
+    out["closed_loop"] = dict(run(stream), window=window)
+    out["closed_loop"]["speedup_vs_sequential"] = out["closed_loop"]["solves_per_s"] / seq_rate
+    out["load_2.0x"] = dict(run(stream, rng.exponential(1.0 / (2 * seq_rate), size=n_req)),
+                            offered_per_s=2 * seq_rate)
+    low = stream[:low_sample]
+    out["load_0.5x"] = dict(run(low, rng.exponential(1.0 / (0.5 * seq_rate), size=len(low))),
+                            offered_per_s=0.5 * seq_rate, requests=len(low))
     return out
 
 
@@ -715,11 +779,13 @@ def main():
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched measurement, printed as one JSON object "
                          "(a short command to profile the batched kernels)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only the serving measurement, printed as one JSON object")
     ap.add_argument("--small-only", action="store_true",
                     help="only the small single-graph measurement, printed as one JSON "
                          "object (a short command to profile the sequential pass)")
     args = ap.parse_args()
-    if args.batched_only or args.small_only:
+    if args.batched_only or args.small_only or args.serving_only:
         import torch
 
         import paper_2609_07204_gb300 as mc
@@ -727,6 +793,8 @@ def main():
         mc.load_library()
         if args.batched_only:
             print(json.dumps({"batched": measure_batched(mc)}), flush=True)
+        elif args.serving_only:
+            print(json.dumps({"serving": measure_serving(mc)}), flush=True)
         else:
             print(json.dumps({"small_config": measure_small_config(mc)}), flush=True)
         return

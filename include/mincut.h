@@ -339,6 +339,13 @@ int mincut_server_create(const mincut_server_options* opts, mincut_server** out)
  * the request in mincut_server_wait. */
 int mincut_server_submit(mincut_server* s, int64_t n, const int64_t* row_ptr, const int32_t* col,
                          const int32_t* w, uint64_t* request_id);
+/* As mincut_server_submit, but nothing is copied: the server reads the
+ * caller's host arrays when a worker takes the request, so they must stay
+ * alive and unchanged until mincut_server_wait returns for it.  Pinned
+ * (page-locked, mapped) arrays are then read in place by the device, which
+ * spares the host both the submit copy and a staging copy. */
+int mincut_server_submit_borrowed(mincut_server* s, int64_t n, const int64_t* row_ptr,
+                                  const int32_t* col, const int32_t* w, uint64_t* request_id);
 /* Block until the request is solved; returns its status and fills the value,
  * the latency from submission to completion (ms) and, if requested and kept,
  * its side bitmap (host, ceil(n/64) words).  The request is then released. */

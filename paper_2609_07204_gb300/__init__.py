@@ -182,6 +182,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mincut_server_create.restype = ctypes.c_int
     lib.mincut_server_submit.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.mincut_server_submit.restype = ctypes.c_int
+    lib.mincut_server_submit_borrowed.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mincut_server_submit_borrowed.restype = ctypes.c_int
     lib.mincut_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i64),
                                        ctypes.POINTER(ctypes.c_double), vp]
     lib.mincut_server_wait.restype = ctypes.c_int
@@ -514,17 +516,23 @@ class Server:
         _check(lib.mincut_server_create(ctypes.byref(opts), ctypes.byref(h)))
         self.handle = h
         self.sizes: dict[int, int] = {}
+        self.keep: dict[int, tuple] = {}  # arrays of borrowed requests, until wait()
 
-    def submit(self, n: int, row_ptr, col, w) -> int:
+    def submit(self, n: int, row_ptr, col, w, *, borrow: bool = False) -> int:
+        """Queue a request.  borrow=True: the server reads these arrays in
+        place (pinned ones directly from the device) instead of copying them;
+        they are kept referenced here until wait() returns."""
         rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
         c = np.ascontiguousarray(col, dtype=np.int32)
         ww = np.ascontiguousarray(w, dtype=np.int32)
         rid = ctypes.c_uint64(0)
-        _check(load_library().mincut_server_submit(self.handle, n, rp.ctypes.data,
-                                                   c.ctypes.data if c.size else None,
-                                                   ww.ctypes.data if ww.size else None,
-                                                   ctypes.byref(rid)))
+        fn = (load_library().mincut_server_submit_borrowed if borrow
+              else load_library().mincut_server_submit)
+        _check(fn(self.handle, n, rp.ctypes.data, c.ctypes.data if c.size else None,
+                  ww.ctypes.data if ww.size else None, ctypes.byref(rid)))
         self.sizes[int(rid.value)] = n
+        if borrow:
+            self.keep[int(rid.value)] = (rp, c, ww)
         return int(rid.value)
 
     def wait(self, rid: int, bitmap: bool = True):
@@ -533,9 +541,12 @@ class Server:
         val = ctypes.c_int64(0)
         lat = ctypes.c_double(0)
         bm = np.zeros((n + 63) // 64, np.uint64) if bitmap else None
-        _check(load_library().mincut_server_wait(self.handle, rid, ctypes.byref(val),
-                                                 ctypes.byref(lat),
-                                                 bm.ctypes.data if bm is not None else None))
+        try:
+            _check(load_library().mincut_server_wait(self.handle, rid, ctypes.byref(val),
+                                                     ctypes.byref(lat),
+                                                     bm.ctypes.data if bm is not None else None))
+        finally:
+            self.keep.pop(rid, None)
         return int(val.value), float(lat.value), bm
 
     def stats(self) -> dict:

@@ -38,8 +38,11 @@ double now_ms() {
 struct Request {
   uint64_t id = 0;
   int64_t n = 0;
-  std::vector<int64_t> rp;
+  std::vector<int64_t> rp;     // owned copy (mincut_server_submit) ...
   std::vector<int32_t> col, w;
+  const int64_t* prp = nullptr;  // ... or the caller's arrays (submit_borrowed)
+  const int32_t* pcol = nullptr;
+  const int32_t* pw = nullptr;
   int64_t footprint = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   bool done = false;
@@ -88,8 +91,8 @@ void finish(mincut_server* S, const std::vector<ReqPtr>& reqs) {
 
 void solve_alone(const mincut_server_options& o, cudaStream_t s, const ReqPtr& r) {
   mincut_graph* g = nullptr;
-  r->status = mincut_graph_from_csr(r->n, r->rp.data(), r->col.data(), r->w.data(),
-                                    MINCUT_HOST_PTRS, (void*)s, nullptr, &g);
+  r->status = mincut_graph_from_csr(r->n, r->prp, r->pcol, r->pw, MINCUT_HOST_PTRS, (void*)s,
+                                    nullptr, &g);
   if (r->status != MINCUT_OK) return;
   if (o.want_bitmap) r->bitmap.assign((size_t)((r->n + 63) / 64), 0);
   r->status = mincut_solve(g, &o.solve, &r->value, o.want_bitmap ? r->bitmap.data() : nullptr,
@@ -104,18 +107,18 @@ void solve_packed(mincut_server* S, const mincut_server_options& o, cudaStream_t
   int64_t entries = 0;
   for (size_t i = 0; i < G; ++i) {
     voff[i + 1] = voff[i] + reqs[i]->n;
-    entries += reqs[i]->rp.back();
+    entries += reqs[i]->prp[reqs[i]->n];
   }
   std::vector<int64_t> rp((size_t)voff[G] + 1);
   std::vector<int32_t> col((size_t)std::max<int64_t>(entries, 1)), w((size_t)std::max<int64_t>(entries, 1));
   int64_t e0 = 0;
   for (size_t i = 0; i < G; ++i) {
     const Request& r = *reqs[i];
-    for (int64_t v = 0; v < r.n; ++v) rp[(size_t)(voff[i] + v)] = e0 + r.rp[(size_t)v];
-    const int64_t m = r.rp.back();
+    for (int64_t v = 0; v < r.n; ++v) rp[(size_t)(voff[i] + v)] = e0 + r.prp[(size_t)v];
+    const int64_t m = r.prp[r.n];
     for (int64_t e = 0; e < m; ++e) {
-      col[(size_t)(e0 + e)] = r.col[(size_t)e] + (int32_t)voff[i];
-      w[(size_t)(e0 + e)] = r.w[(size_t)e];
+      col[(size_t)(e0 + e)] = r.pcol[(size_t)e] + (int32_t)voff[i];
+      w[(size_t)(e0 + e)] = r.pw[(size_t)e];
     }
     e0 += m;
   }
@@ -246,17 +249,26 @@ int mincut_server_create(const mincut_server_options* opts, mincut_server** out)
   return MINCUT_OK;
 }
 
-int mincut_server_submit(mincut_server* S, int64_t n, const int64_t* row_ptr, const int32_t* col,
-                         const int32_t* w, uint64_t* request_id) {
+static int submit_impl(mincut_server* S, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                       const int32_t* w, bool borrow, uint64_t* request_id) {
   if (!S || !row_ptr || !request_id || n < 2 || n > 0x7ffffffe) return MINCUT_ERR_INVALID;
   const int64_t m = row_ptr[n];
   if (row_ptr[0] != 0 || m < 0 || (m > 0 && (!col || !w))) return MINCUT_ERR_INVALID;
   auto r = std::make_shared<Request>();
   r->n = n;
-  r->rp.assign(row_ptr, row_ptr + n + 1);
-  r->col.assign(col, col + m);
-  r->w.assign(w, w + m);
-  if (m == 0) { r->col.push_back(0); r->w.push_back(0); }
+  if (borrow && m > 0) {
+    r->prp = row_ptr;
+    r->pcol = col;
+    r->pw = w;
+  } else {
+    r->rp.assign(row_ptr, row_ptr + n + 1);
+    r->col.assign(col, col + m);
+    r->w.assign(w, w + m);
+    if (m == 0) { r->col.push_back(0); r->w.push_back(0); }
+    r->prp = r->rp.data();
+    r->pcol = r->col.data();
+    r->pw = r->w.data();
+  }
   r->footprint = mincut_graph_footprint(n, m);
   r->t_submit = now_ms();
   {
@@ -270,6 +282,16 @@ int mincut_server_submit(mincut_server* S, int64_t n, const int64_t* row_ptr, co
   S->cv_work.notify_one();
   *request_id = r->id;
   return MINCUT_OK;
+}
+
+int mincut_server_submit(mincut_server* S, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                         const int32_t* w, uint64_t* request_id) {
+  return submit_impl(S, n, row_ptr, col, w, false, request_id);
+}
+
+int mincut_server_submit_borrowed(mincut_server* S, int64_t n, const int64_t* row_ptr,
+                                  const int32_t* col, const int32_t* w, uint64_t* request_id) {
+  return submit_impl(S, n, row_ptr, col, w, true, request_id);
 }
 
 int mincut_server_wait(mincut_server* S, uint64_t request_id, int64_t* cut_value,

@@ -79,3 +79,17 @@ def test_server_rejects_bad_request():
     with pytest.raises(mc.MincutError):
         S.submit(1, np.zeros(2, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
     S.close()
+
+
+def test_server_borrowed_pinned_requests_equal_oracle(requests_small, oracle_values):
+    """Requests submitted without a copy (the server reads the caller's pinned
+    arrays in place until wait returns) give the oracle's values."""
+    sub = requests_small[:40]
+    pinned = [(g.n, torch.from_numpy(g.row_ptr).pin_memory().numpy(),
+               torch.from_numpy(g.col).pin_memory().numpy(),
+               torch.from_numpy(g.w).pin_memory().numpy()) for g in sub]
+    S = mc.Server(workers=4, pack_max_n=1500, pack_max_requests=16)
+    ids = [S.submit(n, rp, col, w, borrow=True) for (n, rp, col, w) in pinned]
+    vals = [S.wait(i)[0] for i in ids]
+    S.close()
+    assert vals == oracle_values[:40]
