@@ -180,8 +180,8 @@ void mincut_default_round_options(mincut_round_options* ro);
  * triples (an asymmetric input passes only on a collision); other inputs are
  * checked exactly after canonicalisation.  Sizes: n <= 2^31 - 2 and
  * M = row_ptr[n] <= 2^31 - 1 (MINCUT_ERR_OVERFLOW beyond, before any device
- * work); in practice device memory bounds them first (about 176 bytes per
- * vertex and 122 per entry, mincut_graph_footprint). */
+ * work); in practice device memory bounds them first (about 208 bytes per
+ * vertex and 126 per entry, mincut_graph_footprint). */
 int mincut_graph_from_csr(int64_t n, const int64_t* row_ptr, const int32_t* col,
                           const int32_t* w, uint32_t flags, void* cuda_stream,
                           const mincut_allocator* alloc, mincut_graph** out);

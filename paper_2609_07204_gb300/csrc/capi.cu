@@ -396,7 +396,12 @@ int ensure_rows(mincut_graph* g) {
       !galloc(g, &r.dense_group, n + 1) ||
       !(r.acc = dev_alloc(g, (size_t)4 * M * wsz)) ||
       !galloc(g, &g->colG, M) ||
-      !(g->wG = dev_alloc(g, (size_t)M * wsz)) || !(g->side_w = dev_alloc(g, (size_t)M * wsz))) {
+      !(g->wG = dev_alloc(g, (size_t)M * wsz)) || !(g->side_w = dev_alloc(g, (size_t)M * wsz)) ||
+      !galloc(g, &r.rep, n + 1) || !galloc(g, &r.fcl, n + 1) || !galloc(g, &r.kpc, n + 1) ||
+      !galloc(g, &r.side_c, M) || !(r.rec = dev_alloc(g, (size_t)(n + 1) * 16)) ||
+      !galloc(g, &r.tile_ht, M / kEntryTile + 2) || !galloc(g, &r.tile_rowG, M / kEntryTile + 2) ||
+      !galloc(g, &r.list, n + 1) || !galloc(g, &r.list_len, 2) ||
+      !galloc(g, &r.vmap, n / 32 + 2) || !galloc(g, &r.mvbits, n / 32 + 2)) {
     r.cnt = nullptr;
     return fail(MINCUT_ERR_OOM, "row-wise contraction buffers");
   }
@@ -468,13 +473,14 @@ int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out, bool defe
   const long long M = g->M;
   const int vbits = bits_for(n2);
   RowScratch& rs = g->rows;
+  const int ndense = g->hst->ndense;  // read with the relabel's synchronisation
   // (the emit of the general rows reads only their entries: it is timed
   // with the row-wise pass, whose algorithmic bytes cover every entry)
   { ProfScope ps(P_ROWS, M, s);
-    CK(rows_count<WT>(n, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, rs, (WT*)g->side_w, s,
-                      &g->launches));
+    CK(rows_count<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, g->flags, g->rank,
+                      g->tile_row, rs, (WT*)g->side_w, s, &g->launches));
     CK(rows_dense_accumulate<WT>(n, M, n2, g->crp(), g->ccol(), (const WT*)g->cw(), g->L,
-                                 g->tile_row, rs, s, &g->launches));
+                                 g->tile_row, rs, ndense, (WT*)g->side_w, s, &g->launches));
     CK(cudaMemsetAsync(&g->st->emit_count, 0, sizeof(long long), s));
     CK(emit_pairs<WT>(n, M, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, vbits, g->tile_row,
                       g->keys[0], (WT*)g->vals[0], g->st, 0, s, &g->launches, rs.gen)); }
@@ -492,8 +498,8 @@ int contract_rows(mincut_graph* g, int n2, int nxt, long long* m2_out, bool defe
   CK(cudaMemcpyAsync(&mG, g->m2_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   { ProfScope ps(P_ROWS, M, s);
-    CK(rows_finish<WT>(n, n2, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, rs,
-                       (const WT*)g->side_w, g->rpG, g->colG, (const WT*)g->wG, mG, g->tile_row,
+    CK(rows_finish<WT>(n, M, n2, g->crp(), g->ccol(), (const WT*)g->cw(), g->L, rs, ndense,
+                       (WT*)g->side_w, g->rpG, g->colG, (const WT*)g->wG, mG, g->tile_row,
                        g->rp[nxt], g->col[nxt], (WT*)g->w[nxt], (WT*)g->degb[nxt], s,
                        &g->launches)); }
   if (defer_m) {
@@ -1682,7 +1688,7 @@ int64_t mincut_graph_footprint(int64_t n, int64_t m_directed) {
   // 8-byte weights and sums double the weight terms; this bound assumes
   // 4-byte ones (total weight < 2^31) plus the label-propagation and the
   // row-wise contraction buffers
-  return (int64_t)(176 * n + 122 * m_directed + 4096 * P + (1 << 20));
+  return (int64_t)(208 * n + 126 * m_directed + 4096 * P + (1 << 20));
 }
 
 int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,

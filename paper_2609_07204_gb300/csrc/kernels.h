@@ -357,8 +357,24 @@ struct RowScratch {
   long long dense_slots;
   int* dense_group;  // n: group of each dense slot
   unsigned long long* dense_entries;  // entries of the dense groups' rows
+  int* rep;     // n: the member of a single-vertex group, -1 for the others
+  // entry-tiled path of the singleton rows (graphs of kFlatMinEntries and more)
+  int* fcl;       // n: clean entries of each row
+  int* kpc;       // n: moved labels of each single-vertex group's row
+  int* side_c;    // M: per row, clean entries by the number of moved labels below them
+  void* rec;      // n: 16-byte record per row (output offset, moved labels, first label)
+  int2* tile_ht;  // entry tiles: clean entries of each tile's first / last row
+  int* tile_rowG; // entry tiles of the general CSR
+  int* list;      // n: rows with several moved labels (two lists, from both ends)
+  int* list_len;  // 2
+  int4* vmap;        // n / 32 + 1: compact vertex map (moved, non-root bits, prefix)
+  unsigned* mvbits;  // n / 32 + 1: the moved bits alone
 };
 constexpr int kDenseChunk = 2048;  // accumulator slots per block of the dense kernels
+constexpr long long kFlatMinEntries = 1ll << 18;  // entry-tiled singleton rows from here
+
+// Whether a graph of M entries takes the entry-tiled singleton-row path.
+bool rows_flat(long long M);
 
 // cnt, gen (multi-member groups) and *single_entries.  n2 only sizes the
 // cleared arrays: any bound >= the relabelled vertex count will do.
@@ -376,25 +392,36 @@ cudaError_t rows_dense_mark(int n_bound, const int* n2_dev, const RowScratch& rs
                             int* launches);
 
 // Dense groups: accumulate their entries (acc must be zero), count the
-// distinct labels into len.
+// distinct labels into len.  ndense: the dense groups asked for (*rs.ndense,
+// read by the host) size the grids.  On the entry-tiled path the slots of
+// multi-member dense groups towards single vertices are transposed into those
+// rows' moved lists (side_v / side_w).
 template <typename WT>
 cudaError_t rows_dense_accumulate(int n, long long M, int n2, const int64_t* rp, const int* col,
                                   const WT* w, const int* L, const int* tile_row,
-                                  const RowScratch& rs, cudaStream_t s, int* launches);
+                                  const RowScratch& rs, int ndense, WT* side_w, cudaStream_t s,
+                                  int* launches);
 
 // Singleton rows: len, kcnt and the moved labels with their summed weights
-// (side_v / side_w); rows that do not fit are added to gen.
+// (side_v / side_w); rows that do not fit are added to gen.  On the
+// entry-tiled path (rows_flat(M)) only the clean entries of every row are
+// counted here; the moved labels come from the other groups' contracted
+// rows in rows_dense_accumulate / rows_finish.  tile_row: the entry tiles of
+// this graph; root_flags / root_rank: the union-find roots behind L (1 per
+// root) and their exclusive prefix sum.
 template <typename WT>
-cudaError_t rows_count(int n, const int64_t* rp, const int* col, const WT* w, const int* L,
-                       const RowScratch& rs, WT* side_w, cudaStream_t s, int* launches);
+cudaError_t rows_count(int n, long long M, const int64_t* rp, const int* col, const WT* w,
+                       const int* L, const int* root_flags, const int* root_rank,
+                       const int* tile_row, const RowScratch& rs, WT* side_w, cudaStream_t s,
+                       int* launches);
 
 // Final CSR (rp2, col2, w2) and degrees deg2 from the singleton rows and the
 // general CSR (rpG over n2 rows, NG entries); rs.total = entries.
 template <typename WT>
-cudaError_t rows_finish(int n, int n2, const int64_t* rp, const int* col, const WT* w,
-                        const int* L, const RowScratch& rs, const WT* side_w,
+cudaError_t rows_finish(int n, long long M, int n2, const int64_t* rp, const int* col,
+                        const WT* w, const int* L, const RowScratch& rs, int ndense, WT* side_w,
                         const int64_t* rpG, const int* colG, const WT* wG, long long NG,
-                        int* tile_row, int64_t* rp2, int* col2, WT* w2, WT* deg2,
+                        const int* tile_row, int64_t* rp2, int* col2, WT* w2, WT* deg2,
                         cudaStream_t s, int* launches);
 
 }  // namespace mc

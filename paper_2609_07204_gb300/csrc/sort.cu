@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(kRsThreads, 3)
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanFold = 2048;  // blocks that sum the partials before them themselves
 
 __device__ __forceinline__ int block_exclusive_int(int v, int* warp_tot, int* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -232,22 +233,43 @@ __device__ __forceinline__ int block_exclusive_int(int v, int* warp_tot, int* to
   return x - v + add;
 }
 
-__global__ void scan_reduce_kernel(const int* __restrict__ in, int N, int* __restrict__ part) {
-  __shared__ int s_w[kScanThreads / 32];
-  const long long base = (long long)blockIdx.x * kScanTile;
-  int s = 0;
-  for (int i = 0; i < kScanItems; ++i) {
-    long long idx = base + i * kScanThreads + threadIdx.x;
-    if (idx < N) s += in[idx];
+// Thread t of block b owns the kScanItems consecutive values from
+// b * kScanTile + t * kScanItems (whole 16-byte vectors when they can be).
+__device__ __forceinline__ void scan_load_run(const int* __restrict__ in, long long i0, int N,
+                                              int (&v)[kScanItems]) {
+  if (i0 + kScanItems <= N && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+    const int4* p = reinterpret_cast<const int4*>(in + i0);
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q) {
+      const int4 a = p[q];
+      v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = i0 + k < N ? in[i0 + k] : 0;
   }
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+}
+
+__device__ __forceinline__ int block_sum_int(int v, int* warp_tot) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w2 = 0; w2 < kScanThreads / 32; ++w2) t += s_w[w2];
-    part[blockIdx.x] = t;
-  }
+  int t = 0;
+  for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += warp_tot[w2];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_reduce_kernel(const int* __restrict__ in, int N, int* __restrict__ part) {
+  __shared__ int s_w[kScanThreads / 32];
+  int v[kScanItems];
+  scan_load_run(in, (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems, N, v);
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) s += v[k];
+  s = block_sum_int(s, s_w);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // Single block: exclusive scan of part[0..nb) in place; *total = sum.
@@ -270,25 +292,48 @@ __global__ void scan_partials_kernel(int* part, int nb, int* total) {
   if (threadIdx.x == 0 && total) *total = s_carry;
 }
 
-__global__ void scan_down_kernel(const int* __restrict__ in, int* __restrict__ out, int N,
-                                 const int* __restrict__ part) {
+// Down-sweep.  fold = 0: part[b] is block b's exclusive prefix.  fold = 1:
+// part[b] is block b's sum, and each block adds up those of the blocks
+// before it (a few thousand at most), the last block writing *total.
+__global__ void __launch_bounds__(kScanThreads)
+    scan_down_kernel(const int* __restrict__ in, int* __restrict__ out, int N,
+                     const int* __restrict__ part, int fold, int* __restrict__ total) {
   __shared__ int s_w[kScanThreads / 32];
-  __shared__ int s_carry;
-  const long long base = (long long)blockIdx.x * kScanTile;
-  if (threadIdx.x == 0) s_carry = part[blockIdx.x];
-  __syncthreads();
-  // items processed in kScanItems rounds of kScanThreads consecutive values
-  for (int i = 0; i < kScanItems; ++i) {
-    long long idx = base + i * kScanThreads + threadIdx.x;
-    int v = idx < N ? in[idx] : 0;
-    int tot;
-    int ex = block_exclusive_int(v, s_w, &tot);
-    int carry = s_carry;
-    if (idx < N) out[idx] = ex + carry;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry = carry + tot;
-    __syncthreads();
+  const long long i0 = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  scan_load_run(in, i0, N, v);
+  int pre;
+  if (fold) {
+    int p = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) p += part[i];
+    pre = block_sum_int(p, s_w);
+  } else {
+    pre = part[blockIdx.x];
   }
+  int run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) run += v[k];
+  int tot;
+  int ex = pre + block_exclusive_int(run, s_w, &tot);
+  if (i0 + kScanItems <= N && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    int4* q = reinterpret_cast<int4*>(out + i0);
+#pragma unroll
+    for (int r = 0; r < kScanItems / 4; ++r) {
+      int4 a;
+      a.x = ex; ex += v[4 * r];
+      a.y = ex; ex += v[4 * r + 1];
+      a.z = ex; ex += v[4 * r + 2];
+      a.w = ex; ex += v[4 * r + 3];
+      q[r] = a;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (i0 + k < N) out[i0 + k] = ex;
+      ex += v[k];
+    }
+  }
+  if (fold && total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = pre + tot;
 }
 
 }  // namespace
@@ -356,10 +401,17 @@ cudaError_t scan_exclusive_i32(const int* in, int* out, int N, int* part, int* t
     return cudaGetLastError();
   }
   const int nb = (N + kScanTile - 1) / kScanTile;
+  if (nb == 1) {  // one block: no partials
+    scan_down_kernel<<<1, kScanThreads, 0, s>>>(in, out, N, part, 1, total);
+    ++*launches;
+    return cudaGetLastError();
+  }
   scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, N, part);
-  scan_partials_kernel<<<1, 1024, 0, s>>>(part, nb, total);
-  scan_down_kernel<<<nb, kScanThreads, 0, s>>>(in, out, N, part);
-  *launches += 3;
+  // up to kScanFold blocks add up the sums before them themselves
+  const bool fold = nb <= kScanFold;
+  if (!fold) scan_partials_kernel<<<1, 1024, 0, s>>>(part, nb, total);
+  scan_down_kernel<<<nb, kScanThreads, 0, s>>>(in, out, N, part, fold ? 1 : 0, total);
+  *launches += fold ? 2 : 3;
   return cudaGetLastError();
 }
 

@@ -297,21 +297,28 @@ def _singleton_entry_share(n, rp, L):
     return float(deg[cnt[L] == 1].sum()) / max(int(rp[-1]), 1)
 
 
-@pytest.mark.parametrize("weights", ["unit", "int64_totals"])
-def test_contract_rowwise_bit_exact(weights):
+@pytest.mark.parametrize("weights,scale", [("unit", 15), ("int64_totals", 15), ("unit", 13)])
+def test_contract_rowwise_bit_exact(weights, scale):
     """Rounds where most groups are single vertices take the row-wise path:
     singleton rows rebuilt in place with the labels of multi-member groups
     merged in (duplicates summed), rows longer than 4096 entries and rows
     with more than 32 distinct multi-member neighbours through the sort.
-    Three chained contractions, each against the oracle's contraction."""
+    The scale-15 graphs hold more than 2^18 entries: their singleton rows go
+    through the entry tiles (rows that cross tile boundaries included), those
+    with several moved labels through the warp-per-row kernels; the scale-13
+    ones (fewer entries) take one warp per singleton row.  Three chained
+    contractions, each against the oracle's contraction."""
     rng = np.random.default_rng(21)
-    s = synth.workload_rmat_core(scale=15, k=8, seed=9)
+    s = synth.workload_rmat_core(scale=scale, k=8, seed=9)
     n, rp, col = s.n, s.row_ptr.copy(), s.col.copy()
     w = s.w.astype(np.int64)
     if weights == "int64_totals":
         w = _sym_weights(n, rp, col, 1 << 22, 1 << 23)
     deg = np.diff(rp)
-    assert deg.max() > 4096
+    if scale == 15:
+        assert deg.max() > 4096 and rp[-1] >= 1 << 18
+    else:
+        assert rp[-1] < 1 << 18
     g = make(n, rp, col, w)
     n0, rp0, col0, w0 = n, rp, col, w
     for step in range(3):
@@ -334,6 +341,15 @@ def test_contract_rowwise_bit_exact(weights):
         others = rng.choice(n, size=40, replace=False)
         pu += [int(x) for x in nb]
         pv += [int(x) for x in others]
+        # rows whose neighbours fall into 2..6 groups (the worklist of the
+        # warp-per-row kernels on large graphs)
+        for _ in range(4):
+            h = int(cand[rng.integers(0, len(cand))])
+            k = int(rng.integers(2, 7))
+            nb = col[rp[h]:rp[h + 1]][-k:]
+            others = rng.choice(n, size=k, replace=False)
+            pu += [int(x) for x in nb]
+            pv += [int(x) for x in others]
         pu = np.asarray(pu, np.int32)
         pv = np.asarray(pv, np.int32)
         n2, L = oracle.labels_from_pairs(n, pu, pv)
@@ -353,6 +369,30 @@ def test_contract_rowwise_bit_exact(weights):
     # row-wise too
     v, _, _ = mc.mincut_solve(g, bitmap=False)
     assert v == oracle.noi(n0, rp0, col0, w0)[0]
+
+
+def test_contract_rowwise_short_rows_bit_exact():
+    """Entry tiles that cover more rows than their shared-memory row table
+    (rows of about two entries) find rows in the global row offsets; the
+    moved labels come from about 3000 pairs and one group of 40.  Against the
+    oracle's contraction."""
+    rng = np.random.default_rng(31)
+    s = synth.cycle_plus(150000, 0.2, 1, 9, 11)
+    n, rp, col, w = s.n, s.row_ptr, s.col, s.w.astype(np.int64)
+    assert rp[-1] >= 1 << 18
+    assert np.diff(rp).mean() < 4
+    groups = np.arange(n, dtype=np.int32)
+    pick = rng.choice(n, size=6000, replace=False)
+    groups[pick[:3000]] = pick[3000:]          # 3000 pairs
+    groups[pick[:40]] = int(pick[0])           # one group of 40 (with their pair mates)
+    n2, L = oracle.labels_from_groups(groups)
+    g = make(n, rp, col, w)
+    ro = mc.default_round_options()
+    ro.groups = groups.ctypes.data
+    res = mc.mincut_contract_round(g, ro)
+    exp = oracle.contract(n, rp, col, w, L, n2)
+    assert res["n_out"] == n2
+    assert_csr_equal(mc.mincut_graph_export_csr(g), exp)
 
 
 # ------------------------------------------------------------------ PR flags
