@@ -122,6 +122,8 @@ struct WpArgs {
   int r_smem;               // r in shared memory
   long long csr_at;         // byte offset of a shared-memory copy of the CSR (-1: none)
   int csr_full;             // the copy holds columns and weights too
+  int stop_low;             // stop once the pass has marked and its highest priority falls
+                            // below half the bound
 };
 
 // x has left the queue and its level-1 node holds the new maximum of its
@@ -497,7 +499,8 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     // that neighbour is next, and its row loads go out before this row's
     // updates are committed
     const bool single = ps.xe - ps.xb <= 64;
-    const bool fast = single && ps.bk > 0 && ps.bk >= ps.kt;
+    const bool fast = single && ps.bk > 0 && ps.bk >= ps.kt &&
+                      !(a.stop_low && 2ll * (long long)(ps.bk - 1) < (long long)ps.lam);
     if (fast) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -541,6 +544,14 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
       apply_batch<4, WT, RS>(ps, y4, c4, r4, b4, rr, lev, top, mark, nmarks, packed);
     }
     __syncwarp();  // this row's updates are visible to the next reads
+    if (a.stop_low) {
+      // the pass has left the region it marked (a prefix of a maximum-
+      // adjacency order: its marks and its alpha stay valid)
+      const unsigned kn = max(ps.bk, ps.kt);
+      if (kn > 0 && 2ll * (long long)(kn - 1) < (long long)ps.lam &&
+          __any_sync(FULL, nmarks != 0))
+        break;
+    }
     // ---- the next vertex: a neighbour holding the highest key, else the
     // smallest vertex id among the highest
     if (ps.bk > 0 && ps.bk >= ps.kt) {
@@ -696,7 +707,8 @@ cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const i
                                   unsigned long long seed, long long lam, int* parent,
                                   WT* r_pool, unsigned char* lev_pool, long long lev_stride,
                                   int* order_pool, int* mark_pool, unsigned long long* pass_best,
-                                  int* pass_len, DevState* st, cudaStream_t s, int* launches) {
+                                  int* pass_len, int stop_low, DevState* st, cudaStream_t s,
+                                  int* launches) {
   if (!warp_pass_key_bytes(lam) || passes < 1 || n < 1) return cudaErrorInvalidValue;
   const WTree t = wtree(n);
   // tree levels from the top down while they fit, then r[], then the CSR
@@ -762,6 +774,7 @@ cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const i
   a.r_smem = r_smem;
   a.csr_at = csr_at;
   a.csr_full = csr_full;
+  a.stop_low = stop_low;
   static bool attr[2][2] = {};
   const int wi = sizeof(WT) == 8 ? 1 : 0;
   if (!attr[wi][r_smem]) {
@@ -785,7 +798,7 @@ cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const i
   template cudaError_t capforest_warp_passes<WT>(                                             \
       int, long long, const int64_t*, const int*, const WT*, const WT*, int, int,              \
       unsigned long long, long long, int*, WT*, unsigned char*, long long, int*, int*,         \
-      unsigned long long*, int*, DevState*, cudaStream_t, int*);
+      unsigned long long*, int*, int, DevState*, cudaStream_t, int*);
 MC_WP_INST(int32_t)
 MC_WP_INST(int64_t)
 

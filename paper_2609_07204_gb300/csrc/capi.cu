@@ -765,7 +765,8 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
                                    (WT*)g->seq_multi_r,
                                    reinterpret_cast<unsigned char*>(g->seq_multi_tree),
                                    seq_tree_words((int)g->n0) * 8, g->seq_multi_order,
-                                   g->seq_multi_mark, g->pass_best, g->pass_len, g->st, s,
+                                   g->seq_multi_mark, g->pass_best, g->pass_len,
+                                   c.capforest == 1 && n >= kWarpStopMinN ? 1 : 0, g->st, s,
                                    &g->launches));
     }
     rc = sync_state(g);

@@ -313,12 +313,17 @@ cudaError_t capforest_sequential_batch(int G, const int64_t* rp, const int* col,
 // mark_pool n ints.  Marks are hooked in parent after the passes; the best
 // alpha goes to st->lambda and, naming its pass (cf_pass = -2 - k, visit
 // order order_pool + k * n), to st->cf_val / cf_len; st->cf_nscanned gets
-// pass 0's visited count.
+// pass 0's visited count.  stop_low: a pass stops once it has marked an
+// edge and the highest priority left in its queue is below half the bound
+// (it has left the region it marked; the marks and alpha of a prefix of a
+// maximum-adjacency order stay valid), else it visits every reachable vertex.
 constexpr size_t kWarpPassSmem = 200 * 1024;
 // global bytes the simultaneous warp passes of a round may keep hot in L2
 constexpr long long kWarpPassL2Budget = 80ll << 20;
 // passes a round runs at least (device memory and SMs permitting)
 constexpr int kWarpPassMin = 4;
+// graphs from this many vertices let the passes of a solve's round stop early
+constexpr int kWarpStopMinN = 1 << 16;
 int warp_pass_key_bytes(long long lam);
 long long warp_pass_lev_bytes(int n);
 // bytes of global memory a pass keeps reading (r and tree levels that do not
@@ -330,7 +335,8 @@ cudaError_t capforest_warp_passes(int n, long long M, const int64_t* rp, const i
                                   unsigned long long seed, long long lam, int* parent,
                                   WT* r_pool, unsigned char* lev_pool, long long lev_stride,
                                   int* order_pool, int* mark_pool, unsigned long long* pass_best,
-                                  int* pass_len, DevState* st, cudaStream_t s, int* launches);
+                                  int* pass_len, int stop_low, DevState* st, cudaStream_t s,
+                                  int* launches);
 
 // ------------------------------------------------------------- contract.cu
 // Row-wise contraction when most groups are single vertices: singleton rows
