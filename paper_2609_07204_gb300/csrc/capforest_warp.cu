@@ -96,8 +96,10 @@ __host__ __device__ inline WTree wtree(int n) {
 
 __device__ __forceinline__ int lev_shift(int l) { return kLeafShift + 5 * (l - 1); }
 
-__device__ __forceinline__ unsigned key_of_wp(long long r, long long lam) {
-  return r > 0 ? (unsigned)((r < lam ? r : lam) + 1) : 0u;
+// In the pass's weight type: r and lam fit it, and keys fit 32 bits.
+template <typename WT>
+__device__ __forceinline__ unsigned key_of_wp(WT r, WT lam) {
+  return r > 0 ? (unsigned)(r < lam ? r : lam) + 1u : 0u;
 }
 
 struct WpArgs {
@@ -164,11 +166,12 @@ template <typename WT, bool RS>
 struct RArr {
   using V = typename RRT<WT>::V;
   V* p;
-  __device__ __forceinline__ V ld(long long i) const { return RS ? p[i] : __ldcg(p + i); }
-  __device__ __forceinline__ WT ld_r(long long i) const {
+  // (vertex ids are below 2^31)
+  __device__ __forceinline__ V ld(int i) const { return RS ? p[i] : __ldcg(p + i); }
+  __device__ __forceinline__ WT ld_r(int i) const {
     return RS ? p[i].x : __ldcg(reinterpret_cast<const WT*>(p + i));
   }
-  __device__ __forceinline__ void st_r(long long i, WT v) const {
+  __device__ __forceinline__ void st_r(int i, WT v) const {
     if (RS) p[i].x = v;
     else __stcg(reinterpret_cast<WT*>(p + i), v);
   }
@@ -253,19 +256,18 @@ __device__ __forceinline__ void apply_batch(PassState<WT>& ps, const int (&y)[NC
 template <int NCH, typename WT>
 __device__ __forceinline__ void best_batch(PassState<WT>& ps, const int (&y)[NCH],
                                            const WT (&c)[NCH], const WT (&r0)[NCH],
-                                           const int (&yb)[NCH], bool packed) {
+                                           const int (&yb)[NCH], bool packed, WT (&r1)[NCH],
+                                           unsigned (&k1)[NCH]) {
   const int lane = threadIdx.x;
   unsigned lbk = 0;
   int lu = 0;
 #pragma unroll
   for (int u = 0; u < NCH; ++u) {
-    if (y[u] >= 0 && r0[u] >= 0) {
-      const WT r1 = r0[u] + c[u];
-      const unsigned k1 = (unsigned)(r1 < ps.lam ? r1 : ps.lam) + 1u;
-      if (k1 > lbk) {
-        lbk = k1;
-        lu = u;
-      }
+    r1[u] = r0[u] + c[u];
+    k1[u] = (y[u] >= 0 && r0[u] >= 0) ? (unsigned)(r1[u] < ps.lam ? r1[u] : ps.lam) + 1u : 0u;
+    if (k1[u] > lbk) {
+      lbk = k1[u];
+      lu = u;
     }
   }
   unsigned km, pos;
@@ -281,13 +283,13 @@ __device__ __forceinline__ void best_batch(PassState<WT>& ps, const int (&y)[NCH
   if (km > ps.bk) {
     const int wl = (int)(pos & 31);
     int sy = y[0], sb = yb[0];
-    WT sr = r0[0] + c[0];
+    WT sr = r1[0];
 #pragma unroll
     for (int u = 1; u < NCH; ++u)
       if (lu == u) {
         sy = y[u];
         sb = yb[u];
-        sr = r0[u] + c[u];
+        sr = r1[u];
       }
     ps.bk = km;
     ps.by = __shfl_sync(FULL, sy, wl);
@@ -296,26 +298,25 @@ __device__ __forceinline__ void best_batch(PassState<WT>& ps, const int (&y)[NCH
   }
 }
 
-// The updates of NCH chunks: r, marks and the tree.
+// The updates of NCH chunks (new r and keys from best_batch): r, marks and
+// the tree.
 template <int NCH, typename WT, bool RS>
 __device__ __forceinline__ void commit_batch(const PassState<WT>& ps, const int (&y)[NCH],
-                                             const WT (&c)[NCH], const WT (&r0)[NCH],
-                                             const RArr<WT, RS> rr, unsigned* const* lev,
-                                             int top, int* __restrict__ mark,
-                                             unsigned& nmarks) {
+                                             const WT (&r0)[NCH], const WT (&r1)[NCH],
+                                             const unsigned (&k1)[NCH], const RArr<WT, RS> rr,
+                                             unsigned* const* lev, int top,
+                                             int* __restrict__ mark, unsigned& nmarks) {
 #pragma unroll
   for (int u = 0; u < NCH; ++u) {
-    if (y[u] >= 0 && r0[u] >= 0) {
-      const WT r1 = r0[u] + c[u];
-      rr.st_r(y[u], r1);
-      if (r0[u] < ps.lam && ps.lam <= r1) {
+    if (k1[u]) {
+      rr.st_r(y[u], r1[u]);
+      if (r0[u] < ps.lam && ps.lam <= r1[u]) {
         mark[y[u]] = ps.x;
         ++nmarks;
       }
-      const unsigned k1 = (unsigned)(r1 < ps.lam ? r1 : ps.lam) + 1u;
 #pragma unroll
       for (int l = 1; l < kMaxLev; ++l)
-        if (l <= top) atomicMax(&lev[l][y[u] >> lev_shift(l)], k1);
+        if (l <= top) atomicMax(&lev[l][y[u] >> lev_shift(l)], k1[u]);
     }
   }
 }
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     {
       unsigned gk = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) gk = max(gk, key_of_wp((long long)g4[j], (long long)ps.lam));
+      for (int j = 0; j < 4; ++j) gk = max(gk, key_of_wp<WT>(g4[j], ps.lam));
       const unsigned node = __reduce_max_sync(FULL, gk);
       if (lane == 0) *(volatile unsigned*)&lev[1][ps.x >> kLeafShift] = node;
       __syncwarp();
@@ -494,7 +495,9 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     ps.by = -1;
     ps.bb = 0;
     ps.br = 0;
-    best_batch<2, WT>(ps, y, c, r0, yb, packed);
+    WT r1[2];
+    unsigned k1[2];
+    best_batch<2, WT>(ps, y, c, r0, yb, packed, r1, k1);
     // a row of at most 64 entries whose best neighbour holds the highest key:
     // that neighbour is next, and its row loads go out before this row's
     // updates are committed
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
       nxe = (int)rp[ps.by + 1];
       nxd = deg[ps.by];
     }
-    commit_batch<2, WT, RS>(ps, y, c, r0, rr, lev, top, mark, nmarks);
+    commit_batch<2, WT, RS>(ps, y, r0, r1, k1, rr, lev, top, mark, nmarks);
     if (fast) {
       __syncwarp();  // this row's updates are visible to the next reads
       ps.x = ps.by;
@@ -591,7 +594,7 @@ __global__ void __launch_bounds__(32) cf_warp_pass_kernel(WpArgs a) {
     int sbv = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const unsigned hb = __ballot_sync(FULL, key_of_wp((long long)rv[j], (long long)ps.lam) == kt);
+      const unsigned hb = __ballot_sync(FULL, key_of_wp<WT>(rv[j], ps.lam) == kt);
       if (found < 0 && hb) {
         found = j * 32 + (__ffs(hb) - 1);
         srv = rv[j];
