@@ -151,6 +151,7 @@ struct mincut_graph {
   void* deg0 = nullptr;     // degrees of the canonical input
   void* degb[2]{};          // degrees of the ping-pong CSRs
   unsigned long long* blk = nullptr;
+  unsigned* short_bits = nullptr;  // n / 32: rows within the PR3/PR4 budget
   int *parent = nullptr, *L = nullptr, *flags = nullptr, *rank = nullptr, *part = nullptr,
       *uid = nullptr, *owner = nullptr, *gmin = nullptr, *map0 = nullptr;
   uint8_t *side0 = nullptr, *cur_side = nullptr;
@@ -706,7 +707,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   if (c.pr_mask) {
     ProfScope ps(P_PR, M, s);
     CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, c.pr_mask, c.pr_budget, g->parent,
-                    flags_dev, g->st, s, &g->launches));
+                    flags_dev, g->short_bits, g->st, s, &g->launches));
   }
   if (c.capforest == 1 && n > 2) {
     CK(cudaMemsetAsync(g->owner, 0, (size_t)n * sizeof(int), s));
@@ -1308,7 +1309,7 @@ int create_impl(int64_t n64, const int64_t* row_ptr, const int32_t* col, const i
        galloc(g, &g->flags, n) && galloc(g, &g->rank, n) && galloc(g, &g->part, scan_parts) &&
        galloc(g, &g->uid, Mb) && galloc(g, &g->owner, n) && galloc(g, &g->gmin, n) &&
        galloc(g, &g->map0, n) && galloc(g, &g->side0, n) && galloc(g, &g->cur_side, n) &&
-       galloc(g, &g->bitmap_dev, (n + 63) / 64) &&
+       galloc(g, &g->bitmap_dev, (n + 63) / 64) && galloc(g, &g->short_bits, n / 32 + 2) &&
        galloc(g, &g->visit_log, (long long)g->max_passes * g->max_table) &&
        galloc(g, &g->pass_best, g->max_passes) && galloc(g, &g->pass_len, g->max_passes) &&
        galloc(g, &g->pass_counter, 1) && (g->seq_r = dev_alloc(g, (size_t)n * wsz)) &&
@@ -1471,7 +1472,7 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
     if (op.pr_mask) {
       ProfScope ps(P_PR, M, s);
       CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, op.pr_mask, op.pr_budget, g->parent,
-                      nullptr, g->st, s, &g->launches, &v));
+                      nullptr, g->short_bits, g->st, s, &g->launches, &v));
     }
     if (!op.deterministic) {
       ProfScope ps(P_CF_PASSES, M, s);

@@ -173,11 +173,14 @@ template <typename WT>
 cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                             const int* tile_row, DevState* st, cudaStream_t s, int* launches);
 
+// short_bits: n / 32 + 1 words of scratch for the budget test's bit map.
+// st->deg_val must hold the graph's minimum weighted degree (the round's
+// degree bound) when bv is null.
 template <typename WT>
 cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                      const WT* deg, const int* tile_row, uint32_t mask, long long budget,
-                     int* parent, uint8_t* flags_out, DevState* st, cudaStream_t s,
-                     int* launches, const BatchView* bv = nullptr);
+                     int* parent, uint8_t* flags_out, unsigned* short_bits, DevState* st,
+                     cudaStream_t s, int* launches, const BatchView* bv = nullptr);
 
 // One label-propagation sweep (vertices with ((v ^ sweep) & 1) == 0 update).
 // Rows up to 128 entries use a warp table, up to 4096 a block table, longer

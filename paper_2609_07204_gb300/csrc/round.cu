@@ -387,13 +387,26 @@ __global__ void sym_final_kernel(DevState* st) {
 // tile do not leave the other lanes idle.
 constexpr int kPrQueue = kET;
 
+// bits[v / 32] bit v % 32: row v has at most `budget` entries (a 1-bit copy
+// of the budget test that stays in L1 where the row offsets do not).
+__global__ void short_rows_kernel(int n, const int64_t* __restrict__ rp, long long budget,
+                                  unsigned* __restrict__ bits) {
+  const int nw = (n + 31) >> 5;
+  for (int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nw;
+       wi += (gridDim.x * blockDim.x) >> 5) {
+    const int v = (wi << 5) + (threadIdx.x & 31);
+    const unsigned b = __ballot_sync(FULL, v < n && rp[v + 1] - rp[v] <= budget);
+    if ((threadIdx.x & 31) == 0) bits[wi] = b;
+  }
+}
+
 template <typename WT>
 __global__ void __launch_bounds__(kETThreads, 5)
     pr_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
               const WT* __restrict__ w, const WT* __restrict__ deg,
               const int* __restrict__ tile_row, int ntiles, uint32_t mask, long long budget,
-              int* parent, uint8_t* __restrict__ flags_out, DevState* st, BatchView bv,
-              int batch) {
+              int* parent, uint8_t* __restrict__ flags_out,
+              const unsigned* __restrict__ short_bits, DevState* st, BatchView bv, int batch) {
   __shared__ TileRowsSmem tr;
   __shared__ int q_u[kPrQueue];
   __shared__ unsigned q_ef[kPrQueue];  // entry offset in the tile | PR1/PR2 flags << 16
@@ -403,6 +416,9 @@ __global__ void __launch_bounds__(kETThreads, 5)
   // entry offsets fit 32 bits: graphs hold fewer than 2^31 entries
   const bool exact = flags_out != nullptr;
   const long long lam_global = (long long)*(volatile unsigned long long*)&st->lambda;
+  // every weighted degree is at least the round's minimum degree: PR2 needs
+  // 2c(u,v) > it, so lighter edges skip the degree gathers
+  const long long dmin = batch ? 0 : (long long)*(volatile unsigned long long*)&st->deg_val;
   const long long e0 = (long long)blockIdx.x * kET;
   unsigned long long nmarks = 0;
   bool uf_fail = false;
@@ -427,13 +443,21 @@ __global__ void __launch_bounds__(kETThreads, 5)
     }
     const long long lam = batch ? (long long)*(volatile unsigned long long*)&bv.lam_g[gu] : lam_global;
     const long long c = (long long)w[e];
-    const long long du = (long long)deg[u], dv = (long long)deg[v];
     uint8_t f = 0;
     if ((mask & 1u) && c >= lam) f |= 1;
-    if ((mask & 2u) && (du < 2 * c || dv < 2 * c)) f |= 2;
+    if ((mask & 2u) && 2 * c > dmin) {
+      const long long du = (long long)deg[u], dv = (long long)deg[v];
+      if (du < 2 * c || dv < 2 * c) f |= 2;
+    }
     if ((mask & 12u) && (exact || f == 0)) {
-      const int lu = (int)(rp[u + 1] - rp[u]), lv = (int)(rp[v + 1] - rp[v]);
-      if (budget < 0 || min(lu, lv) <= budget) {
+      // u's row length from the tile's row offsets; v's budget test from
+      // the bit map
+      const long long lu = tile_rp(tr, rp, u + 1) - tile_rp(tr, rp, u);
+      bool within = budget < 0 || lu <= budget;
+      if (!within)
+        within = short_bits ? ((__ldg(&short_bits[v >> 5]) >> (v & 31)) & 1u)
+                            : rp[v + 1] - rp[v] <= budget;
+      if (within) {
         const int slot = atomicAdd(&q_n, 1);
         q_u[slot] = u;
         q_ef[slot] = (unsigned)(e - e0) | ((unsigned)f << 16);
@@ -1290,14 +1314,21 @@ cudaError_t check_symmetric(int n, long long M, const int64_t* rp, const int* co
 template <typename WT>
 cudaError_t pr_marks(int n, long long M, const int64_t* rp, const int* col, const WT* w,
                      const WT* deg, const int* tile_row, uint32_t mask, long long budget,
-                     int* parent, uint8_t* flags_out, DevState* st, cudaStream_t s,
-                     int* launches, const BatchView* bv) {
+                     int* parent, uint8_t* flags_out, unsigned* short_bits, DevState* st,
+                     cudaStream_t s, int* launches, const BatchView* bv) {
   if (M <= 0 || mask == 0) return cudaSuccess;
   const int ntiles = (int)((M + kET - 1) / kET);
   BatchView v{};
   if (bv) v = *bv;
+  const bool bits = (mask & 12u) && budget >= 0;
+  if (bits) {
+    short_rows_kernel<<<grid_for((n + 31) / 32 * 32, 256), 256, 0, s>>>(n, rp, budget,
+                                                                         short_bits);
+    ++*launches;
+  }
   pr_kernel<WT><<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, w, deg, tile_row, ntiles, mask,
-                                               budget, parent, flags_out, st, v, bv ? 1 : 0);
+                                               budget, parent, flags_out,
+                                               bits ? short_bits : nullptr, st, v, bv ? 1 : 0);
   ++*launches;
   return cudaGetLastError();
 }
@@ -1481,7 +1512,7 @@ cudaError_t side_to_bitmap(const uint8_t* side0, int n0, u64* bitmap, cudaStream
                                            int*);                                                \
   template cudaError_t pr_marks<WT>(int, long long, const int64_t*, const int*, const WT*,       \
                                     const WT*, const int*, uint32_t, long long, int*, uint8_t*,  \
-                                    DevState*, cudaStream_t, int*, const BatchView*);            \
+                                    unsigned*, DevState*, cudaStream_t, int*, const BatchView*); \
   template cudaError_t lp_sweep<WT>(int, const int64_t*, const int*, const WT*, const int*,      \
                                     int*, int, const LpScratch&, DevState*, cudaStream_t, int*); \
   template cudaError_t lp_first_sweep<WT>(int, long long, const int64_t*, const int*, const WT*, \
