@@ -9,10 +9,15 @@
 // Only the entries towards multi-member groups ("moved" entries) can break
 // the order or coincide.  So a singleton row is rebuilt in place: its clean
 // entries are copied in order and the (few) distinct moved labels, summed
-// and sorted, are merged in at their ranks.  Rows of multi-member groups, and
-// singleton rows with more than kSrMoved distinct moved labels or more than
-// kSrMaxRow entries, are "general": their entries alone go through the
-// relabel / radix sort / segmented sum path, and the resulting rows are
+// and sorted, are merged in at their ranks.  Two forms: on graphs of
+// kFlatMinEntries entries or more, kernels over the round's entry tiles that
+// take the moved entries, by symmetry, from the other groups' contracted
+// rows (the "flat rows" section below); on smaller graphs one warp per row
+// that sums them itself (sr_count / sr_write).  Rows of multi-member groups,
+// singleton rows of more than kSrMaxRow entries (and, in the warp form, those
+// with more than kSrMoved distinct moved labels) are "general": their
+// entries alone go through the relabel / radix sort / segmented sum path, or
+// a dense accumulator for the largest groups, and the resulting rows are
 // copied to their place.  The output is the same canonical CSR the full sort
 // gives (rows ascending, parallel edges summed, self-loops dropped).
 #include <algorithm>
