@@ -598,12 +598,25 @@ __device__ __forceinline__ T peer_sum(unsigned peers, T v) {
 //   vmap.z  vertices below x0 that are not roots
 // and mvbits = vmap.x alone.  A single vertex y is a root, and its label (the
 // rank of its root among the roots) is y - vmap.z - popc(vmap.y below y).
+// It also clears the counters of the flat path (fcl, kpc: n; tile_ht:
+// ntiles; list_len: 2).
 __global__ void fr_vmap_kernel(int n, const int* __restrict__ vinfo,
                                const int* __restrict__ root_flags,
                                const int* __restrict__ root_rank, int4* __restrict__ vmap,
-                               unsigned* __restrict__ mvbits) {
+                               unsigned* __restrict__ mvbits, int* __restrict__ fcl,
+                               int* __restrict__ kpc, int2* __restrict__ tile_ht, int ntiles,
+                               int* __restrict__ list_len) {
   const int lane = threadIdx.x & 31;
   const int nw = (n + 31) >> 5;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    fcl[i] = 0;
+    kpc[i] = 0;
+    if (i < ntiles) tile_ht[i] = make_int2(0, 0);
+    if (i < 2) list_len[i] = 0;
+  }
+  for (int i = n + blockIdx.x * blockDim.x + threadIdx.x; i < ntiles;
+       i += gridDim.x * blockDim.x)
+    tile_ht[i] = make_int2(0, 0);
   for (int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nw;
        wi += (gridDim.x * blockDim.x) >> 5) {
     const int x = (wi << 5) + lane;
@@ -750,8 +763,12 @@ __global__ void fr_finalize_kernel(int n, const int64_t* __restrict__ rp,
                                    const int* __restrict__ vinfo, const int* __restrict__ gen,
                                    const int* __restrict__ fcl, const int* __restrict__ kpc,
                                    int* __restrict__ len, int* __restrict__ side_c,
-                                   int* __restrict__ list, int* __restrict__ list_len) {
+                                   int* __restrict__ list, int* __restrict__ list_len, int n2,
+                                   const int64_t* __restrict__ rpG) {
   const int lane = threadIdx.x & 31;
+  // the general rows' lengths (from the general CSR)
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n2; g += gridDim.x * blockDim.x)
+    if (gen[g] == 1) len[g] = (int)(rpG[g + 1] - rpG[g]);
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int u = base + threadIdx.x;
     int kind = 0;  // 1: warp sort, 2: block sort
@@ -868,7 +885,11 @@ struct __align__(16) FlatRec {
 __global__ void fr_rowrec_kernel(int n, const int64_t* __restrict__ rp,
                                  const int* __restrict__ vinfo, const int* __restrict__ gen,
                                  const int* __restrict__ kpc, const int* __restrict__ side_v,
-                                 const int64_t* __restrict__ rp2, FlatRec* __restrict__ rec) {
+                                 const int* __restrict__ off, const int* __restrict__ total,
+                                 int n2, int64_t* __restrict__ rp2, FlatRec* __restrict__ rec) {
+  // the new row offsets (exclusive scan of the lengths, then the total)
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= n2; g += gridDim.x * blockDim.x)
+    rp2[g] = g < n2 ? (int64_t)off[g] : (int64_t)*total;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
     const int v = vinfo[u];
     FlatRec o;
@@ -878,7 +899,7 @@ __global__ void fr_rowrec_kernel(int n, const int64_t* __restrict__ rp,
     o.g = v & ~kMovedBit;
     if (!(v & kMovedBit) && gen[v] == 0) {
       const long long b = rp[u];
-      o.base = (int)rp2[v];
+      o.base = off[v];
       o.kp = (int)min((long long)kpc[v], rp[u + 1] - b);
       if (o.kp > 0) o.g0 = side_v[b];
     }
@@ -1096,35 +1117,32 @@ __global__ void __launch_bounds__(kETThreads, sizeof(WT) == 4 ? 5 : 4)
   }
 }
 
-// The moved entries of flat rows with one moved label (one thread per row).
+// The moved entries of the flat rows: blocks below `split` take the rows
+// with one moved label (one thread per row); the others the listed rows with
+// several (one warp per row; the clean entries below label j are the
+// histogram's bins 0 .. j).
 template <typename WT>
-__global__ void fr_moved1_kernel(int n, const int64_t* __restrict__ rp,
-                                 const FlatRec* __restrict__ rec, const int* __restrict__ side_v,
-                                 const WT* __restrict__ side_w, const int* __restrict__ side_c,
-                                 int* __restrict__ col2, WT* __restrict__ w2) {
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-    const FlatRec f = rec[u];
-    if (f.base < 0 || f.kp != 1) continue;
-    const long long b = rp[u];
-    const long long pos = (long long)f.base + side_c[b];
-    col2[pos] = side_v[b];
-    w2[pos] = side_w[b];
+__global__ void fr_moved_kernel(int n, const int64_t* __restrict__ rp,
+                                const FlatRec* __restrict__ rec, const int* __restrict__ list,
+                                const int* __restrict__ list_len, const int* __restrict__ side_v,
+                                const WT* __restrict__ side_w, const int* __restrict__ side_c,
+                                int* __restrict__ col2, WT* __restrict__ w2, int split) {
+  if ((int)blockIdx.x < split) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += split * blockDim.x) {
+      const FlatRec f = rec[u];
+      if (f.base < 0 || f.kp != 1) continue;
+      const long long b = rp[u];
+      const long long pos = (long long)f.base + side_c[b];
+      col2[pos] = side_v[b];
+      w2[pos] = side_w[b];
+    }
+    return;
   }
-}
-
-// ... and of the listed rows with several (one warp per row; the clean
-// entries below label j are the histogram's bins 0 .. j).
-template <typename WT>
-__global__ void fr_moved_list_kernel(int n, const int64_t* __restrict__ rp,
-                                     const FlatRec* __restrict__ rec, const int* __restrict__ list,
-                                     const int* __restrict__ list_len,
-                                     const int* __restrict__ side_v, const WT* __restrict__ side_w,
-                                     const int* __restrict__ side_c, int* __restrict__ col2,
-                                     WT* __restrict__ w2) {
   const int lane = threadIdx.x & 31;
   const int na = list_len[0], nrows = na + list_len[1];
-  for (int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nrows;
-       wi += (gridDim.x * blockDim.x) >> 5) {
+  const int nb = (int)gridDim.x - split;
+  for (int wi = (((int)blockIdx.x - split) * blockDim.x + threadIdx.x) >> 5; wi < nrows;
+       wi += (nb * blockDim.x) >> 5) {
     const int u = wi < na ? list[wi] : list[n - 1 - (wi - na)];
     const FlatRec f = rec[u];
     const long long b = rp[u];
@@ -1215,13 +1233,9 @@ cudaError_t rows_count(int n, long long M, const int64_t* rp, const int* col, co
     return cudaGetLastError();
   }
   const int ntiles = (int)((M + kET - 1) / kET);
-  cudaMemsetAsync(rs.fcl, 0, (size_t)n * sizeof(int), s);
-  cudaMemsetAsync(rs.kpc, 0, (size_t)n * sizeof(int), s);
-  cudaMemsetAsync(rs.tile_ht, 0, (size_t)ntiles * sizeof(int2), s);
-  cudaMemsetAsync(rs.list_len, 0, 2 * sizeof(int), s);
-  fr_vmap_kernel<<<grid_blocks((n + 31) / 32 * 32, 256), 256, 0, s>>>(n, rs.vinfo, root_flags,
-                                                                      root_rank, rs.vmap,
-                                                                      rs.mvbits);
+  fr_vmap_kernel<<<grid_blocks(std::max(n, ntiles), 256), 256, 0, s>>>(
+      n, rs.vinfo, root_flags, root_rank, rs.vmap, rs.mvbits, rs.fcl, rs.kpc, rs.tile_ht, ntiles,
+      rs.list_len);
   fr_count_kernel<<<ntiles, kETThreads, 0, s>>>(n, M, rp, col, rs.mvbits, tile_row, ntiles,
                                                 rs.fcl, rs.tile_ht);
   *launches += 2;
@@ -1250,22 +1264,26 @@ cudaError_t rows_finish(int n, long long M, int n2, const int64_t* rp, const int
                                                         rs.side_v, side_w);
       ++*launches;
     }
-    fr_finalize_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(n, rp, rs.vinfo, rs.gen, rs.fcl, rs.kpc,
-                                                           rs.len, rs.side_c, rs.list,
-                                                           rs.list_len);
+    fr_finalize_kernel<<<grid_blocks(std::max(n, n2), 256), 256, 0, s>>>(
+        n, rp, rs.vinfo, rs.gen, rs.fcl, rs.kpc, rs.len, rs.side_c, rs.list, rs.list_len, n2,
+        rpG);
     fr_tsort_warp_kernel<WT><<<num_sms() * 4, 256, 0, s>>>(rp, rs.vinfo, rs.kpc, rs.list,
                                                            rs.list_len, rs.side_v, side_w);
     fr_tsort_block_kernel<WT><<<num_sms(), kTsortBlock, 0, s>>>(n, rp, rs.vinfo, rs.kpc, rs.list,
                                                                 rs.list_len, rs.side_v, side_w);
     *launches += 3;
   }
-  gen_len_kernel<<<grid_blocks(n2, 256), 256, 0, s>>>(rpG, rs.gen, n2, rs.len);
-  ++*launches;
+  if (!flat) {
+    gen_len_kernel<<<grid_blocks(n2, 256), 256, 0, s>>>(rpG, rs.gen, n2, rs.len);
+    ++*launches;
+  }
   err = scan_exclusive_i32(rs.len, rs.off, n2, rs.part, rs.total, s, launches);
   if (err != cudaSuccess) return err;
-  rp_from_offsets_kernel<<<grid_blocks(n2 + 1, 256), 256, 0, s>>>(rs.off, rs.total, n2, rp2);
+  if (!flat) {
+    rp_from_offsets_kernel<<<grid_blocks(n2 + 1, 256), 256, 0, s>>>(rs.off, rs.total, n2, rp2);
+    ++*launches;
+  }
   cudaMemsetAsync(deg2, 0, (size_t)n2 * sizeof(WT), s);
-  ++*launches;
   if (!flat) {
     const int blocks = (n + kSrWarps - 1) / kSrWarps;
     sr_write_kernel<WT><<<blocks, kSrWarps * 32, 0, s>>>(n, rp, col, w, rs.vinfo, rs.gen, rs.kcnt,
@@ -1276,8 +1294,8 @@ cudaError_t rows_finish(int n, long long M, int n2, const int64_t* rp, const int
     // the round's entry tiles: tile_row still describes the round's graph
     const int ntiles = (int)((M + kET - 1) / kET);
     FlatRec* rec = static_cast<FlatRec*>(rs.rec);
-    fr_rowrec_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(n, rp, rs.vinfo, rs.gen, rs.kpc,
-                                                         rs.side_v, rp2, rec);
+    fr_rowrec_kernel<<<grid_blocks(std::max(n, n2 + 1), 256), 256, 0, s>>>(
+        n, rp, rs.vinfo, rs.gen, rs.kpc, rs.side_v, rs.off, rs.total, n2, rp2, rec);
     const size_t stage = (size_t)(kETThreads / 32) * kStage * 2 * sizeof(int);
     static bool stage_attr = false;
     if (!stage_attr) {
@@ -1290,12 +1308,11 @@ cudaError_t rows_finish(int n, long long M, int n2, const int64_t* rp, const int
                                                       rec, rs.fcl, rs.tile_ht, rs.side_v,
                                                       rs.side_c,
                                                       col2, w2, deg2);
-    fr_moved1_kernel<WT><<<grid_blocks(n, 256), 256, 0, s>>>(n, rp, rec, rs.side_v, side_w,
-                                                             rs.side_c, col2, w2);
-    fr_moved_list_kernel<WT><<<num_sms() * 4, 256, 0, s>>>(n, rp, rec, rs.list, rs.list_len,
-                                                           rs.side_v, side_w, rs.side_c, col2,
-                                                           w2);
-    *launches += 4;
+    const int split = grid_blocks(n, 256);
+    fr_moved_kernel<WT><<<split + num_sms() * 4, 256, 0, s>>>(n, rp, rec, rs.list, rs.list_len,
+                                                              rs.side_v, side_w, rs.side_c, col2,
+                                                              w2, split);
+    *launches += 3;
   }
   const int max_dense = std::min(dense_capacity(n2, rs), ndense);
   if (max_dense > 0) {

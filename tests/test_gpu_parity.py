@@ -371,6 +371,37 @@ def test_contract_rowwise_bit_exact(weights, scale):
     assert v == oracle.noi(n0, rp0, col0, w0)[0]
 
 
+def test_contract_rowwise_full_size_rmat20():
+    """The contraction at the size the bench times: the R-MAT scale-20
+    10-core graph (29 M directed entries) contracted by groups that exercise
+    every part of the entry-tiled path -- 20,000 random pairs, one group of
+    the 64 highest-degree vertices (a dense accumulator), and 200 rows whose
+    neighbours fall into 2..40 groups -- compared entry by entry with the
+    oracle's contraction."""
+    rng = np.random.default_rng(2020)
+    s = synth.workload_rmat_core(20, 10, 2)
+    n, rp, col, w = s.n, s.row_ptr, s.col, s.w.astype(np.int64)
+    d = np.diff(rp)
+    groups = np.arange(n, dtype=np.int32)
+    pick = rng.choice(n, size=40000, replace=False)
+    groups[pick[:20000]] = pick[20000:]
+    top = np.argsort(-d, kind="stable")[:64]
+    groups[top] = int(top[0])
+    cand = np.flatnonzero((d >= 64) & (d <= 4096))
+    for h in rng.choice(cand, size=200, replace=False):
+        k = int(rng.integers(2, 41))
+        nb = col[rp[h]:rp[h + 1]][-k:]
+        groups[nb] = rng.choice(n, size=k, replace=False).astype(np.int32)
+    n2, L = oracle.labels_from_groups(groups)
+    exp = oracle.contract(n, rp, col, w, L, n2)
+    g = make(n, rp, col, w)
+    ro = mc.default_round_options()
+    ro.groups = groups.ctypes.data
+    res = mc.mincut_contract_round(g, ro)
+    assert res["n_out"] == n2
+    assert_csr_equal(mc.mincut_graph_export_csr(g), exp)
+
+
 def test_contract_rowwise_short_rows_bit_exact():
     """Entry tiles that cover more rows than their shared-memory row table
     (rows of about two entries) find rows in the global row offsets; the
