@@ -734,7 +734,9 @@ __device__ __forceinline__ void fr_fill_one(int G, int c, WT W, const int64_t* _
 }
 
 // The general CSR's rows of multi-member groups, transposed (entry tiles of
-// the general CSR).
+// the general CSR).  The gathers of a thread's entries go out together, one
+// level at a time (column, then its member and group state, then the
+// member's row offsets and the slot).
 template <typename WT>
 __global__ void __launch_bounds__(kETThreads)
     fr_fill_kernel(int n2, long long NG, const int64_t* __restrict__ rpG,
@@ -747,12 +749,41 @@ __global__ void __launch_bounds__(kETThreads)
   bool use;
   tile_rows_load1(tr, rpG, n2, tile_rowG, ntiles, blockIdx.x, r0, r1, use);
   const long long e0 = (long long)blockIdx.x * kET;
+  int G[kETItems], c[kETItems], u[kETItems];
+  WT W[kETItems];
+#pragma unroll
   for (int i = 0; i < kETItems; ++i) {
     const long long e = e0 + i * kETThreads + threadIdx.x;
-    if (e >= NG) break;
-    const int G = tile_row_of(tr, rpG, e);
-    if (rep[G] >= 0) continue;  // a single vertex: its entries are clean ones
-    fr_fill_one<WT>(G, colG[e], wG[e], rp, rep, gen, kpc, side_v, side_w);
+    G[i] = -1;
+    c[i] = 0;
+    W[i] = 0;
+    if (e < NG) {
+      G[i] = tile_row_of(tr, rpG, e);
+      c[i] = colG[e];
+      W[i] = wG[e];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kETItems; ++i) {
+    u[i] = -1;
+    // a single vertex's general row holds clean entries only
+    if (G[i] >= 0 && rep[G[i]] < 0) {
+      const int m = rep[c[i]];
+      if (m >= 0 && gen[c[i]] == 0) u[i] = m;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kETItems; ++i) {
+    if (u[i] < 0) continue;
+    const long long b = rp[u[i]];
+    const long long len = rp[u[i] + 1] - b;
+    const int slot = atomicAdd(&kpc[c[i]], 1);
+    // (the slot stays inside the row's span: a row has at least as many
+    // entries as moved labels)
+    if (slot < len) {
+      side_v[b + slot] = G[i];
+      side_w[b + slot] = W[i];
+    }
   }
 }
 
