@@ -144,14 +144,10 @@ __global__ void __launch_bounds__(kETThreads)
 
 // Per chunk of kDenseChunk accumulator slots: the nonzero slots (blockIdx.y =
 // dense slot).  chunk[d * nchunks + c]; len[g] gets the total.
-template <typename WT>
-__device__ __forceinline__ void fr_fill_one(int G, int c, WT W, const int64_t* __restrict__ rp,
-                                            const int* __restrict__ rep,
-                                            const int* __restrict__ gen, int* __restrict__ kpc,
-                                            int* __restrict__ side_v, WT* __restrict__ side_w);
 
 // flat != 0: the nonzero slots of multi-member dense groups towards single
-// vertices are also transposed into those rows' moved lists (fr_fill_one).
+// vertices are also transposed into those rows' moved lists (as in
+// fr_fill_kernel: slot = kpc[label]++ inside the member's row span).
 template <typename WT>
 __global__ void __launch_bounds__(256)
     dense_count_kernel(int n2, const WT* __restrict__ acc, const int* ndense, int max_dense,
@@ -166,11 +162,39 @@ __global__ void __launch_bounds__(256)
   const int G = flat ? dense_group[d] : 0;
   const bool transpose = flat && rep[G] < 0;
   int cntv = 0;
-  for (int i = c * kDenseChunk + threadIdx.x; i < min(n2, (c + 1) * kDenseChunk);
-       i += blockDim.x) {
-    const WT v = acc[base + i];
-    cntv += v != 0;
-    if (transpose && v != 0) fr_fill_one<WT>(G, i, v, rp, rep, gen, kpc, side_v, side_w);
+  constexpr int kPer = kDenseChunk / 256;  // slots per thread (blocks of 256 threads)
+  const int i0 = c * kDenseChunk + threadIdx.x, iend = min(n2, (c + 1) * kDenseChunk);
+  WT v[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int i = i0 + k * 256;
+    v[k] = i < iend ? acc[base + i] : WT(0);
+    cntv += v[k] != 0;
+  }
+  if (transpose) {
+    // the gathers of a thread's slots go out together, level by level
+    int m[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int i = i0 + k * 256;
+      m[k] = -1;
+      if (v[k] != 0) {
+        const int r = rep[i];
+        if (r >= 0 && gen[i] == 0) m[k] = r;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (m[k] < 0) continue;
+      const int i = i0 + k * 256;
+      const long long b = rp[m[k]];
+      const long long len = rp[m[k] + 1] - b;
+      const int slot = atomicAdd(&kpc[i], 1);
+      if (slot < len) {
+        side_v[b + slot] = G;
+        side_w[b + slot] = v[k];
+      }
+    }
   }
   cntv = (int)__reduce_add_sync(FULL, (unsigned)cntv);
   __shared__ int s_w[8];
@@ -704,32 +728,6 @@ __global__ void __launch_bounds__(kETThreads)
   if ((threadIdx.x & 31) == 0) {
     if (hcnt) atomicAdd(&tile_ht[t].x, hcnt);
     if (tcnt) atomicAdd(&tile_ht[t].y, tcnt);
-  }
-}
-
-// Whether label c is a single vertex whose row is rebuilt by the flat path
-// (member u = rep[c]).
-__device__ __forceinline__ int fr_flat_member(const int* __restrict__ rep,
-                                              const int* __restrict__ gen, int c) {
-  const int u = rep[c];
-  return (u >= 0 && gen[c] == 0) ? u : -1;
-}
-
-// Transposes one entry (G, c, W) of a multi-member group's contracted row into
-// the moved list of row c (unordered; sorted later).  The slot stays inside
-// the row's span: a row has at least as many entries as moved labels.
-template <typename WT>
-__device__ __forceinline__ void fr_fill_one(int G, int c, WT W, const int64_t* __restrict__ rp,
-                                            const int* __restrict__ rep,
-                                            const int* __restrict__ gen, int* __restrict__ kpc,
-                                            int* __restrict__ side_v, WT* __restrict__ side_w) {
-  const int u = fr_flat_member(rep, gen, c);
-  if (u < 0) return;
-  const long long b = rp[u];
-  const int slot = atomicAdd(&kpc[c], 1);
-  if (slot < rp[u + 1] - b) {
-    side_v[b + slot] = G;
-    side_w[b + slot] = W;
   }
 }
 
