@@ -426,6 +426,42 @@ def test_contract_rowwise_short_rows_bit_exact():
     assert_csr_equal(mc.mincut_graph_export_csr(g), exp)
 
 
+def test_contract_rowwise_empty_rows_bit_exact():
+    """Isolated vertices (empty rows) spread through a graph large enough for
+    the entry tiles: the row walks of the counting and writing passes step
+    over them, and their groups stay empty rows of the contracted graph."""
+    rng = np.random.default_rng(41)
+    s = synth.cycle_plus(140000, 1.0, 1, 9, 13)
+    n0, rp0, col0, w0 = s.n, s.row_ptr, s.col, s.w.astype(np.int64)
+    # every 97th new id is an isolated vertex
+    n = n0 + n0 // 90 + 10
+    keep = np.ones(n, bool)
+    keep[::97] = False
+    new_ids = np.flatnonzero(keep)[:n0]
+    n = int(new_ids[-1]) + 1
+    new_of_old = new_ids
+    deg_new = np.zeros(n, np.int64)
+    deg_new[new_of_old] = np.diff(rp0)
+    rp = np.concatenate([[0], np.cumsum(deg_new)])
+    row_old = np.repeat(np.arange(n0), np.diff(rp0))
+    u = new_of_old[row_old]
+    v = new_of_old[col0]
+    order = np.lexsort((v, u))
+    col = v[order].astype(np.int32)
+    w = w0[order]
+    assert rp[-1] >= 1 << 18 and (np.diff(rp) == 0).sum() > 1000
+    groups = np.arange(n, dtype=np.int32)
+    pick = rng.choice(np.flatnonzero(np.diff(rp) > 0), size=8000, replace=False)
+    groups[pick[:4000]] = pick[4000:]
+    n2, L = oracle.labels_from_groups(groups)
+    g = make(n, rp, col, w)
+    ro = mc.default_round_options()
+    ro.groups = groups.ctypes.data
+    res = mc.mincut_contract_round(g, ro)
+    assert res["n_out"] == n2
+    assert_csr_equal(mc.mincut_graph_export_csr(g), oracle.contract(n, rp, col, w, L, n2))
+
+
 # ------------------------------------------------------------------ PR flags
 @pytest.mark.parametrize("budget", [-1, 3])
 def test_pr_flags_bit_exact(budget):
