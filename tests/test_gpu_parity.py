@@ -92,6 +92,29 @@ def test_from_csr_large_multi_tile_multi_pass():
     assert_csr_equal(mc.mincut_graph_export_csr(g), canon(n, rp, dst.astype(np.int32), ww))
 
 
+def test_from_csr_above_the_scan_fold():
+    """More than 2048 scan blocks (8.4 M values): the exclusive scans of the
+    canonicalisation take their three-launch form (a separate partials pass)
+    instead of the two-launch one.  10 M raw entries, rows out of order,
+    duplicates; against the oracle's canonical form."""
+    rng = np.random.default_rng(44)
+    n, m = 1 << 20, 5_000_000
+    u = rng.integers(0, n, size=m)
+    v = rng.integers(0, n, size=m)
+    w = rng.integers(1, 9, size=m)
+    src = np.concatenate([u, v]); dst = np.concatenate([v, u]); ww = np.concatenate([w, w])
+    order = rng.permutation(src.size)
+    src, dst, ww = src[order], dst[order], ww[order]
+    o2 = np.argsort(src, kind="stable")
+    src, dst, ww = src[o2], dst[o2], ww[o2]
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, src + 1, 1)
+    rp = np.cumsum(rp)
+    assert rp[-1] > 2048 * 4096
+    g = make(n, rp, dst, ww)
+    assert_csr_equal(mc.mincut_graph_export_csr(g), canon(n, rp, dst.astype(np.int32), ww))
+
+
 @pytest.mark.parametrize("defect", ["none", "self", "zero", "swap", "swap_tile_edge"])
 @pytest.mark.parametrize("big", [False, True])
 def test_from_csr_canonical_input_and_single_defects(defect, big):
