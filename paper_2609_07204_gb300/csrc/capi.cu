@@ -601,6 +601,10 @@ int contract_current(mincut_graph* g, int* n2_out, long long* m2_out, bool compo
   return MINCUT_OK;
 }
 
+// Graphs of at most this many vertices skip the concurrent passes in the
+// rounds after one where they marked almost nothing.
+constexpr int kSkipConcurrentMaxN = 8192;
+
 struct RoundCfg {
   int lp_iters, lp_min_n;
   bool lp_now;
@@ -613,6 +617,7 @@ struct RoundCfg {
   int seq_passes = 1;  // sequential passes when the concurrent ones mark nothing (0: auto)
   int seq_kernel = 0;  // 0: warp-driven passes; 1: block passes (smaller-id ties)
   bool coarsen = false;  // heuristic round: also join every label-propagation cluster
+  bool skip_concurrent = false;  // capforest 1: go straight to the whole-graph passes
   int cf_start;
   int passes, table;
   unsigned long long seed;
@@ -628,6 +633,7 @@ struct RoundOut {
   bool seq_pass = false;
   long long lambda = kInf;
   long long marks_pr = 0, marks_cf = 0;
+  long long marks_cc = 0;  // of marks_cf, those of the concurrent passes
   long long cf_nscanned = 0, cf_nmarks = 0;
   int src = 0;  // which bound source set lambda this round
 };
@@ -709,7 +715,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, c.pr_mask, c.pr_budget, g->parent,
                     flags_dev, g->short_bits, g->st, s, &g->launches));
   }
-  if (c.capforest == 1 && n > 2) {
+  if (c.capforest == 1 && n > 2 && !c.skip_concurrent) {
     CK(cudaMemsetAsync(g->owner, 0, (size_t)n * sizeof(int), s));
     PassConfig pc;
     pc.table = c.table;
@@ -728,6 +734,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     CK(cudaMemcpyAsync(c.pr_flags_host, flags_dev, (size_t)M, cudaMemcpyDeviceToHost, s));
   long long marks = (long long)(g->hst->marks_pr + g->hst->marks_cf);
   o->marks_pr = (long long)g->hst->marks_pr;
+  o->marks_cc = (long long)g->hst->marks_cf;
   // the sequential pass when the round marked nothing (Algorithm 2), and on
   // small graphs (n <= 8192, where a pass costs a few rounds' fixed cost at
   // most) also when it marked so little (fewer edges than n / 64) that
@@ -888,6 +895,7 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
   long long lambda = *lambda_io;
   double rate[2] = {-1.0, -1.0};
   int mode = op.cf_visit == 1 ? 1 : 0;
+  bool skip_cc = false;
   for (;; ++*round_io) {
     const int round = *round_io;
     if (op.max_rounds > 0 && round >= op.max_rounds) break;
@@ -897,6 +905,7 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
       else mode = rate[1] > rate[0] ? 1 : 0;
     }
     c.cf_private = mode;
+    c.skip_concurrent = skip_cc && g->n <= kSkipConcurrentMaxN;
     c.lp_now = lp_allowed && (op.lp_every_round || round == 0);
     c.passes = op.passes > 0 ? op.passes : std::max(32, std::min(g->max_passes, g->n / 4));
     c.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
@@ -906,6 +915,12 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
     int rc = mark_round<WT>(g, c, lambda, &o);
     if (rc) return rc;
     if (o.src) stl->lambda_source = o.src;
+    // concurrent passes that marked almost nothing before the whole-graph
+    // passes had to run: small graphs skip them in the next round
+    // (and keep skipping them while those passes keep running)
+    skip_cc = c.skip_concurrent ? o.seq_pass
+                                : c.capforest == 1 && o.seq_pass &&
+                                      o.marks_cc * 64 < (long long)n_before;
     const bool improved = o.lambda < lambda;
     lambda = std::min(lambda, o.lambda);
     if (o.stopped) break;
