@@ -17,6 +17,7 @@
 // sweep, the cluster cut) take runs of 8 consecutive entries per thread
 // instead, searching a run's first row once and walking forward.
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -386,6 +387,8 @@ __global__ void sym_final_kernel(DevState* st) {
 // gives every entry its own lane group, so that a few long intersections in a
 // tile do not leave the other lanes idle.
 constexpr int kPrQueue = kET;
+// a's entries a lane of a PR3/PR4 intersection searches at once
+constexpr int kPrIlp = 4;
 
 // bits[v / 32] bit v % 32: row v has at most `budget` entries (a 1-bit copy
 // of the budget test that stays in L1 where the row offsets do not).
@@ -401,7 +404,7 @@ __global__ void short_rows_kernel(int n, const int64_t* __restrict__ rp, long lo
 }
 
 template <typename WT>
-__global__ void __launch_bounds__(kETThreads, 5)
+__global__ void __launch_bounds__(kETThreads, 4)
     pr_kernel(int n, long long M, const int64_t* __restrict__ rp, const int* __restrict__ col,
               const WT* __restrict__ w, const WT* __restrict__ deg,
               const int* __restrict__ tile_row, int ntiles, uint32_t mask, long long budget,
@@ -508,32 +511,65 @@ __global__ void __launch_bounds__(kETThreads, 5)
       // still possible (rem = weight of a's unscanned edges bounds the PR4
       // sum still to come; PR3 needs a single edge heavier than da/2 - c).
       long long rem = da - c;
-      int lo = bb;
+      // b's entries are ascending and a lane's neighbours too: once one is
+      // past b's last entry the lane has nothing left to find
+      const int bmax = be > bb ? col[be - 1] : INT_MIN;
       bool lane_done = false;
-      // lane r of the group takes a's entries ab + r, ab + r + g, ...
-      for (int base = ab; base < ae; base += g) {
-        const int ea = base + r;
+      // lane r of the group takes a's entries ab + r, ab + r + g, ..., kPrIlp
+      // of them per step; their lower bounds in b's row are searched in
+      // lockstep (over the same row every search takes the same number of
+      // halvings), so a lane keeps kPrIlp loads in flight per halving
+      // instead of walking its entries one dependent chain after another
+      for (int base = ab; base < ae; base += g * kPrIlp) {
+        int xs[kPrIlp], pos[kPrIlp];
+        WT ca[kPrIlp];
+        bool act[kPrIlp];
+#pragma unroll
+        for (int j = 0; j < kPrIlp; ++j) {
+          const int ea = base + r + j * g;
+          act[j] = ea < ae && !lane_done;
+          xs[j] = act[j] ? col[ea] : INT_MAX;
+          ca[j] = act[j] ? w[ea] : (WT)0;
+        }
         long long add = 0, used = 0;
         bool p3 = false;
-        if (ea < ae && !lane_done) {
-          const int x = col[ea];
-          if (x != u && x != v) {
-            const long long cax = (long long)w[ea];
-            used = cax;
-            // a lane's neighbours ascend, so its search window only moves right
-            int hi = be;
-            while (lo < hi) {
-              const int mid = (int)(((unsigned)lo + (unsigned)hi) >> 1);
-              if (col[mid] < x) lo = mid + 1; else hi = mid;
-            }
-            if (lo >= be) {
-              lane_done = true;
-            } else if (col[lo] == x) {
-              const long long cbx = (long long)w[lo];
-              const long long cux = a_is_u ? cax : cbx, cvx = a_is_u ? cbx : cax;
-              add = cux < cvx ? cux : cvx;
-              p3 = du < 2 * (c + cux) && dv < 2 * (c + cvx);
-            }
+#pragma unroll
+        for (int j = 0; j < kPrIlp; ++j) {
+          if (xs[j] == u || xs[j] == v) act[j] = false;
+          if (act[j]) used += (long long)ca[j];
+          if (act[j] && xs[j] > bmax) {
+            act[j] = false;
+            lane_done = true;
+          }
+          pos[j] = bb;
+        }
+        // answer (first entry >= x) in [pos, pos + nn]; lanes whose x are
+        // all inactive skip the loads but not the loop
+        int nn = be - bb;
+        while (nn > 1) {
+          const int half = nn >> 1;
+#pragma unroll
+          for (int j = 0; j < kPrIlp; ++j)
+            if (act[j] && col[pos[j] + half - 1] < xs[j]) pos[j] += half;
+          nn -= half;
+        }
+        int hit[kPrIlp];
+#pragma unroll
+        for (int j = 0; j < kPrIlp; ++j) {
+          hit[j] = -1;
+          if (act[j]) {
+            const int c0 = col[pos[j]];
+            const int c1 = pos[j] + 1 < be ? col[pos[j] + 1] : INT_MAX;
+            hit[j] = c0 == xs[j] ? pos[j] : c1 == xs[j] ? pos[j] + 1 : -1;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kPrIlp; ++j) {
+          if (hit[j] >= 0) {
+            const long long cax = (long long)ca[j], cbx = (long long)w[hit[j]];
+            const long long cux = a_is_u ? cax : cbx, cvx = a_is_u ? cbx : cax;
+            add += cux < cvx ? cux : cvx;
+            p3 = p3 || (du < 2 * (c + cux) && dv < 2 * (c + cvx));
           }
         }
         for (int o = g >> 1; o > 0; o >>= 1) {
