@@ -550,6 +550,72 @@ def test_pr_flags_bit_exact_hub_rows(budget, big):
     assert res["marks_pr"] == int(((exp != 0) & (src < c[1])).sum())
 
 
+def _pr_clustered_graph(rng, n, big):
+    """Rows of two to four heavy entries (they set the degree bound above the
+    light edges' weights), rows whose ids sit in two narrow windows at both
+    ends of the id range, and a light clique over one window (many common
+    neighbours), so that the PR3/PR4 searches meet short and long rows,
+    uneven id spreads and several search steps per lane."""
+    win = list(range(0, 40)) + list(range(n - 40, n))
+    hubs = [n // 2, n // 2 + 1, n // 3]
+    light, heavy = {}, {}
+    for h in hubs:
+        for x in win:
+            light[(min(h, x), max(h, x))] = int(rng.integers(1, 13))
+    for i in range(40):
+        for j in range(i + 1, 40):
+            if rng.random() < 0.6:
+                light[(i, j)] = int(rng.integers(1, 13))
+    for v in range(40, n - 40):
+        if v in hubs:
+            continue
+        for k in rng.choice(len(win), 2 + v % 3, replace=False):
+            x = win[int(k)]
+            heavy[(min(v, x), max(v, x))] = int(rng.integers(20, 41))
+    edges = sorted(set(light) | set(heavy))
+    scale = 1 << 25 if big else 1  # big: 64-bit totals
+    wts = [scale * heavy.get(e, light.get(e, 0)) for e in edges]
+    return canon(n, *G.from_edges(n, edges, wts))
+
+
+@pytest.mark.parametrize("budget,big", [(-1, False), (16, False), (3, False), (-1, True)])
+def test_pr_clustered_ids_flags_and_round_bit_exact(budget, big):
+    """PR flags entry by entry, then a PR-only round without a flags output
+    (the early-exit form the solve runs) contracted exactly like the
+    oracle's round with the same bound and budget."""
+    rng = np.random.default_rng(5 + budget + 7 * big)
+    for n in (300, 2500):
+        c = _pr_clustered_graph(rng, n, big)
+        M = int(c[0][-1])
+        lam = int(oracle.degrees(n, *c).min())
+        flags = np.zeros(M, np.uint8)
+        g = make(n, c[0], c[1], c[2])
+        ro = mc.default_round_options()
+        ro.capforest = 0
+        ro.lp_iters = 0
+        ro.pr_budget = budget
+        ro.pr_flags_out = flags.ctypes.data
+        res = mc.mincut_contract_round(g, ro)
+        assert not res["stopped"]
+        exp = oracle.pr_marks(n, *c, lam, 0xF, budget)
+        assert np.array_equal(flags, exp)
+        # the intersections decide marks that PR1/PR2 do not
+        assert int(((exp & 12 != 0) & (exp & 3 == 0)).sum()) > 0
+        g.destroy()
+        g = make(n, c[0], c[1], c[2])
+        ro = mc.default_round_options()
+        ro.capforest = 0
+        ro.lp_iters = 0
+        ro.pr_budget = budget
+        res = mc.mincut_contract_round(g, ro)
+        n2, rp2, col2, w2, info = oracle.round_(n, *c, lambda_in=INF, lp_iters=0,
+                                                pr_mask=0xF, pr_budget=budget, capforest=False)
+        assert res["lambda_out"] == info["lambda"]
+        assert res["n_out"] == n2
+        assert_csr_equal(mc.mincut_graph_export_csr(g), (rp2, col2, w2))
+        g.destroy()
+
+
 # ------------------------------------------------ deterministic CAPFOREST pass
 def _det_round(n, c, lam_in=INF, start=0, lp_iters=0, lp_min_n=10000, pr_mask=0xF,
                capforest=2):
