@@ -75,7 +75,7 @@ ALG_BYTES = {
 # capture summarised under profiles/), scaled to a launch by its units.  A
 # kernel changed since its capture has no entry here (traffic: null).
 TRAFFIC_PER_UNIT = {
-    "pr_marks": (400.845568e6 + 3.486208e6) / 29031216,
+    "pr_marks": (422.862080e6 + 3.253248e6) / 29031216,
 }
 
 
