@@ -78,7 +78,8 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
                                  unsigned long long* __restrict__ pass_best,
                                  int* __restrict__ pass_len, int total_passes, int table,
                                  unsigned long long seed, int* pass_counter, DevState* st,
-                                 BatchView bv, int batch, int priv) {
+                                 BatchView bv, int batch, int priv, long long skip_pr) {
+  if (skip_pr >= 0 && (long long)*(volatile unsigned long long*)&st->marks_pr >= skip_pr) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -253,9 +254,19 @@ __global__ void cf_passes_kernel(int n, const int64_t* __restrict__ rp, const in
 }
 
 __global__ void cf_best_kernel(const unsigned long long* __restrict__ pass_best,
-                               const int* __restrict__ pass_len, int passes, DevState* st) {
+                               const int* __restrict__ pass_len, int passes, DevState* st,
+                               long long skip_pr) {
   __shared__ unsigned long long sv[32];
   __shared__ int sp[32];
+  if (skip_pr >= 0 && (long long)*(volatile unsigned long long*)&st->marks_pr >= skip_pr) {
+    // the passes were skipped: their per-pass words are stale
+    if (threadIdx.x == 0) {
+      st->cf_val = ~0ull;
+      st->cf_pass = -1;
+      st->cf_len = 0;
+    }
+    return;
+  }
   unsigned long long bv = ~0ull;
   int bp = 0x7fffffff;
   for (int p = threadIdx.x; p < passes; p += blockDim.x) {
@@ -734,10 +745,10 @@ cudaError_t capforest_passes(int n, const int64_t* rp, const int* col, const WT*
   if (bv) v = *bv;
   cf_passes_kernel<WT><<<blocks, pc.warps_per_block * 32, smem, s>>>(
       n, rp, col, w, deg, owner, parent, visit_log, pass_best, pass_len, pc.passes, pc.table,
-      pc.seed, pass_counter, st, v, bv ? 1 : 0, pc.private_visit);
+      pc.seed, pass_counter, st, v, bv ? 1 : 0, pc.private_visit, bv ? -1ll : pc.skip_pr);
   ++*launches;
   if (!bv) {
-    cf_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, pc.passes, st);
+    cf_best_kernel<<<1, 1024, 0, s>>>(pass_best, pass_len, pc.passes, st, pc.skip_pr);
     ++*launches;
   }
   return cudaGetLastError();

@@ -618,6 +618,9 @@ struct RoundCfg {
   int seq_kernel = 0;  // 0: warp-driven passes; 1: block passes (smaller-id ties)
   bool coarsen = false;  // heuristic round: also join every label-propagation cluster
   bool skip_concurrent = false;  // capforest 1: go straight to the whole-graph passes
+  // capforest 1, >= 0: the concurrent passes stand down (decided on the
+  // device) when the round's PR tests hooked at least this many edges
+  long long cc_skip_pr = -1;
   int cf_start;
   int passes, table;
   unsigned long long seed;
@@ -634,6 +637,7 @@ struct RoundOut {
   long long lambda = kInf;
   long long marks_pr = 0, marks_cf = 0;
   long long marks_cc = 0;  // of marks_cf, those of the concurrent passes
+  bool cc_ran = false;     // the concurrent passes ran (were not skipped)
   long long cf_nscanned = 0, cf_nmarks = 0;
   int src = 0;  // which bound source set lambda this round
 };
@@ -723,6 +727,7 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     pc.passes = std::min(c.passes, g->max_passes);
     pc.seed = c.seed;
     pc.private_visit = c.cf_private;
+    pc.skip_pr = c.cc_skip_pr;
     ProfScope ps(P_CF_PASSES, M, s);
     CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log,
                             g->pass_best, g->pass_len, g->pass_counter, pc, g->st, s,
@@ -735,6 +740,8 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
   long long marks = (long long)(g->hst->marks_pr + g->hst->marks_cf);
   o->marks_pr = (long long)g->hst->marks_pr;
   o->marks_cc = (long long)g->hst->marks_cf;
+  o->cc_ran = c.capforest == 1 && n > 2 && !c.skip_concurrent &&
+              !(c.cc_skip_pr >= 0 && o->marks_pr >= c.cc_skip_pr);
   // the sequential pass when the round marked nothing (Algorithm 2), and on
   // small graphs (n <= 8192, where a pass costs a few rounds' fixed cost at
   // most) also when it marked so little (fewer edges than n / 64) that
@@ -896,6 +903,9 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
   double rate[2] = {-1.0, -1.0};
   int mode = op.cf_visit == 1 ? 1 : 0;
   bool skip_cc = false;
+  // the concurrent passes marked fewer than n / 64 edges the last time they
+  // ran: they stand down in rounds whose PR tests hook at least n / 64
+  bool cc_low = false;
   for (;; ++*round_io) {
     const int round = *round_io;
     if (op.max_rounds > 0 && round >= op.max_rounds) break;
@@ -906,6 +916,7 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
     }
     c.cf_private = mode;
     c.skip_concurrent = skip_cc && g->n <= kSkipConcurrentMaxN;
+    c.cc_skip_pr = cc_low && c.capforest == 1 && op.cf_visit != 2 ? (g->n + 63) / 64 : -1;
     c.lp_now = lp_allowed && (op.lp_every_round || round == 0);
     c.passes = op.passes > 0 ? op.passes : std::max(32, std::min(g->max_passes, g->n / 4));
     c.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
@@ -921,6 +932,7 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
     skip_cc = c.skip_concurrent ? o.seq_pass
                                 : c.capforest == 1 && o.seq_pass &&
                                       o.marks_cc * 64 < (long long)n_before;
+    if (o.cc_ran) cc_low = o.marks_cc * 64 < (long long)n_before;
     const bool improved = o.lambda < lambda;
     lambda = std::min(lambda, o.lambda);
     if (o.stopped) break;

@@ -248,6 +248,10 @@ struct PassConfig {
   int warps_per_block;
   unsigned long long seed;
   int private_visit = 0;  // 1: each pass has its own visit set (owner is not used)
+  // >= 0: the passes do nothing (no marks, no bound) when the round's PR
+  // tests already hooked at least this many edges (read on the device from
+  // st->marks_pr, so the choice needs no host synchronisation)
+  long long skip_pr = -1;
 };
 // Concurrent CAPFOREST passes (Algorithm 1).  owner[n] must be zero on entry
 // (the shared visit array T); visit_log[passes*table], pass_best/pass_len
