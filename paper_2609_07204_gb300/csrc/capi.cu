@@ -211,6 +211,21 @@ struct mincut_graph {
   int* bw_scratch = nullptr;
   long long bw_scratch_words = 0;
   int bw_slots = 0;
+  // the launches of a solve whose graphs all take the one-warp solver,
+  // captured as a CUDA graph at the second solve with the same split
+  cudaGraphExec_t bw_exec = nullptr;
+  cudaStream_t bw_capture = nullptr;  // private stream the launches are captured on
+  int bw_exec_launches = 0;
+  struct BwKey {
+    int threshold = -1;
+    const int* scratch = nullptr;
+    const int* voff = nullptr;  // the offsets buffer in use (round solves swap it)
+    unsigned pr = 0;
+    bool operator==(const BwKey& o) const {
+      return threshold == o.threshold && scratch == o.scratch && voff == o.voff && pr == o.pr;
+    }
+  } bw_key, bw_exec_key;
+  int bw_key_runs = 0;
   unsigned long long* batch_levels = nullptr;
   long long* batch_vals = nullptr;
   long long spin_limit = 1ll << 22;
@@ -349,6 +364,15 @@ bool galloc(mincut_graph* g, T** out, long long count) {
 }
 
 void free_all(mincut_graph* g) {
+  if (g->bw_exec) {
+    cudaStreamSynchronize(g->stream);
+    cudaGraphExecDestroy(g->bw_exec);
+    g->bw_exec = nullptr;
+  }
+  if (g->bw_capture) {
+    cudaStreamDestroy(g->bw_capture);
+    g->bw_capture = nullptr;
+  }
   for (auto& a : g->allocs) {
     if (g->user_alloc) g->alloc.free(a.p, a.bytes, (void*)g->stream, g->alloc.ctx);
     else cudaFreeAsync(a.p, g->stream);
@@ -1447,9 +1471,38 @@ int bw_prepare(mincut_graph* g, int threshold) {
   return MINCUT_OK;
 }
 
+// A solve whose graphs all take the one-warp solver: state reset, then the
+// warp solver over the whole list (no round kernels, no host decisions
+// before the completion check).  Only stream-ordered calls, so that it can
+// be captured.
+cudaError_t bw_enqueue(mincut_graph* g, uint32_t pr, cudaStream_t s, int* launches) {
+  BatchState& b = g->batch;
+  const int G = b.G;
+  cudaError_t e = cudaMemsetAsync(g->st, 0, sizeof(DevState), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.voff, b.voff0, (size_t)(G + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
+                        s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.gid, b.gid0, (size_t)g->n0 * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = batch_start(G, b.lam_g, b.done_g, s, launches);
+  if (e == cudaSuccess) {
+    iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
+    ++*launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->side0, 0, (size_t)g->n0, s);
+  if (e == cudaSuccess) e = batch_warp_mark(g->bw_list, g->bw_count, b.done_g, g->st, s, launches);
+  if (e == cudaSuccess)
+    e = batch_warp_solve(g->bw_list, g->bw_count, g->bw_cursor, b.voff0, g->rp0, g->col0,
+                         (const int*)g->w0, g->bw_scratch, g->bw_slots, g->bw_nmax, g->bw_mmax,
+                         pr, b.lam_g, g->side0, g->st, s, launches);
+  return e;
+}
+
 template <typename WT>
 int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_values,
-                     uint64_t* side_bitmap, mincut_stats* stats, int small_n) {
+                     uint64_t* side_bitmap, mincut_stats* stats, int small_n,
+                     bool allow_graph) {
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = g->stream;
   BatchState& b = g->batch;
@@ -1460,87 +1513,129 @@ int batch_solve_impl(mincut_graph* g, const mincut_options& op, int64_t* cut_val
   g->M = g->M0;
   g->m_pending = false;
   if (op.spin_limit > 0) g->spin_limit = op.spin_limit;
-  CK(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
-  CK(cudaMemcpyAsync(b.voff, b.voff0, (size_t)(G + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(b.gid, b.gid0, (size_t)g->n0 * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  CK(batch_start(G, b.lam_g, b.done_g, s, &g->launches));
-  iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
-  ++g->launches;
-  CK(cudaMemsetAsync(g->side0, 0, (size_t)g->n0, s));
   // the small graphs are the warp solver's: the round kernels treat them as done
   {
     const int rc0 = bw_prepare(g, small_n);
     if (rc0) return rc0;
   }
-  if (g->bw_count > 0)
-    CK(batch_warp_mark(g->bw_list, g->bw_count, b.done_g, g->st, s, &g->launches));
   mincut_stats stl{};
   stl.n_input = g->n0;
   stl.m_input = g->M0 / 2;
-  const int table = op.pass_table > 0 ? std::min(op.pass_table, g->max_table) : g->max_table;
   const int max_rounds = op.max_rounds > 0 ? op.max_rounds : g->max_graph_n + 8;
-  for (int round = 0; g->bw_count < G && round < max_rounds; ++round) {
-    const int n = g->n;
-    const long long M = g->M;
-    const int64_t* rp = g->crp();
-    const int* col = g->ccol();
-    const WT* w = (const WT*)g->cw();
-    const WT* deg = (const WT*)g->cdeg();
-    reset_round_kernel<<<1, 1, 0, s>>>(g->st);
+  if (G > 0 && g->bw_count == G && !tl_prof) {
+    // every graph on the one-warp solver (no profiling): the same launches
+    // on every solve of this batch, replayed from a CUDA graph once the
+    // same split comes a second time (a batch solved once pays no capture);
+    // captured on a private stream, since the caller's may be the legacy one
+    mincut_graph::BwKey key;
+    key.threshold = g->bw_threshold;
+    key.scratch = g->bw_scratch;
+    key.voff = b.voff;
+    key.pr = op.pr_mask & 3u;
+    g->bw_key_runs = key == g->bw_key ? g->bw_key_runs + 1 : 1;
+    g->bw_key = key;
+    if (g->bw_exec && !(g->bw_exec_key == key)) {
+      CK(cudaStreamSynchronize(s));
+      cudaGraphExecDestroy(g->bw_exec);
+      g->bw_exec = nullptr;
+    }
+    if (!g->bw_exec && allow_graph && g->bw_key_runs >= 2) {
+      if (!g->bw_capture) CK(cudaStreamCreateWithFlags(&g->bw_capture, cudaStreamNonBlocking));
+      int nl = 0;
+      CK(cudaStreamBeginCapture(g->bw_capture, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = bw_enqueue(g, key.pr, g->bw_capture, &nl);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(g->bw_capture, &graph);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&g->bw_exec, graph, 0ull);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g->bw_exec = nullptr;
+        return fail(MINCUT_ERR_CUDA, "capturing the batch's launches: %s", cudaGetErrorString(e));
+      }
+      g->bw_exec_key = key;
+      g->bw_exec_launches = nl;
+    }
+    if (g->bw_exec) {
+      CK(cudaGraphLaunch(g->bw_exec, s));
+      g->launches += g->bw_exec_launches;
+    } else {
+      CK(bw_enqueue(g, key.pr, s, &g->launches));
+    }
+  } else {
+    CK(cudaMemsetAsync(g->st, 0, sizeof(DevState), s));
+    CK(cudaMemcpyAsync(b.voff, b.voff0, (size_t)(G + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(b.gid, b.gid0, (size_t)g->n0 * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    CK(batch_start(G, b.lam_g, b.done_g, s, &g->launches));
+    iota_kernel<<<std::min((g->n0 + 255) / 256, g->sms * 8), 256, 0, s>>>(g->map0, g->n0);
     ++g->launches;
-    CK(batch_round_reset(G, b, s, &g->launches));
-    { ProfScope ps(P_DEGREE, n, s);
-      CK(batch_degree_bound<WT>(n, G, deg, b, &g->st->batch_done, s, &g->launches)); }
-    { ProfScope ps(P_TILES, n, s);
-      CK(tile_rows(rp, n, M, g->tile_row, s, &g->launches)); }
-    { ProfScope ps(P_UF, n, s);
-      CK(uf_init(g->parent, n, s, &g->launches)); }
-    const BatchView v = b.view();
-    if (op.pr_mask) {
-      ProfScope ps(P_PR, M, s);
-      CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, op.pr_mask, op.pr_budget, g->parent,
-                      nullptr, g->short_bits, g->st, s, &g->launches, &v));
+    CK(cudaMemsetAsync(g->side0, 0, (size_t)g->n0, s));
+    if (g->bw_count > 0)
+      CK(batch_warp_mark(g->bw_list, g->bw_count, b.done_g, g->st, s, &g->launches));
+    const int table = op.pass_table > 0 ? std::min(op.pass_table, g->max_table) : g->max_table;
+    for (int round = 0; g->bw_count < G && round < max_rounds; ++round) {
+      const int n = g->n;
+      const long long M = g->M;
+      const int64_t* rp = g->crp();
+      const int* col = g->ccol();
+      const WT* w = (const WT*)g->cw();
+      const WT* deg = (const WT*)g->cdeg();
+      reset_round_kernel<<<1, 1, 0, s>>>(g->st);
+      ++g->launches;
+      CK(batch_round_reset(G, b, s, &g->launches));
+      { ProfScope ps(P_DEGREE, n, s);
+        CK(batch_degree_bound<WT>(n, G, deg, b, &g->st->batch_done, s, &g->launches)); }
+      { ProfScope ps(P_TILES, n, s);
+        CK(tile_rows(rp, n, M, g->tile_row, s, &g->launches)); }
+      { ProfScope ps(P_UF, n, s);
+        CK(uf_init(g->parent, n, s, &g->launches)); }
+      const BatchView v = b.view();
+      if (op.pr_mask) {
+        ProfScope ps(P_PR, M, s);
+        CK(pr_marks<WT>(n, M, rp, col, w, deg, g->tile_row, op.pr_mask, op.pr_budget, g->parent,
+                        nullptr, g->short_bits, g->st, s, &g->launches, &v));
+      }
+      if (!op.deterministic) {
+        ProfScope ps(P_CF_PASSES, M, s);
+        CK(cudaMemsetAsync(g->owner, 0, (size_t)n * sizeof(int), s));
+        PassConfig pc;
+        pc.table = table;
+        pc.warps_per_block = 4;
+        pc.passes = op.passes > 0 ? std::min(op.passes, g->max_passes)
+                                  : std::max(32, std::min(g->max_passes, n / 4));
+        pc.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
+        pc.private_visit = op.cf_visit == 1 ? 1 : 0;
+        CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log, g->pass_best,
+                                g->pass_len, g->pass_counter, pc, g->st, s, &g->launches, &v));
+      }
+      { ProfScope ps(P_CF_SEQ, M, s);
+        CK(capforest_sequential_batch<WT>(G, rp, col, w, deg, g->parent, (WT*)g->seq_r,
+                                          g->batch_levels, b.level_off, g->seq_order,
+                                          g->max_graph_n, op.deterministic ? 1 : 0, v, g->st, s,
+                                          &g->launches)); }
+      { ProfScope ps(P_WITNESS, g->n0, s);
+        CK(batch_witness(G, g->n0, b, g->visit_log, table, g->pass_len, g->seq_order, g->cur_side,
+                         g->map0, g->side0, g->st, s, &g->launches)); }
+      CK(batch_collapse(n, b, g->parent, s, &g->launches));
+      stl.rounds++;
+      stl.entries_processed += M;
+      int n2 = 0;
+      long long m2 = 0;
+      int rc = contract_current<WT>(g, &n2, &m2, true);
+      if (rc) return rc;
+      CK(batch_new_offsets(G, b, g->rank, g->st, s, &g->launches));
+      std::swap(b.voff, b.voff_next);
+      CK(batch_gid(b.voff, G, n2, b.gid, s, &g->launches));
+      if (g->hst->batch_done >= G) break;
     }
-    if (!op.deterministic) {
-      ProfScope ps(P_CF_PASSES, M, s);
-      CK(cudaMemsetAsync(g->owner, 0, (size_t)n * sizeof(int), s));
-      PassConfig pc;
-      pc.table = table;
-      pc.warps_per_block = 4;
-      pc.passes = op.passes > 0 ? std::min(op.passes, g->max_passes)
-                                : std::max(32, std::min(g->max_passes, n / 4));
-      pc.seed = op.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1);
-      pc.private_visit = op.cf_visit == 1 ? 1 : 0;
-      CK(capforest_passes<WT>(n, rp, col, w, deg, g->owner, g->parent, g->visit_log, g->pass_best,
-                              g->pass_len, g->pass_counter, pc, g->st, s, &g->launches, &v));
+    if (g->bw_count > 0) {
+      ProfScope ps(P_BATCH_WARP, g->bw_count, s);
+      // PR1 / PR2 only: on one warp the PR3 / PR4 intersections cost several
+      // times the rest of a graph's solve (the pass of each round marks anyway)
+      CK(batch_warp_solve(g->bw_list, g->bw_count, g->bw_cursor, b.voff0, g->rp0, g->col0,
+                          (const int*)g->w0, g->bw_scratch, g->bw_slots, g->bw_nmax, g->bw_mmax,
+                          op.pr_mask & 3u, b.lam_g, g->side0, g->st, s, &g->launches));
     }
-    { ProfScope ps(P_CF_SEQ, M, s);
-      CK(capforest_sequential_batch<WT>(G, rp, col, w, deg, g->parent, (WT*)g->seq_r,
-                                        g->batch_levels, b.level_off, g->seq_order,
-                                        g->max_graph_n, op.deterministic ? 1 : 0, v, g->st, s,
-                                        &g->launches)); }
-    { ProfScope ps(P_WITNESS, g->n0, s);
-      CK(batch_witness(G, g->n0, b, g->visit_log, table, g->pass_len, g->seq_order, g->cur_side,
-                       g->map0, g->side0, g->st, s, &g->launches)); }
-    CK(batch_collapse(n, b, g->parent, s, &g->launches));
-    stl.rounds++;
-    stl.entries_processed += M;
-    int n2 = 0;
-    long long m2 = 0;
-    int rc = contract_current<WT>(g, &n2, &m2, true);
-    if (rc) return rc;
-    CK(batch_new_offsets(G, b, g->rank, g->st, s, &g->launches));
-    std::swap(b.voff, b.voff_next);
-    CK(batch_gid(b.voff, G, n2, b.gid, s, &g->launches));
-    if (g->hst->batch_done >= G) break;
-  }
-  if (g->bw_count > 0) {
-    ProfScope ps(P_BATCH_WARP, g->bw_count, s);
-    // PR1 / PR2 only: on one warp the PR3 / PR4 intersections cost several
-    // times the rest of a graph's solve (the pass of each round marks anyway)
-    CK(batch_warp_solve(g->bw_list, g->bw_count, g->bw_cursor, b.voff0, g->rp0, g->col0,
-                        (const int*)g->w0, g->bw_scratch, g->bw_slots, g->bw_nmax, g->bw_mmax,
-                        op.pr_mask & 3u, b.lam_g, g->side0, g->st, s, &g->launches));
   }
   int rc = sync_state(g);
   if (rc) return rc;
@@ -1825,7 +1920,7 @@ int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut
         last_count = cnt;
       }
       const auto t0 = std::chrono::steady_clock::now();
-      const int r = batch_solve_impl<int32_t>(g, op, tmp.data(), nullptr, nullptr, t);
+      const int r = batch_solve_impl<int32_t>(g, op, tmp.data(), nullptr, nullptr, t, false);
       if (r) return r;
       const double ms =
           std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1840,7 +1935,7 @@ int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut
   int rc;
   {
     ProfGuard pg(g, op.profile != 0);
-    rc = batch_solve_impl<int32_t>(g, op, cut_values, side_bitmap, stats, small_n);
+    rc = batch_solve_impl<int32_t>(g, op, cut_values, side_bitmap, stats, small_n, true);
   }
   g->cur = -1;
   g->n = g->n0;

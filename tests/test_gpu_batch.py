@@ -95,6 +95,47 @@ def test_batch_warp_path_weighted_and_pr_variants():
         _check_batch(graphs, expect, mc.default_options(batch_small_n=2048, pr_mask=mask))
 
 
+def _solve_and_check(B, vo, graphs, expect, opts):
+    vals, bm, st = mc.mincut_batch_solve(B, opts)
+    side_all = mc.bitmap_to_side(bm, int(vo[-1]))
+    for i, (n, grp, gcol, gw) in enumerate(graphs):
+        assert vals[i] == expect[i], (i, n, vals[i], expect[i])
+        side = side_all[vo[i]:vo[i + 1]]
+        assert side[0] == 0 and 0 < side.sum() < n, i
+        assert oracle.cut_weight(n, grp, gcol, gw, side) == vals[i], i
+    return st
+
+
+@pytest.mark.parametrize("own_stream", [False, True])
+def test_batch_repeated_solves_replay_captured_launches(own_stream):
+    """Solving the same batch again (every graph on its own warp) replays the
+    launches captured as a CUDA graph at the second solve; a changed PR mask,
+    a round-kernel solve in between (which swaps the offsets buffer) and a
+    profiled solve take the direct launches or a new capture.  Every solve
+    matches the oracle."""
+    graphs, expect = [], []
+    for i in range(160):
+        s = synth.batch_graph(4, 1000 + i)
+        graphs.append((s.n, s.row_ptr, s.col, s.w.astype(np.int64)))
+        expect.append(oracle.noi(s.n, s.row_ptr, s.col, s.w)[0])
+    vo, rp, col, w = mc.pack_graphs(graphs)
+    strm = torch.cuda.Stream() if own_stream else None
+    B = mc.mincut_batch_from_csr(vo, rp, col, w, stream=strm)
+    warp = mc.default_options(batch_small_n=2048)
+    launches = set()
+    for _ in range(4):
+        launches.add(_solve_and_check(B, vo, graphs, expect, warp)["kernel_launches"])
+    assert len(launches) == 1  # the replayed graph launches the same kernels
+    for _ in range(3):
+        _solve_and_check(B, vo, graphs, expect, mc.default_options(batch_small_n=2048, pr_mask=0x1))
+    _solve_and_check(B, vo, graphs, expect, mc.default_options(batch_small_n=-1))
+    for _ in range(3):
+        _solve_and_check(B, vo, graphs, expect, warp)
+    _solve_and_check(B, vo, graphs, expect, mc.default_options(batch_small_n=2048, profile=1))
+    _solve_and_check(B, vo, graphs, expect, warp)
+    B.destroy()
+
+
 def test_batch_rejects_cross_graph_edge_and_tiny_graph():
     c1 = oracle.canonicalize(3, *G.cycle(3))
     c2 = oracle.canonicalize(3, *G.cycle(3))
