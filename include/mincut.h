@@ -234,7 +234,11 @@ int mincut_batch_from_csr(int64_t num_graphs, const int64_t* vertex_offsets,
  * first); the others share one set of round kernels, each graph with its own
  * bound, stop test and witness.  cut_values: host int64[num_graphs].  side_bitmap (nullable, host or device, ceil(n/64)
  * words): bit v = 1 iff vertex v is on the side of its graph's minimum cut
- * that does not hold the graph's first vertex. */
+ * that does not hold the graph's first vertex.  When every graph takes the
+ * one-warp solver and profiling is off, the second solve of the batch with
+ * the same split captures that solve's launches as a CUDA graph (on a stream
+ * the library creates) and later solves replay it on the batch's stream;
+ * both are released by mincut_graph_destroy. */
 int mincut_batch_solve(mincut_graph* g, const mincut_options* opts, int64_t* cut_values,
                        uint64_t* side_bitmap, mincut_stats* stats);
 
