@@ -645,6 +645,9 @@ struct RoundCfg {
   // capforest 1, >= 0: the concurrent passes stand down (decided on the
   // device) when the round's PR tests hooked at least this many edges
   long long cc_skip_pr = -1;
+  // skip_concurrent rounds: run the whole passes without first reading the
+  // PR count (set while the rounds barely shrink the graph)
+  bool eager_seq = false;
   int cf_start;
   int passes, table;
   unsigned long long seed;
@@ -757,22 +760,31 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
                             g->pass_best, g->pass_len, g->pass_counter, pc, g->st, s,
                             &g->launches));
   }
-  rc = sync_state(g);
-  if (rc) return rc;
-  if (flags_dev && M > 0)
-    CK(cudaMemcpyAsync(c.pr_flags_host, flags_dev, (size_t)M, cudaMemcpyDeviceToHost, s));
-  long long marks = (long long)(g->hst->marks_pr + g->hst->marks_cf);
-  o->marks_pr = (long long)g->hst->marks_pr;
-  o->marks_cc = (long long)g->hst->marks_cf;
-  o->cc_ran = c.capforest == 1 && n > 2 && !c.skip_concurrent &&
-              !(c.cc_skip_pr >= 0 && o->marks_pr >= c.cc_skip_pr);
-  // the sequential pass when the round marked nothing (Algorithm 2), and on
-  // small graphs (n <= 8192, where a pass costs a few rounds' fixed cost at
-  // most) also when it marked so little (fewer edges than n / 64) that
-  // contracting would spend a whole round on almost no vertices; its marks
-  // only add
-  bool need_seq = c.capforest == 2 || c.capforest == 4 ||
-                  (c.capforest == 1 && (marks == 0 || (n <= 8192 && marks * 64 < n)));
+  // a round whose concurrent passes stand down because the last one needed
+  // the whole passes runs those again without first reading the PR count
+  // (one host synchronisation less; nothing since the degree bound's
+  // synchronisation has changed the bound: no LP, PR does not lower it)
+  const bool eager_seq = c.eager_seq && c.capforest == 1 && n > 2 && c.skip_concurrent &&
+                         !c.lp_now && !flags_dev;
+  bool need_seq = eager_seq;
+  if (!eager_seq) {
+    rc = sync_state(g);
+    if (rc) return rc;
+    if (flags_dev && M > 0)
+      CK(cudaMemcpyAsync(c.pr_flags_host, flags_dev, (size_t)M, cudaMemcpyDeviceToHost, s));
+    const long long marks = (long long)(g->hst->marks_pr + g->hst->marks_cf);
+    o->marks_pr = (long long)g->hst->marks_pr;
+    o->marks_cc = (long long)g->hst->marks_cf;
+    o->cc_ran = c.capforest == 1 && n > 2 && !c.skip_concurrent &&
+                !(c.cc_skip_pr >= 0 && o->marks_pr >= c.cc_skip_pr);
+    // the sequential pass when the round marked nothing (Algorithm 2), and on
+    // small graphs (n <= 8192, where a pass costs a few rounds' fixed cost at
+    // most) also when it marked so little (fewer edges than n / 64) that
+    // contracting would spend a whole round on almost no vertices; its marks
+    // only add
+    need_seq = c.capforest == 2 || c.capforest == 4 ||
+               (c.capforest == 1 && (marks == 0 || (n <= 8192 && marks * 64 < n)));
+  }
   // whole passes driven by one warp each (the default), when the bound fits
   // their keys: one pass from cf_start in mode 4, else several from
   // different start vertices with private arrays, as many as keep their hot
@@ -891,6 +903,14 @@ int mark_round(mincut_graph* g, const RoundCfg& c, long long lambda_before, Roun
     }
     CK(cudaStreamSynchronize(s));
   }
+  if (eager_seq) {
+    if (!o->seq_pass) {  // (no pass could run: the state is read here)
+      rc = sync_state(g);
+      if (rc) return rc;
+    }
+    o->marks_pr = (long long)g->hst->marks_pr;
+    o->marks_cc = 0;
+  }
   o->marks_cf = (long long)g->hst->marks_cf;
   lam = (long long)g->hst->lambda;
   if (lam < lambda_before) {
@@ -930,6 +950,7 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
   // the concurrent passes marked fewer than n / 64 edges the last time they
   // ran: they stand down in rounds whose PR tests hook at least n / 64
   bool cc_low = false;
+  bool barely = false;  // the last contraction kept at least half the vertices
   for (;; ++*round_io) {
     const int round = *round_io;
     if (op.max_rounds > 0 && round >= op.max_rounds) break;
@@ -940,6 +961,7 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
     }
     c.cf_private = mode;
     c.skip_concurrent = skip_cc && g->n <= kSkipConcurrentMaxN;
+    c.eager_seq = c.skip_concurrent && barely;
     c.cc_skip_pr = cc_low && c.capforest == 1 && op.cf_visit != 2 ? (g->n + 63) / 64 : -1;
     c.lp_now = lp_allowed && (op.lp_every_round || round == 0);
     c.passes = op.passes > 0 ? op.passes : std::max(32, std::min(g->max_passes, g->n / 4));
@@ -953,7 +975,9 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
     // concurrent passes that marked almost nothing before the whole-graph
     // passes had to run: small graphs skip them in the next round
     // (and keep skipping them while those passes keep running)
-    skip_cc = c.skip_concurrent ? o.seq_pass
+    // (in a skipping round the whole passes run regardless: they were needed
+    // if PR alone hooked fewer than n / 64 edges)
+    skip_cc = c.skip_concurrent ? o.seq_pass && o.marks_pr * 64 < (long long)n_before
                                 : c.capforest == 1 && o.seq_pass &&
                                       o.marks_cc * 64 < (long long)n_before;
     if (o.cc_ran) cc_low = o.marks_cc * 64 < (long long)n_before;
@@ -975,6 +999,7 @@ int exact_rounds(mincut_graph* g, const mincut_options& op, RoundCfg c, bool lp_
     // (the visit-mode choice times each round to its end: no deferral then)
     rc = contract_current<WT>(g, &n2, &m2, true, op.cf_visit != 2);
     if (rc) return rc;
+    barely = 2 * (long long)n2 >= (long long)n_before;
     if (op.cf_visit == 2 && rate[mode] < 0) {
       const double ms = std::chrono::duration<double, std::milli>(
                             std::chrono::steady_clock::now() - t0).count();
