@@ -385,7 +385,8 @@ __global__ void sym_final_kernel(DevState* st) {
 // shared memory; phase 2 spreads the queued intersections over all threads
 // of the block, g lanes per entry with g the largest power of two that still
 // gives every entry its own lane group, so that a few long intersections in a
-// tile do not leave the other lanes idle.
+// tile do not leave the other lanes idle; each lane searches kPrIlp of the
+// shorter row's entries at once, in lockstep over the longer row.
 constexpr int kPrQueue = kET;
 // a's entries a lane of a PR3/PR4 intersection searches at once
 constexpr int kPrIlp = 4;
