@@ -89,3 +89,29 @@ def test_kernel_table_shares_and_algorithmic_rates():
     assert t["pr_marks"]["frac"] == pytest.approx(gbs / 8000.0)
     assert "alg_gbs" not in t["union_find"]  # no algorithmic byte count
     assert bench.kernel_table({}, 1, 8000.0) == {}
+
+
+def test_roofline_of_dominant_kernel_traffic_and_note():
+    # pr_marks has the longest time among the categories with a byte count
+    # (union_find has none and is ignored even though it is listed)
+    prof = {"pr_marks": {"ms": 3.0, "units": 3 * 29031216, "launches": 3},
+            "contract_rows": {"ms": 2.0, "units": 4 * 10**7, "launches": 4},
+            "union_find": {"ms": 9.0, "units": 0, "launches": 12}}
+    r = bench.roofline_of(prof, 6776.3, "measured")
+    assert r["kernel"] == "pr_marks" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    alg = 29031216 * bench.ALG_BYTES["pr_marks"]  # per launch
+    assert r["alg_bytes_per_launch"] == pytest.approx(alg)
+    assert r["avg_launch_ms"] == pytest.approx(1.0)
+    assert r["achieved"] == pytest.approx(alg / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6776.3)
+    # traffic: the captured DRAM bytes per entry, scaled to a launch's entries
+    assert r["traffic"] == pytest.approx(bench.TRAFFIC_PER_UNIT["pr_marks"] * 29031216)
+    assert "note" not in r
+    # a latency-bound category carries its note, and no traffic without a capture
+    prof = {"capforest_seq": {"ms": 5000.0, "units": 2 * 169364222, "launches": 2},
+            "pr_marks": {"ms": 8.0, "units": 10**8, "launches": 10}}
+    r = bench.roofline_of(prof, 6776.3, "measured")
+    assert r["kernel"] == "capforest_seq" and r["traffic"] is None
+    assert "latency-bound" in r["note"]
+    assert bench.roofline_of({"union_find": {"ms": 1.0, "units": 0, "launches": 1}},
+                             6776.3, "measured") is None
